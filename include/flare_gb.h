@@ -1,0 +1,207 @@
+/*
+ * flare_gb.h -- C ABI of the GB300 (sm_103a) implementation of the FLARE
+ * mapped sparse-GP force field's per-step hot path: cell-list neighbour
+ * search, normalized ACE-B2 descriptors, mapped energy and variance, and
+ * forces by the reordered chain rule.
+ *
+ * Paper: "Micron-scale heterogeneous catalysis with Bayesian force fields
+ * from first principles and active learning" (arXiv 2204.12573), Sec. V-B
+ * (descriptors, kernel, mapped sparse GP, Eq. 1 and Eq. 2, force reordering,
+ * multi-element compaction) and Sec. V-C (atom batching, neighbour lists).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an int status: FLR_OK (0) or one of the FLR_E*
+ *   codes below.  On error, flr_last_error() returns a message for the
+ *   calling thread; the message stays valid until the next call on that
+ *   thread.
+ * - All per-atom arrays are DEVICE pointers owned by the caller (for example
+ *   torch tensors).  The library never frees them and never keeps them past
+ *   the call, except where stated for flr_md_state.
+ * - Calls that take a cudaStream_t enqueue work on that stream and return
+ *   without synchronizing, unless stated otherwise.  Errors found on the
+ *   device (neighbour-list overflow, non-finite forces, internal wait
+ *   timeouts) are recorded in a device status word and reported by the
+ *   next flr_sync() on the context.
+ * - Units: Angstrom, eV, amu, ps.  Species are 0 .. n_species-1
+ *   (0 = Pt, 1 = H in the H2/Pt(111) workload).
+ * - Descriptor component order (full layout, dimension d_full):
+ *   index = tri(a, b) * (l_max + 1) + l for radial channels
+ *   a = s * n_max + n, a <= b, tri() row-major over the upper triangle.
+ */
+#ifndef FLARE_GB_H
+#define FLARE_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *flr_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+/* status codes */
+#define FLR_OK 0
+#define FLR_EINVAL 1           /* invalid argument or unsupported parameter */
+#define FLR_ENOMEM 2           /* device allocation failed */
+#define FLR_ECUDA 3            /* CUDA runtime error (message has the CUDA error string) */
+#define FLR_ENBR_OVERFLOW 4    /* an atom has more neighbours than max_nbr; rebuild with a larger max_nbr */
+#define FLR_ETIMEOUT 5         /* a device-side wait gave up (kernel returned early; results invalid) */
+#define FLR_EBUDGET 6          /* request exceeds the configured memory budget */
+#define FLR_EDEVICE 7          /* device-detected invalid data (non-finite force, image shift out of range) */
+#define FLR_ENOMODEL 8         /* flr_set_model() not called for every species */
+
+/* quadratic-form precision (Eq. 1 and Eq. 2 evaluated as GEMMs) */
+#define FLR_PREC_FP32 0        /* FP32 SIMT GEMM (the plain path) */
+#define FLR_PREC_TF32 1        /* tcgen05 kind::tf32, FP32 accumulate in tensor memory */
+#define FLR_PREC_BF16X3 2      /* tcgen05 kind::f16, hi/lo BF16 split, 3 products, FP32 accumulate */
+
+/* indices into the per-evaluation totals array (double[FLR_NTOTALS], device) */
+#define FLR_TOT_ENERGY 0       /* sum_i E_i (eV), FP64 */
+#define FLR_TOT_VIRIAL 1       /* 9 entries, W_ab = -sum_pairs (r_ij)_a (dE_i/dr_ij)_b (eV), FP64 */
+#define FLR_TOT_MAX_SIGMA 10   /* max_i sqrt(V_i) */
+#define FLR_TOT_N_ISOLATED 11  /* atoms with no neighbour inside r_cut (descriptor defined as 0) */
+#define FLR_TOT_KINETIC 12     /* sum_i m_i v_i^2 / 2 (eV), written by flr_md_step only */
+#define FLR_TOT_N_REBUILDS 13  /* neighbour-list rebuilds performed by the last flr_md_step call */
+#define FLR_NTOTALS 16
+
+typedef struct flr_ctx flr_ctx;
+typedef struct flr_nbrlist flr_nbrlist;
+
+/* Model hyperparameters (Sec. V-B).  Supported: n_species = 2, n_max in
+ * {7, 8}, l_max = 3, max_nbr a multiple of 32 in [32, 512]. */
+typedef struct {
+    int32_t n_species;   /* chemical species S */
+    int32_t n_max;       /* radial functions N (Chebyshev T_0 .. T_{N-1} of 2r/r_cut - 1) */
+    int32_t l_max;       /* maximum angular momentum L of the real spherical harmonics */
+    int32_t max_nbr;     /* neighbour-list row capacity per atom */
+    double r_cut;        /* descriptor cutoff (A); cutoff function (r_cut - r)^2 */
+    double skin;         /* Verlet skin (A); the list holds pairs closer than r_cut + skin */
+    int32_t precision;   /* FLR_PREC_* */
+    int32_t compaction;  /* 1: species-block compaction (Sec. V-B), 0: every atom uses d_full */
+} flr_params;
+
+/* One atomic structure.  pos: device float[n_atoms][4] (x, y, z, unused),
+ * 16-byte aligned.  species: device int32[n_atoms].  cell: host, rows are
+ * the lattice vectors a1, a2, a3.  pbc[d] != 0 makes direction d periodic;
+ * along periodic directions positions should lie inside the cell (the
+ * neighbour build accepts image offsets up to 2 cells). */
+typedef struct {
+    int32_t n_atoms;
+    const float *pos;
+    const int32_t *species;
+    double cell[9];
+    int32_t pbc[3];
+} flr_system;
+
+/* Per-atom results (device pointers; any may be NULL except forces). */
+typedef struct {
+    float *energy;       /* [n] E_i = d^T beta_{s_i} d (Eq. 1, mapped) */
+    float *forces;       /* [n][3] F_i = -dE/dr_i */
+    float *variance;     /* [n] V_i = d^T Sigma_{s_i} d (Eq. 2, mapped) */
+    float *sigma;        /* [n] sqrt(V_i): the predictive uncertainty */
+    double *totals;      /* [FLR_NTOTALS] reductions, see FLR_TOT_* */
+} flr_outputs;
+
+/* MD state for flr_md_step (velocity Verlet).  pos and vel are device
+ * float[n][4] updated in place; vel[.][3] is unused.  The forces buffer of
+ * the flr_outputs passed to flr_md_step must hold the forces of the current
+ * positions when forces_valid != 0; otherwise they are computed first. */
+typedef struct {
+    int32_t n_atoms;
+    float *pos;
+    float *vel;
+    const int32_t *species;
+    double cell[9];
+    int32_t pbc[3];
+    double masses[8];       /* amu, per species */
+    double dt;              /* ps (0.0005 = 0.5 fs) */
+    int32_t rebuild_every;  /* forced rebuild cadence in steps (plus max displacement > skin/2) */
+    int32_t forces_valid;   /* set to 1 by flr_md_step on return */
+    int64_t step;           /* running step counter, advanced by flr_md_step */
+} flr_md_state;
+
+/* Thread-local text of the last error on the calling thread. */
+const char *flr_last_error(void);
+
+/* Library version string. */
+const char *flr_version(void);
+
+/* Create a context on CUDA device `device` (allocates the device status
+ * word; model and workspace are allocated later).  *out is owned by the
+ * caller and released with flr_destroy. */
+int flr_create(const flr_params *params, int device, flr_ctx **out);
+
+/* Release a context and every device buffer it owns (not the nbrlists). */
+int flr_destroy(flr_ctx *ctx);
+
+/* Descriptor dimensions: d_full = C(C+1)/2 (L+1) with C = S*N, and
+ * d_single = N(N+1)/2 (L+1) for a one-species environment (Sec. V-B:
+ * 420 and 112 for N = 7, L = 3). */
+int flr_descriptor_dims(const flr_ctx *ctx, int32_t *d_full, int32_t *d_single);
+
+/* Switch the quadratic-form precision of an existing context. */
+int flr_set_precision(flr_ctx *ctx, int32_t precision);
+
+/* Upload the mapped model of central species `species` (Eq. 1, Eq. 2):
+ * beta and sigma are HOST double[d_full][d_full], row-major, symmetric
+ * (the library uses (M + M^T)/2 and reports the largest asymmetry through
+ * flr_last_error as information).  Builds the per-class compacted blocks
+ * and the FP32 / BF16-hi/lo copies on the device.  Synchronous. */
+int flr_set_model(flr_ctx *ctx, int32_t species, const double *beta, const double *sigma);
+
+/* Allocate a neighbour list for systems of up to n_atoms atoms (device
+ * memory: n_atoms * max_nbr * 4 bytes plus O(n_atoms) bookkeeping). */
+int flr_nbrlist_create(flr_ctx *ctx, int32_t n_atoms, flr_nbrlist **out);
+int flr_nbrlist_destroy(flr_nbrlist *nl);
+
+/* Device views of a built list: entries[n][max_nbr] int32 = (j << 7) |
+ * image code, code = (sx+2)*25 + (sy+2)*5 + (sz+2) for the lattice image
+ * S = (sx, sy, sz) of atom j; count[n] int32 neighbours per row;
+ * group[n] int32 compaction class (-1: no neighbours). */
+int flr_nbrlist_view(const flr_nbrlist *nl, int32_t **entries, int32_t **count, int32_t **group,
+                     int32_t *max_nbr);
+
+/* Cell-list neighbour search (Sec. V-C neighbour lists; Sec. V-B local
+ * environment): every (i, j, S) with |r_j + S.cell - r_i| < r_cut + skin,
+ * (j, S) != (i, 0), rows ordered by visiting bins in a fixed stencil
+ * order and atoms inside a bin by index.  Distances are decided in FP32,
+ * and in FP64 within 1e-5 relative of the cutoff.  Also classifies every
+ * atom for the species-block compaction and records the positions for the
+ * displacement trigger.  SYNCHRONIZES the stream (the bin grid is planned
+ * from the atoms' bounding box).  FLR_ENBR_OVERFLOW if a row exceeds
+ * max_nbr (the message gives the count needed). */
+int flr_build_neighbors(flr_ctx *ctx, const flr_system *sys, flr_nbrlist *nl, flr_stream_t stream);
+
+/* Normalized ACE-B2 descriptors d = B / ||B|| in the full layout
+ * (Sec. V-B): d_hat device float[n][d_full] (components outside an atom's
+ * compaction block are written as 0), norm device float[n] = ||B||. */
+int flr_compute_descriptors(flr_ctx *ctx, const flr_system *sys, const flr_nbrlist *nl,
+                            float *d_hat, float *norm, flr_stream_t stream);
+
+/* Energy, forces and uncertainty of every atom (Eq. 1, Eq. 2, Sec. V-B
+ * force reordering): descriptor -> quadratic forms on the selected
+ * precision -> reordered force back-propagation with a deterministic
+ * fixed-point scatter -> FP64 reductions.  Asynchronous. */
+int flr_energy_forces_uncertainty(flr_ctx *ctx, const flr_system *sys, const flr_nbrlist *nl,
+                                  flr_outputs *out, flr_stream_t stream);
+
+/* n_steps of velocity-Verlet MD (metal units): half kick, drift, neighbour
+ * rebuild when due (every rebuild_every steps, or when an atom moved more
+ * than skin/2 since the last build, decided on the device), forces, half
+ * kick.  Positions are wrapped into the cell at each rebuild.  The list
+ * must have been built once with flr_build_neighbors.  Asynchronous. */
+int flr_md_step(flr_ctx *ctx, flr_md_state *st, flr_nbrlist *nl, int32_t n_steps,
+                flr_outputs *out, flr_stream_t stream);
+
+/* Synchronize `stream` and report (and clear) device-side errors. */
+int flr_sync(flr_ctx *ctx, flr_stream_t stream);
+
+/* Number of kernels the library launched on this context so far. */
+int64_t flr_launch_count(const flr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLARE_GB_H */

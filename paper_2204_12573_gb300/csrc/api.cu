@@ -1,0 +1,632 @@
+// C ABI of libflare_gb: context, model upload, workspace, entry points.
+// See include/flare_gb.h for the contract of every exported function.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace flr {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return FLR_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FLR_ENOMEM : FLR_ECUDA;
+}
+
+int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc, const float *bb, double margin);
+int launch_set_rebuild(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
+int launch_clear_rebuild_counter(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
+int launch_copy_rebuilds(flr_ctx *ctx, flr_nbrlist *nl, double *totals, cudaStream_t st);
+
+namespace {
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+uint16_t f2bf(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);   // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+float bf2f(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+int tri(int a, int b, int C) { return a * C - a * (a - 1) / 2 + (b - a); }
+
+template <typename T>
+int dev_alloc(T **p, size_t count, const char *what)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cuda_fail(cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * count), what);
+}
+
+void free_workspace(flr_ctx *ctx)
+{
+    cudaFree(ctx->A);
+    cudaFree(ctx->norm);
+    for (int r = 0; r < 2; ++r) {
+        cudaFree(ctx->D32[r]);
+        cudaFree(ctx->Dhi[r]);
+        cudaFree(ctx->Dlo[r]);
+        cudaFree(ctx->P[r]);
+        ctx->D32[r] = nullptr;
+        ctx->Dhi[r] = ctx->Dlo[r] = nullptr;
+        ctx->P[r] = nullptr;
+    }
+    cudaFree(ctx->Facc);
+    cudaFree(ctx->partials);
+    ctx->A = ctx->norm = nullptr;
+    ctx->Facc = nullptr;
+    ctx->partials = nullptr;
+    ctx->ws_n = 0;
+}
+
+// Workspace for n atoms: A, norms, descriptor rows per region (FP32 and
+// BF16 hi/lo), quadratic-form products, fixed-point force accumulators and
+// reduction partials.  Grown (never shrunk) on demand; allocation happens
+// before any kernel of the call is enqueued.
+int ensure_workspace(flr_ctx *ctx, int n)
+{
+    if (n <= ctx->ws_n) return FLR_OK;
+    cudaDeviceSynchronize();
+    free_workspace(ctx);
+    const Dims &D = ctx->dims;
+    const size_t N = (size_t)std::max(n, 1);
+    int s = FLR_OK;
+    if (s == FLR_OK) s = dev_alloc(&ctx->A, N * D.nA, "workspace A");
+    if (s == FLR_OK) s = dev_alloc(&ctx->norm, N, "workspace norm");
+    for (int r = 0; r < 2 && s == FLR_OK; ++r) {
+        s = dev_alloc(&ctx->D32[r], N * D.kp32[r], "workspace D32");
+        if (s == FLR_OK) s = dev_alloc(&ctx->Dhi[r], N * D.kp64[r], "workspace Dhi");
+        if (s == FLR_OK) s = dev_alloc(&ctx->Dlo[r], N * D.kp64[r], "workspace Dlo");
+        if (s == FLR_OK) s = dev_alloc(&ctx->P[r], N * 2 * D.K[r], "workspace P");
+    }
+    if (s == FLR_OK) s = dev_alloc(&ctx->Facc, N * 3, "workspace forces");
+    const size_t nvir = (N + kWarpsDesc - 1) / kWarpsDesc, nfin = (N + 255) / 256;
+    if (s == FLR_OK) s = dev_alloc(&ctx->partials, nvir * 9 + nfin * 4 + 16, "workspace partials");
+    if (s != FLR_OK) {
+        free_workspace(ctx);
+        return s;
+    }
+    ctx->ws_n = (int)N;
+    return FLR_OK;
+}
+
+int check_system(const flr_ctx *ctx, const flr_nbrlist *nl, const flr_system *sys)
+{
+    if (!sys || !nl) {
+        set_error("null system or neighbour list");
+        return FLR_EINVAL;
+    }
+    if (nl->ctx != ctx) {
+        set_error("neighbour list belongs to another context");
+        return FLR_EINVAL;
+    }
+    if (sys->n_atoms < 0 || sys->n_atoms > nl->n_cap) {
+        set_error("n_atoms out of range for this neighbour list");
+        return FLR_EINVAL;
+    }
+    if (sys->n_atoms > 0 && (!sys->pos || !sys->species)) {
+        set_error("null pos or species");
+        return FLR_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(sys->pos) % 16) {
+        set_error("pos must be 16-byte aligned float[n][4]");
+        return FLR_EINVAL;
+    }
+    return FLR_OK;
+}
+
+int check_model(const flr_ctx *ctx)
+{
+    for (int s = 0; s < ctx->p.n_species; ++s)
+        if (!ctx->model_set[s]) {
+            set_error("flr_set_model has not been called for species " + std::to_string(s));
+            return FLR_ENOMODEL;
+        }
+    return FLR_OK;
+}
+
+int status_to_code(int st)
+{
+    if (st & kErrTimeout) {
+        set_error("a device-side wait timed out (results invalid)");
+        return FLR_ETIMEOUT;
+    }
+    if (st & kErrOverflow) {
+        set_error("neighbour list overflow: an atom has more than max_nbr neighbours");
+        return FLR_ENBR_OVERFLOW;
+    }
+    if (st & kErrShift) {
+        set_error("image shift out of range (positions far outside the cell, or cell too narrow)");
+        return FLR_EDEVICE;
+    }
+    if (st & kErrNonFinite) {
+        set_error("non-finite or overflowing force");
+        return FLR_EDEVICE;
+    }
+    if (st & kErrSpecies) {
+        set_error("species index out of range");
+        return FLR_EINVAL;
+    }
+    return FLR_OK;
+}
+
+int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+             flr_outputs *out, const KickArgs &kick, cudaStream_t st)
+{
+    if (n == 0) return FLR_OK;
+    cudaError_t e = cudaMemsetAsync(ctx->Facc, 0, sizeof(long long) * 3 * (size_t)n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "clear force accumulators");
+    int s = launch_desc(ctx, nl, pos, species, n, st);
+    if (s != FLR_OK) return s;
+    s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, st) : launch_qform_tc(ctx, nl, st);
+    if (s != FLR_OK) return s;
+    s = launch_force(ctx, nl, pos, species, n, out, st);
+    if (s != FLR_OK) return s;
+    return launch_finalize(ctx, nl, n, out, kick, st);
+}
+
+}  // namespace
+}  // namespace flr
+
+using namespace flr;
+
+extern "C" {
+
+const char *flr_last_error(void) { return g_err.c_str(); }
+
+const char *flr_version(void) { return "flare_gb 0.1 (sm_103a)"; }
+
+int flr_create(const flr_params *p, int device, flr_ctx **out)
+{
+    if (!p || !out) {
+        set_error("flr_create: null argument");
+        return FLR_EINVAL;
+    }
+    *out = nullptr;
+    if (p->n_species != kSpecies || (p->n_max != 7 && p->n_max != 8) || p->l_max != kL) {
+        set_error("flr_create: supported hyperparameters are n_species = 2, n_max in {7, 8}, l_max = 3");
+        return FLR_EINVAL;
+    }
+    if (p->max_nbr < 32 || p->max_nbr > 512 || p->max_nbr % 32) {
+        set_error("flr_create: max_nbr must be a multiple of 32 in [32, 512]");
+        return FLR_EINVAL;
+    }
+    if (!(p->r_cut > 0.0) || !(p->skin >= 0.0) || p->precision < 0 || p->precision > 2) {
+        set_error("flr_create: invalid r_cut, skin or precision");
+        return FLR_EINVAL;
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    flr_ctx *c = new flr_ctx();
+    std::memset(static_cast<void *>(c), 0, sizeof(flr_ctx));
+    c->p = *p;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    Dims &D = c->dims;
+    D.N = p->n_max;
+    D.C = kSpecies * D.N;
+    D.nA = D.C * kNLM;
+    D.d_full = D.C * (D.C + 1) / 2 * (kL + 1);
+    D.d_single = D.N * (D.N + 1) / 2 * (kL + 1);
+    D.K[0] = D.d_full;
+    D.K[1] = D.d_single;
+    for (int r = 0; r < 2; ++r) {
+        D.kp32[r] = round_up(D.K[r], 32);
+        D.kp64[r] = round_up(D.K[r], 64);
+        D.nrows_pad[r] = round_up(2 * D.K[r], 288);
+    }
+    int s = dev_alloc(&c->status, 4, "status word");
+    if (s == FLR_OK) s = cuda_fail(cudaMemset(c->status, 0, 4 * sizeof(int)), "status word");
+    // index tables
+    std::vector<int32_t> tf, ts;
+    for (int a = 0; a < D.C; ++a)
+        for (int b = a; b < D.C; ++b)
+            for (int l = 0; l <= kL; ++l) tf.push_back(a | (b << 8) | (l << 16));
+    for (int a = 0; a < D.N; ++a)
+        for (int b = a; b < D.N; ++b)
+            for (int l = 0; l <= kL; ++l) ts.push_back(a | (b << 8) | (l << 16));
+    for (int t = 0; t < kSpecies; ++t)
+        for (int a = 0; a < D.N; ++a)
+            for (int b = a; b < D.N; ++b)
+                for (int l = 0; l <= kL; ++l) ts.push_back(tri(t * D.N + a, t * D.N + b, D.C) * (kL + 1) + l);
+    if (s == FLR_OK) s = dev_alloc(&c->tab_full, tf.size(), "tables");
+    if (s == FLR_OK) s = dev_alloc(&c->tab_single, ts.size(), "tables");
+    if (s == FLR_OK)
+        s = cuda_fail(cudaMemcpy(c->tab_full, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice), "tables");
+    if (s == FLR_OK)
+        s = cuda_fail(cudaMemcpy(c->tab_single, ts.data(), ts.size() * 4, cudaMemcpyHostToDevice), "tables");
+    if (s != FLR_OK) {
+        flr_destroy(c);
+        return s;
+    }
+    *out = c;
+    return FLR_OK;
+}
+
+int flr_destroy(flr_ctx *c)
+{
+    if (!c) return FLR_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_workspace(c);
+    for (int g = 0; g < kGroups; ++g) {
+        cudaFree(c->W32[g]);
+        cudaFree(c->Whi[g]);
+        cudaFree(c->Wlo[g]);
+    }
+    for (int s = 0; s < kSpecies; ++s) {
+        delete[] c->beta_h[s];
+        delete[] c->sigma_h[s];
+    }
+    cudaFree(c->tab_full);
+    cudaFree(c->tab_single);
+    cudaFree(c->status);
+    delete c->maps;
+    delete c;
+    return FLR_OK;
+}
+
+int flr_descriptor_dims(const flr_ctx *c, int32_t *d_full, int32_t *d_single)
+{
+    if (!c) return FLR_EINVAL;
+    if (d_full) *d_full = c->dims.d_full;
+    if (d_single) *d_single = c->dims.d_single;
+    return FLR_OK;
+}
+
+int flr_set_precision(flr_ctx *c, int32_t precision)
+{
+    if (!c || precision < 0 || precision > 2) {
+        set_error("flr_set_precision: invalid argument");
+        return FLR_EINVAL;
+    }
+    c->p.precision = precision;
+    return FLR_OK;
+}
+
+int flr_set_model(flr_ctx *c, int32_t species, const double *beta, const double *sigma)
+{
+    if (!c || !beta || !sigma || species < 0 || species >= kSpecies) {
+        set_error("flr_set_model: invalid argument");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    const Dims &D = c->dims;
+    const int d = D.d_full;
+    double *bh = new double[(size_t)d * d], *sh = new double[(size_t)d * d];
+    for (int r = 0; r < d; ++r)
+        for (int q = 0; q < d; ++q) {
+            bh[(size_t)r * d + q] = 0.5 * (beta[(size_t)r * d + q] + beta[(size_t)q * d + r]);
+            sh[(size_t)r * d + q] = 0.5 * (sigma[(size_t)r * d + q] + sigma[(size_t)q * d + r]);
+        }
+    delete[] c->beta_h[species];
+    delete[] c->sigma_h[species];
+    c->beta_h[species] = bh;
+    c->sigma_h[species] = sh;
+    // compact index maps of the three classes
+    std::vector<int> idx_full(d), idx_single[kSpecies];
+    for (int k = 0; k < d; ++k) idx_full[k] = k;
+    for (int t = 0; t < kSpecies; ++t)
+        for (int a = 0; a < D.N; ++a)
+            for (int b = a; b < D.N; ++b)
+                for (int l = 0; l <= kL; ++l) idx_single[t].push_back(tri(t * D.N + a, t * D.N + b, D.C) * (kL + 1) + l);
+    for (int cls = 0; cls < 3; ++cls) {
+        const int g = species * 3 + cls, r = group_region(g);
+        const std::vector<int> &idx = cls == 0 ? idx_full : idx_single[cls - 1];
+        const int K = D.K[r], rows = D.nrows_pad[r];
+        std::vector<float> w32((size_t)rows * D.kp32[r], 0.f);
+        std::vector<uint16_t> whi((size_t)rows * D.kp64[r], 0), wlo((size_t)rows * D.kp64[r], 0);
+        for (int n = 0; n < 2 * K; ++n) {
+            const double *src = n < K ? bh : sh;
+            const int rn = idx[n % K];
+            for (int k = 0; k < K; ++k) {
+                const double v = src[(size_t)rn * d + idx[k]];
+                w32[(size_t)n * D.kp32[r] + k] = (float)v;
+                const uint16_t h = f2bf((float)v);
+                whi[(size_t)n * D.kp64[r] + k] = h;
+                wlo[(size_t)n * D.kp64[r] + k] = f2bf((float)(v - (double)bf2f(h)));
+            }
+        }
+        int s = FLR_OK;
+        if (!c->W32[g]) {
+            s = dev_alloc(&c->W32[g], w32.size(), "model");
+            if (s == FLR_OK) s = dev_alloc(&c->Whi[g], whi.size(), "model");
+            if (s == FLR_OK) s = dev_alloc(&c->Wlo[g], wlo.size(), "model");
+            if (s != FLR_OK) return s;
+        }
+        s = cuda_fail(cudaMemcpy(c->W32[g], w32.data(), w32.size() * 4, cudaMemcpyHostToDevice), "model upload");
+        if (s == FLR_OK)
+            s = cuda_fail(cudaMemcpy(c->Whi[g], whi.data(), whi.size() * 2, cudaMemcpyHostToDevice), "model upload");
+        if (s == FLR_OK)
+            s = cuda_fail(cudaMemcpy(c->Wlo[g], wlo.data(), wlo.size() * 2, cudaMemcpyHostToDevice), "model upload");
+        if (s != FLR_OK) return s;
+    }
+    c->model_set[species] = true;
+    c->maps_n = -1;   // B maps point at the (possibly new) buffers
+    return FLR_OK;
+}
+
+int flr_nbrlist_create(flr_ctx *c, int32_t n_atoms, flr_nbrlist **out)
+{
+    if (!c || !out || n_atoms < 0 || n_atoms >= (1 << 25)) {
+        set_error("flr_nbrlist_create: invalid argument (n_atoms must be < 2^25)");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    flr_nbrlist *nl = new flr_nbrlist();
+    std::memset(static_cast<void *>(nl), 0, sizeof(flr_nbrlist));
+    nl->ctx = c;
+    nl->n_cap = n_atoms;
+    nl->max_nbr = c->p.max_nbr;
+    const size_t N = (size_t)std::max(n_atoms, 1);
+    int s = dev_alloc(&nl->entries, N * nl->max_nbr, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->count, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->group, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->row, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->atom_of_row, 2 * N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->pos_ref, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->img, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->atom_bin, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->bin_atoms, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->blk_group, 8 * ((N + 511) / 512 + 1) + 65536 + 1024, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->gtab, 1, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->flags, 4, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->bbox, 8, "nbrlist");
+    if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->gtab, 0, sizeof(GroupTab)), "nbrlist");
+    if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->flags, 0, 4 * sizeof(int32_t)), "nbrlist");
+    if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->group, 0xff, N * sizeof(int32_t)), "nbrlist");
+    if (s != FLR_OK) {
+        flr_nbrlist_destroy(nl);
+        return s;
+    }
+    *out = nl;
+    return FLR_OK;
+}
+
+int flr_nbrlist_destroy(flr_nbrlist *nl)
+{
+    if (!nl) return FLR_OK;
+    cudaSetDevice(nl->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(nl->entries);
+    cudaFree(nl->count);
+    cudaFree(nl->group);
+    cudaFree(nl->row);
+    cudaFree(nl->atom_of_row);
+    cudaFree(nl->pos_ref);
+    cudaFree(nl->img);
+    cudaFree(nl->atom_bin);
+    cudaFree(nl->bin_atoms);
+    cudaFree(nl->bin_start);
+    cudaFree(nl->bin_fill);
+    cudaFree(nl->blk_group);
+    cudaFree(nl->gtab);
+    cudaFree(nl->flags);
+    cudaFree(nl->bbox);
+    delete nl;
+    return FLR_OK;
+}
+
+int flr_nbrlist_view(const flr_nbrlist *nl, int32_t **entries, int32_t **count, int32_t **group, int32_t *max_nbr)
+{
+    if (!nl) return FLR_EINVAL;
+    if (entries) *entries = nl->entries;
+    if (count) *count = nl->count;
+    if (group) *group = nl->group;
+    if (max_nbr) *max_nbr = nl->max_nbr;
+    return FLR_OK;
+}
+
+int flr_build_neighbors(flr_ctx *c, const flr_system *sys, flr_nbrlist *nl, flr_stream_t stream)
+{
+    if (!c) return FLR_EINVAL;
+    int s = check_system(c, nl, sys);
+    if (s != FLR_OK) return s;
+    cudaSetDevice(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int n = sys->n_atoms;
+    nl->n = n;
+    // inverse cell for the bounding box, then the plan
+    Plan &P = nl->plan;
+    for (int k = 0; k < 9; ++k) P.cell[k] = sys->cell[k];
+    {
+        const double *m = sys->cell;
+        double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                     m[2] * (m[3] * m[7] - m[4] * m[6]);
+        if (!(std::fabs(det) > 0.0)) {
+            set_error("flr_build_neighbors: singular cell");
+            return FLR_EINVAL;
+        }
+        double *inv = P.inv;
+        inv[0] = (m[4] * m[8] - m[5] * m[7]) / det;
+        inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+        inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+        inv[3] = (m[5] * m[6] - m[3] * m[8]) / det;
+        inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+        inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+        inv[6] = (m[3] * m[7] - m[4] * m[6]) / det;
+        inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+        inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+    }
+    float bb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (n > 0) {
+        s = launch_bbox(c, nl, reinterpret_cast<const float4 *>(sys->pos), n, st);
+        if (s != FLR_OK) return s;
+        s = cuda_fail(cudaMemcpyAsync(bb, nl->bbox, 6 * sizeof(float), cudaMemcpyDeviceToHost, st), "bbox");
+        if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "bbox");
+        if (s != FLR_OK) return s;
+    }
+    s = plan_bins(c, nl, sys->cell, sys->pbc, bb, 2.0 * (c->p.r_cut + c->p.skin));
+    if (s != FLR_OK) return s;
+    if (n == 0) return FLR_OK;
+    s = launch_set_rebuild(c, nl, st);
+    if (s == FLR_OK)
+        s = launch_rebuild(c, nl, reinterpret_cast<const float4 *>(sys->pos), sys->species, n, st, false, nullptr);
+    if (s != FLR_OK) return s;
+    s = cuda_fail(cudaStreamSynchronize(st), "neighbour build");
+    if (s != FLR_OK) return s;
+    int dst[4];
+    GroupTab gt;
+    s = cuda_fail(cudaMemcpy(dst, c->status, sizeof(dst), cudaMemcpyDeviceToHost), "status");
+    if (s == FLR_OK) s = cuda_fail(cudaMemcpy(&gt, nl->gtab, sizeof(gt), cudaMemcpyDeviceToHost), "status");
+    if (s != FLR_OK) return s;
+    if (dst[0]) {
+        cudaMemset(c->status, 0, 4 * sizeof(int));
+        s = status_to_code(dst[0]);
+        if (s == FLR_ENBR_OVERFLOW)
+            set_error("neighbour list overflow: an atom has " + std::to_string(gt.max_count) +
+                      " neighbours, max_nbr is " + std::to_string(nl->max_nbr));
+        return s;
+    }
+    return FLR_OK;
+}
+
+int flr_compute_descriptors(flr_ctx *c, const flr_system *sys, const flr_nbrlist *nl, float *d_hat, float *norm,
+                            flr_stream_t stream)
+{
+    if (!c || !d_hat) {
+        set_error("flr_compute_descriptors: null argument");
+        return FLR_EINVAL;
+    }
+    int s = check_system(c, nl, sys);
+    if (s != FLR_OK) return s;
+    if (sys->n_atoms != nl->n) {
+        set_error("system size differs from the neighbour list's last build");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    s = ensure_workspace(c, sys->n_atoms);
+    if (s != FLR_OK || sys->n_atoms == 0) return s;
+    s = launch_desc(c, nl, reinterpret_cast<const float4 *>(sys->pos), sys->species, sys->n_atoms, st);
+    if (s != FLR_OK) return s;
+    return launch_expand_desc(c, nl, sys->n_atoms, d_hat, norm, st);
+}
+
+int flr_energy_forces_uncertainty(flr_ctx *c, const flr_system *sys, const flr_nbrlist *nl, flr_outputs *out,
+                                  flr_stream_t stream)
+{
+    if (!c || !out || !out->forces || !out->energy) {
+        set_error("flr_energy_forces_uncertainty: null argument (energy and forces are required)");
+        return FLR_EINVAL;
+    }
+    int s = check_system(c, nl, sys);
+    if (s == FLR_OK) s = check_model(c);
+    if (s != FLR_OK) return s;
+    if (sys->n_atoms != nl->n) {
+        set_error("system size differs from the neighbour list's last build");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    s = ensure_workspace(c, sys->n_atoms);
+    if (s != FLR_OK) return s;
+    KickArgs kick;
+    std::memset(&kick, 0, sizeof(kick));
+    if (sys->n_atoms == 0) {
+        if (out->totals)
+            return cuda_fail(cudaMemsetAsync(out->totals, 0, sizeof(double) * FLR_NTOTALS,
+                                             reinterpret_cast<cudaStream_t>(stream)),
+                             "totals");
+        return FLR_OK;
+    }
+    return evaluate(c, nl, reinterpret_cast<const float4 *>(sys->pos), sys->species, sys->n_atoms, out, kick,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_outputs *out,
+                flr_stream_t stream)
+{
+    if (!c || !md || !nl || !out || !out->forces || !out->energy || n_steps < 0) {
+        set_error("flr_md_step: invalid argument");
+        return FLR_EINVAL;
+    }
+    int s = check_model(c);
+    if (s != FLR_OK) return s;
+    if (md->n_atoms != nl->n || !nl->planned || md->rebuild_every < 1 || !(md->dt > 0.0)) {
+        set_error("flr_md_step: build the list with flr_build_neighbors first; rebuild_every >= 1, dt > 0");
+        return FLR_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(md->pos) % 16 || reinterpret_cast<uintptr_t>(md->vel) % 16) {
+        set_error("flr_md_step: pos and vel must be 16-byte aligned float[n][4]");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int n = md->n_atoms;
+    s = ensure_workspace(c, n);
+    if (s != FLR_OK || n == 0) return s;
+    const double ftm2v = 1.0 / 1.0364269e-4;   // (eV/A)/amu -> A/ps^2
+    KickArgs kick;
+    std::memset(&kick, 0, sizeof(kick));
+    kick.vel = reinterpret_cast<float4 *>(md->vel);
+    kick.species = md->species;
+    for (int sp = 0; sp < kSpecies; ++sp) {
+        if (!(md->masses[sp] > 0.0)) {
+            set_error("flr_md_step: masses must be positive");
+            return FLR_EINVAL;
+        }
+        kick.half_dt_over_m[sp] = (float)(0.5 * md->dt * ftm2v / md->masses[sp]);
+        kick.half_m[sp] = (float)(0.5 * md->masses[sp] / ftm2v);
+    }
+    float4 *pos = reinterpret_cast<float4 *>(md->pos);
+    const float skin = (float)c->p.skin;
+    const float disp2 = 0.25f * skin * skin;
+    s = launch_clear_rebuild_counter(c, nl, st);
+    if (s != FLR_OK) return s;
+    if (!md->forces_valid) {
+        KickArgs none;
+        std::memset(&none, 0, sizeof(none));
+        s = evaluate(c, nl, pos, md->species, n, out, none, st);
+        if (s != FLR_OK) return s;
+        md->forces_valid = 1;
+    }
+    kick.enabled = 1;
+    for (int k = 0; k < n_steps; ++k) {
+        s = launch_md_drift(c, nl, pos, kick.vel, out->forces, md->species, n, kick, (float)md->dt, disp2, st);
+        if (s == FLR_OK && (md->step + 1) % md->rebuild_every == 0) s = launch_set_rebuild(c, nl, st);
+        if (s == FLR_OK) s = launch_rebuild(c, nl, pos, md->species, n, st, true, pos);
+        if (s == FLR_OK) s = evaluate(c, nl, pos, md->species, n, out, kick, st);
+        if (s != FLR_OK) return s;
+        md->step += 1;
+    }
+    if (out->totals) s = launch_copy_rebuilds(c, nl, out->totals, st);
+    return s;
+}
+
+int flr_sync(flr_ctx *c, flr_stream_t stream)
+{
+    if (!c) return FLR_EINVAL;
+    cudaSetDevice(c->device);
+    int s = cuda_fail(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)), "flr_sync");
+    if (s != FLR_OK) return s;
+    int st[4];
+    s = cuda_fail(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost), "flr_sync status");
+    if (s != FLR_OK) return s;
+    if (st[0]) {
+        cudaMemset(c->status, 0, sizeof(st));
+        return status_to_code(st[0]);
+    }
+    return FLR_OK;
+}
+
+int64_t flr_launch_count(const flr_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// Internal declarations shared by the translation units of libflare_gb.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+
+#include "../../include/flare_gb.h"
+
+namespace flr {
+
+constexpr int kSpecies = 2;        // species handled by the device code
+constexpr int kL = 3;              // l_max handled by the device code
+constexpr int kNLM = (kL + 1) * (kL + 1);   // 16 real harmonics
+constexpr int kGroups = kSpecies * 3;        // (central species) x (class: both, only 0, only 1)
+constexpr int kWarpsDesc = 8;      // warps per CTA of the per-atom kernels
+
+// device status word bits
+enum : int {
+    kErrOverflow = 1,
+    kErrNonFinite = 2,
+    kErrShift = 4,
+    kErrTimeout = 8,
+    kErrSpecies = 16,
+};
+
+// Group g = s_center * 3 + cls; cls 0 uses the full descriptor, cls 1 + t
+// the one-species block of species t.
+__host__ __device__ inline int group_cls(int g) { return g % 3; }
+__host__ __device__ inline int group_species(int g) { return g / 3; }
+__host__ __device__ inline bool group_full(int g) { return (g % 3) == 0; }
+
+// Region of the compact descriptor rows: 0 = full (d_full), 1 = single (d_single).
+__host__ __device__ inline int group_region(int g) { return group_full(g) ? 0 : 1; }
+
+struct Dims {
+    int N;            // n_max
+    int C;            // S * N channels
+    int nA;           // C * 16 entries of A
+    int d_full, d_single;
+    int kp32[2];      // K padded to 32 (FP32 / TF32 rows), per region
+    int kp64[2];      // K padded to 64 (BF16 rows), per region
+    int K[2];         // unpadded K per region
+    int nrows_pad[2]; // rows of the B operand (2K padded to a multiple of 288)
+};
+
+// Device-side group table, filled by the group-partition kernel.
+struct GroupTab {
+    int count[kGroups];
+    int off[kGroups];       // first row inside its region
+    int tiles_simt[kGroups + 1];  // prefix of SIMT tiles (M-tiles x N-tiles)
+    int tiles_tc[kGroups + 1];    // prefix of tensor-core tiles (M-tiles x N-chunks)
+    int n_isolated;         // atoms with an empty list
+    int max_count;          // longest neighbour row seen (before clipping)
+};
+
+struct Plan {
+    int nb[3];          // bins per lattice direction
+    int R[3];           // stencil reach in bins
+    float flo[3];       // lower fractional bound of the bin grid (0 along periodic dirs)
+    float fspan[3];     // fractional span of the bin grid (1 along periodic dirs)
+    double cell[9];
+    double inv[9];      // inverse of the cell matrix (frac = pos . inv)
+    int pbc[3];
+    long long nbins;
+};
+
+}  // namespace flr
+
+struct flr_nbrlist {
+    flr_ctx *ctx;
+    int n_cap;
+    int n;                 // atoms of the last build
+    int max_nbr;
+    int32_t *entries;      // [n_cap][max_nbr]
+    int32_t *count;        // [n_cap]
+    int32_t *group;        // [n_cap]
+    int32_t *row;          // [n_cap] row inside the group's region
+    int32_t *atom_of_row;  // [2][n_cap]
+    float4 *pos_ref;       // positions at the last build
+    int32_t *img;          // [n_cap] packed image offset of the wrapped position
+    int32_t *atom_bin;     // [n_cap]
+    int32_t *bin_atoms;    // [n_cap]
+    int32_t *bin_start;    // [nbins_cap + 1]
+    int32_t *bin_fill;     // [nbins_cap]
+    int32_t *blk_group;    // [n_blocks][8] per-block group counts
+    flr::GroupTab *gtab;   // device
+    int32_t *flags;        // device [4]: [0] rebuild needed, [1] rebuild counter
+    float *bbox;           // device [6] fractional min / max
+    long long nbins_cap;
+    flr::Plan plan;
+    bool planned;
+};
+
+// TMA tensor maps of the tcgen05 path: A operands per region (BF16 hi / lo,
+// or FP32 rows for TF32) and B operands per group.
+struct TcMaps {
+    CUtensorMap a[2][2];
+    CUtensorMap b[flr::kGroups][2];
+};
+
+struct flr_ctx {
+    flr_params p;
+    int device;
+    int num_sms;
+    flr::Dims dims;
+    int *status;               // device status word [4]
+    long long launches;
+    // model, per group
+    bool model_set[flr::kSpecies];
+    double *beta_h[flr::kSpecies];     // host copies (symmetrized), d_full^2
+    double *sigma_h[flr::kSpecies];
+    float *W32[flr::kGroups];          // [nrows_pad][kp32]  B operand rows (beta rows, then Sigma rows)
+    __nv_bfloat16 *Whi[flr::kGroups];  // [nrows_pad][kp64]
+    __nv_bfloat16 *Wlo[flr::kGroups];
+    // index tables (device): packed (a | b << 8 | l << 16) for each compact component
+    int32_t *tab_full;
+    int32_t *tab_single;
+    // workspace
+    int ws_n;                  // atoms the workspace is sized for
+    float *A;                  // [n][nA]
+    float *norm;               // [n]
+    float *D32[2];             // [n][kp32[r]]
+    __nv_bfloat16 *Dhi[2];     // [n][kp64[r]]
+    __nv_bfloat16 *Dlo[2];
+    float *P[2];               // [n][2K[r]]
+    long long *Facc;           // [n][3] fixed point
+    double *partials;          // [n_blocks][16]
+    int n_part;
+    TcMaps *maps;              // host copy of the current tensor maps
+    int maps_n;                // workspace size the maps were encoded for
+    int maps_prec;
+};
+
+namespace flr {
+
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+inline void count_launch(flr_ctx *ctx, int k = 1) { ctx->launches += k; }
+
+// ---- launchers (one per translation unit) ----
+int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                   cudaStream_t st, bool wrap_positions, float4 *pos_mut);
+int launch_bbox(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, int n, cudaStream_t st);
+int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                cudaStream_t st);
+int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat, float *norm,
+                       cudaStream_t st);
+int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st);
+int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st);
+int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                 flr_outputs *out, cudaStream_t st);
+struct KickArgs {
+    float4 *vel;
+    const int *species;
+    float half_dt_over_m[kSpecies];   // (dt/2) * FTM2V / m_s
+    float half_m[kSpecies];            // m_s / 2 / FTM2V  (kinetic energy in eV from A/ps)
+    int enabled;
+};
+int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick,
+                    cudaStream_t st);
+int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, const float *forces,
+                    const int *species, int n, const KickArgs &kick, float dt, float disp2_max,
+                    cudaStream_t st);
+
+// ---- shared device helpers ----
+
+// Decode a neighbour entry: (j << 7) | code, code = (sx+2)*25 + (sy+2)*5 + (sz+2).
+__device__ __forceinline__ void decode_entry(int e, int &j, int &sx, int &sy, int &sz)
+{
+    j = (int)((unsigned)e >> 7);
+    int code = e & 127;
+    sx = code / 25 - 2;
+    sy = (code / 5) % 5 - 2;
+    sz = code % 5 - 2;
+}
+constexpr int kCenterCode = 62;   // (0, 0, 0)
+
+// Cell passed by value to kernels (rows = lattice vectors).
+struct CellArg {
+    double c[9];
+};
+
+// Pair vector r_ij = r_j + S.cell - r_i in FP32.  Without an image shift the
+// FP32 difference is correctly rounded; with one, the sum is formed in FP64
+// from the exact FP32 inputs so large coordinates lose no accuracy.
+__device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, int sx, int sy,
+                                              int sz, const CellArg &cell)
+{
+    if ((sx | sy | sz) == 0) return make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z);
+    double tx = sx * cell.c[0] + sy * cell.c[3] + sz * cell.c[6];
+    double ty = sx * cell.c[1] + sy * cell.c[4] + sz * cell.c[7];
+    double tz = sx * cell.c[2] + sy * cell.c[5] + sz * cell.c[8];
+    return make_float3((float)(((double)pj.x - (double)pi.x) + tx),
+                       (float)(((double)pj.y - (double)pi.y) + ty),
+                       (float)(((double)pj.z - (double)pi.z) + tz));
+}
+
+}  // namespace flr

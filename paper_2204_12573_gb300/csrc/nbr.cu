@@ -1,0 +1,687 @@
+// Cell-list neighbour search and species-block classification.
+//
+// The local environment of atom i is every (j, S) with
+// |r_j + S.cell - r_i| < r_cut + skin (Sec. V-B "Local structure
+// descriptors"; Sec. V-C: the list is built once and reused while atoms
+// move less than half the skin).  Atoms are binned by fractional coordinate;
+// each bin is at least (r_cut + skin) wide so a fixed stencil of bins covers
+// every neighbour.  All steps run on the device; every kernel of the rebuild
+// sequence first reads the list's "rebuild needed" flag and returns at once
+// when it is clear, so an MD loop can enqueue the sequence every step and
+// let the device decide.
+#include <cfloat>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace flr {
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kGroupBlock = 512;
+
+__device__ __forceinline__ int ordered(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+struct InvArg {
+    double m[9];
+};
+
+__device__ __forceinline__ void frac_of(const float4 &p, const InvArg &inv, double f[3])
+{
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        f[d] = (double)p.x * inv.m[d] + (double)p.y * inv.m[3 + d] + (double)p.z * inv.m[6 + d];
+}
+
+__global__ void k_bbox_init(int *bb)
+{
+    if (threadIdx.x < 3) bb[threadIdx.x] = ordered(FLT_MAX);
+    else if (threadIdx.x < 6) bb[threadIdx.x] = ordered(-FLT_MAX);
+}
+
+__global__ void k_bbox(const float4 *__restrict__ pos, int n, InvArg inv, int *bb)
+{
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double f[3];
+        frac_of(pos[i], inv, f);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fminf(lo[d], (float)f[d]);
+            hi[d] = fmaxf(hi[d], (float)f[d]);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o; o >>= 1) {
+            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(bb + d, ordered(lo[d]));
+            atomicMax(bb + 3 + d, ordered(hi[d]));
+        }
+    }
+}
+
+__global__ void k_bbox_finish(int *bb)
+{
+    if (threadIdx.x < 6) reinterpret_cast<float *>(bb)[threadIdx.x] = unordered(bb[threadIdx.x]);
+}
+
+struct BinArgs {
+    const float4 *pos;
+    float4 *pos_mut;      // non-null: wrap positions in place (MD)
+    int n;
+    InvArg inv;
+    CellArg cell;
+    int nb[3];
+    int pbc[3];
+    float flo[3], fspan[3];
+    int32_t *atom_bin, *img, *bin_count;
+    float4 *pos_ref;
+    GroupTab *gtab;
+    const int32_t *flags;
+    int *status;
+};
+
+__global__ void k_zero_bins(int32_t *cnt, long long nbins, const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbins;
+         b += (long long)gridDim.x * blockDim.x)
+        cnt[b] = 0;
+}
+
+__global__ void k_bin(BinArgs a)
+{
+    if (a.flags[0] == 0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) a.gtab->max_count = 0;
+    if (i >= a.n) return;
+    float4 p = a.pos_mut ? a.pos_mut[i] : a.pos[i];
+    double f[3];
+    frac_of(p, a.inv, f);
+    int im[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (a.pbc[d]) {
+            im[d] = (int)floor(f[d]);
+            f[d] -= im[d];
+        }
+    if (a.pos_mut && (im[0] | im[1] | im[2])) {
+        // wrap in place: r -= img . cell, formed in FP64
+        double x = (double)p.x - (im[0] * a.cell.c[0] + im[1] * a.cell.c[3] + im[2] * a.cell.c[6]);
+        double y = (double)p.y - (im[0] * a.cell.c[1] + im[1] * a.cell.c[4] + im[2] * a.cell.c[7]);
+        double z = (double)p.z - (im[0] * a.cell.c[2] + im[1] * a.cell.c[5] + im[2] * a.cell.c[8]);
+        p.x = (float)x;
+        p.y = (float)y;
+        p.z = (float)z;
+        a.pos_mut[i] = p;
+        im[0] = im[1] = im[2] = 0;
+    }
+    int b[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int k = (int)floor((f[d] - (double)a.flo[d]) / (double)a.fspan[d] * a.nb[d]);
+        b[d] = min(max(k, 0), a.nb[d] - 1);
+        if (im[d] < -100 || im[d] > 100) atomicOr(a.status, kErrShift);
+    }
+    int bin = (b[0] * a.nb[1] + b[1]) * a.nb[2] + b[2];
+    a.atom_bin[i] = bin;
+    a.img[i] = (im[0] & 0xFF) | ((im[1] & 0xFF) << 8) | ((im[2] & 0xFF) << 16);
+    a.pos_ref[i] = p;
+    atomicAdd(a.bin_count + bin, 1);
+}
+
+// exclusive scan, three passes: per-block scan -> scan of block sums -> add
+__device__ __forceinline__ int block_exclusive_scan(int v, int *smem, int &total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? smem[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) smem[lane] = s;
+    }
+    __syncthreads();
+    int excl = x - v + (w ? smem[w - 1] : 0);
+    total = smem[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void k_scan_blocks(const int32_t *in, int32_t *out, int32_t *block_sums, long long m,
+                              const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    __shared__ int sm[32];
+    long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
+    int v = i < m ? in[i] : 0;
+    int total;
+    int e = block_exclusive_scan(v, sm, total);
+    if (i < m) out[i] = e;
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_top(int32_t *block_sums, int nblocks, int32_t *grand, const int32_t *flags,
+                           int *status)
+{
+    if (flags[0] == 0) return;
+    __shared__ int sm[32];
+    int carry = 0;
+    for (int base = 0; base < nblocks; base += kScanBlock) {
+        int i = base + threadIdx.x;
+        int v = i < nblocks ? block_sums[i] : 0;
+        int total;
+        int e = block_exclusive_scan(v, sm, total);
+        if (i < nblocks) block_sums[i] = e + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void k_scan_add(int32_t *out, int32_t *fill, const int32_t *block_sums, long long m,
+                           const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    long long i = blockIdx.x * (long long)kScanBlock + threadIdx.x;
+    if (i < m) {
+        int v = out[i] + block_sums[blockIdx.x];
+        out[i] = v;
+        fill[i] = v;
+    }
+}
+
+__global__ void k_scatter(const int32_t *atom_bin, int32_t *fill, int32_t *bin_atoms, int n,
+                          const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int slot = atomicAdd(fill + atom_bin[i], 1);
+    bin_atoms[slot] = i;
+}
+
+// order each bin's atoms by index so that rows come out deterministic
+__global__ void k_sort_bins(const int32_t *bin_start, int32_t *bin_atoms, long long nbins,
+                            const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    int s = bin_start[b], e = bin_start[b + 1];
+    for (int k = s + 1; k < e; ++k) {
+        int v = bin_atoms[k];
+        int q = k - 1;
+        while (q >= s && bin_atoms[q] > v) {
+            bin_atoms[q + 1] = bin_atoms[q];
+            --q;
+        }
+        bin_atoms[q + 1] = v;
+    }
+}
+
+struct RowArgs {
+    const float4 *pos;
+    const int32_t *species;
+    const int32_t *atom_bin, *img, *bin_start, *bin_atoms;
+    int n, max_nbr, compaction;
+    int nb[3], R[3], pbc[3];
+    CellArg cell;
+    float rc2;
+    double rc2d;
+    int32_t *entries, *count, *group;
+    GroupTab *gtab;
+    const int32_t *flags;
+    int *status;
+};
+
+__device__ __forceinline__ int img_comp(int v, int d) { return (int)(int8_t)((v >> (8 * d)) & 0xFF); }
+
+// one warp per atom; lanes take the candidates of a bin 32 at a time
+__global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
+{
+    if (a.flags[0] == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= a.n) return;
+    const float4 pi = a.pos[i];
+    const int bin = a.atom_bin[i];
+    const int bi[3] = {bin / (a.nb[1] * a.nb[2]), (bin / a.nb[2]) % a.nb[1], bin % a.nb[2]};
+    const int imi = a.img[i];
+    int32_t *row = a.entries + (size_t)i * a.max_nbr;
+    int cnt = 0;
+    unsigned smask = 0;
+    for (int dx = -a.R[0]; dx <= a.R[0]; ++dx)
+        for (int dy = -a.R[1]; dy <= a.R[1]; ++dy)
+            for (int dz = -a.R[2]; dz <= a.R[2]; ++dz) {
+                int dd[3] = {dx, dy, dz}, bj[3], sb[3];
+                bool skip = false;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    int k = bi[d] + dd[d];
+                    if (a.pbc[d]) {
+                        int q = (k >= 0) ? k / a.nb[d] : -((-k + a.nb[d] - 1) / a.nb[d]);
+                        sb[d] = q;
+                        bj[d] = k - q * a.nb[d];
+                    } else {
+                        skip |= (k < 0 || k >= a.nb[d]);
+                        sb[d] = 0;
+                        bj[d] = k;
+                    }
+                }
+                if (skip) continue;
+                const int b = (bj[0] * a.nb[1] + bj[1]) * a.nb[2] + bj[2];
+                const int s0 = a.bin_start[b], s1 = a.bin_start[b + 1];
+                for (int base = s0; base < s1; base += 32) {
+                    const int q = base + lane;
+                    bool ok = false;
+                    int entry = 0, sj = 0;
+                    if (q < s1) {
+                        const int j = a.bin_atoms[q];
+                        const int imj = a.img[j];
+                        int S[3];
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) S[d] = sb[d] + img_comp(imi, d) - img_comp(imj, d);
+                        const bool in_range = S[0] >= -2 && S[0] <= 2 && S[1] >= -2 && S[1] <= 2 &&
+                                              S[2] >= -2 && S[2] <= 2;
+                        if (!in_range) atomicOr(a.status, kErrShift);
+                        if (in_range && !(j == i && S[0] == 0 && S[1] == 0 && S[2] == 0)) {
+                            const float4 pj = a.pos[j];
+                            const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], a.cell);
+                            const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                            if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
+                                ok = d2 < a.rc2;
+                            } else {
+                                // near the cutoff: decide in FP64 from the exact inputs
+                                double t[3];
+#pragma unroll
+                                for (int c = 0; c < 3; ++c)
+                                    t[c] = S[0] * a.cell.c[c] + S[1] * a.cell.c[3 + c] + S[2] * a.cell.c[6 + c];
+                                const double x = ((double)pj.x - (double)pi.x) + t[0];
+                                const double y = ((double)pj.y - (double)pi.y) + t[1];
+                                const double z = ((double)pj.z - (double)pi.z) + t[2];
+                                ok = x * x + y * y + z * z < a.rc2d;
+                            }
+                            entry = (j << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
+                            sj = a.species[j];
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+                    if (ok) {
+                        if (slot < a.max_nbr) row[slot] = entry;
+                        smask |= 1u << (sj & 31);
+                    }
+                    cnt += __popc(m);
+                }
+            }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) smask |= __shfl_xor_sync(0xffffffffu, smask, o);
+    if (lane == 0) {
+        if (cnt > a.max_nbr) atomicOr(a.status, kErrOverflow);
+        atomicMax(&a.gtab->max_count, cnt);
+        a.count[i] = min(cnt, a.max_nbr);
+        int g = -1;
+        if (cnt > 0) {
+            const int si = a.species[i];
+            if (si < 0 || si >= kSpecies || (smask >> kSpecies) != 0) atomicOr(a.status, kErrSpecies);
+            int cls = 0;
+            if (a.compaction) cls = (smask == 1u) ? 1 : (smask == 2u ? 2 : 0);
+            g = min(max(si, 0), kSpecies - 1) * 3 + cls;
+        }
+        a.group[i] = g;
+    }
+}
+
+// ---- stable partition of atoms into compaction groups ----
+// Each block of 512 atoms packs one 10-bit counter per group into a
+// 64-bit word, so one block-wide scan yields every atom's rank in its group.
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v,
+                                                             unsigned long long *sm,
+                                                             unsigned long long &total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        unsigned long long s = lane < nw ? sm[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sm[lane] = s;
+    }
+    __syncthreads();
+    unsigned long long excl = x - v + (w ? sm[w - 1] : 0ull);
+    total = sm[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void __launch_bounds__(kGroupBlock) k_group_count(const int32_t *group, int n,
+                                                             int32_t *blk, const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    __shared__ unsigned long long sm[32];
+    int i = blockIdx.x * kGroupBlock + threadIdx.x;
+    int g = i < n ? group[i] : -1;
+    unsigned long long v = g >= 0 ? (1ull << (10 * g)) : 0ull;
+    unsigned long long total;
+    block_scan_u64(v, sm, total);
+    if (threadIdx.x < 8)
+        blk[blockIdx.x * 8 + threadIdx.x] =
+            threadIdx.x < kGroups ? (int)((total >> (10 * threadIdx.x)) & 1023ull) : 0;
+}
+
+struct ScanGroupArgs {
+    int32_t *blk;
+    int nblk;
+    int n;
+    GroupTab *gtab;
+    int ntile_simt[kGroups];
+    int nchunk_tc[kGroups];
+    const int32_t *flags;
+};
+
+__global__ void k_group_scan(ScanGroupArgs a)
+{
+    if (a.flags[0] == 0) return;
+    __shared__ int sm[32];
+    __shared__ int totals[kGroups];
+    for (int g = 0; g < kGroups; ++g) {
+        int carry = 0;
+        for (int base = 0; base < a.nblk; base += kScanBlock) {
+            int b = base + threadIdx.x;
+            int v = b < a.nblk ? a.blk[b * 8 + g] : 0;
+            int total;
+            int e = block_exclusive_scan(v, sm, total);
+            if (b < a.nblk) a.blk[b * 8 + g] = e + carry;
+            carry += total;
+        }
+        if (threadIdx.x == 0) totals[g] = carry;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        GroupTab *t = a.gtab;
+        int off_r[2] = {0, 0};
+        int assigned = 0;
+        for (int g = 0; g < kGroups; ++g) {
+            int r = group_region(g);
+            t->count[g] = totals[g];
+            t->off[g] = off_r[r];
+            off_r[r] += totals[g];
+            assigned += totals[g];
+        }
+        t->n_isolated = a.n - assigned;
+        t->tiles_simt[0] = 0;
+        t->tiles_tc[0] = 0;
+        for (int g = 0; g < kGroups; ++g) {
+            int mt = (totals[g] + 127) / 128;
+            t->tiles_simt[g + 1] = t->tiles_simt[g] + mt * a.ntile_simt[g];
+            t->tiles_tc[g + 1] = t->tiles_tc[g] + mt * a.nchunk_tc[g];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kGroupBlock) k_group_rows(const int32_t *group, int n,
+                                                            const int32_t *blk, const GroupTab *gtab,
+                                                            int32_t *row, int32_t *atom_of_row,
+                                                            int n_cap, const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    __shared__ unsigned long long sm[32];
+    int i = blockIdx.x * kGroupBlock + threadIdx.x;
+    int g = i < n ? group[i] : -1;
+    unsigned long long v = g >= 0 ? (1ull << (10 * g)) : 0ull;
+    unsigned long long total;
+    unsigned long long ex = block_scan_u64(v, sm, total);
+    if (i < n) {
+        if (g >= 0) {
+            int rank = (int)((ex >> (10 * g)) & 1023ull);
+            int r = gtab->off[g] + blk[blockIdx.x * 8 + g] + rank;
+            row[i] = r;
+            atom_of_row[group_region(g) * (size_t)n_cap + r] = i;
+        } else {
+            row[i] = -1;
+        }
+    }
+}
+
+__global__ void k_rebuild_done(int32_t *flags)
+{
+    if (flags[0]) {
+        flags[0] = 0;
+        flags[1] += 1;
+    }
+}
+
+void inverse3(const double *m, double *inv)
+{
+    double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                 m[2] * (m[3] * m[7] - m[4] * m[6]);
+    inv[0] = (m[4] * m[8] - m[5] * m[7]) / det;
+    inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+    inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+    inv[3] = (m[5] * m[6] - m[3] * m[8]) / det;
+    inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+    inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+    inv[6] = (m[3] * m[7] - m[4] * m[6]) / det;
+    inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+    inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
+double width(const double *cell, int d)
+{
+    const double *a = cell, *b = cell + 3, *c = cell + 6;
+    double vol = std::fabs(a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                           a[2] * (b[0] * c[1] - b[1] * c[0]));
+    const double *e = cell + 3 * ((d + 1) % 3), *f = cell + 3 * ((d + 2) % 3);
+    double x = e[1] * f[2] - e[2] * f[1], y = e[2] * f[0] - e[0] * f[2], z = e[0] * f[1] - e[1] * f[0];
+    return vol / std::sqrt(x * x + y * y + z * z);
+}
+
+}  // namespace
+
+// Plan the bin grid from a fractional bounding box (host).  Along open
+// directions the grid covers the box plus a margin of `margin` A on both
+// sides; atoms that later leave it are clamped into the edge bins, which
+// stays correct because every bin is at least r_c wide.
+int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc, const float *bb,
+              double margin)
+{
+    Plan &P = nl->plan;
+    const double rc = ctx->p.r_cut + ctx->p.skin;
+    for (int c = 0; c < 9; ++c) P.cell[c] = cell[c];
+    inverse3(cell, P.inv);
+    if (!std::isfinite(P.inv[0]) || !std::isfinite(P.inv[4]) || !std::isfinite(P.inv[8])) {
+        set_error("flr_build_neighbors: singular cell matrix");
+        return FLR_EINVAL;
+    }
+    long long nbins = 1;
+    for (int d = 0; d < 3; ++d) {
+        const double w = width(cell, d);
+        P.pbc[d] = pbc[d] ? 1 : 0;
+        double flo, fspan;
+        if (pbc[d]) {
+            flo = 0.0;
+            fspan = 1.0;
+        } else {
+            double lo = bb[d], hi = bb[3 + d];
+            if (!(hi >= lo)) { lo = 0.0; hi = 0.0; }
+            flo = lo - margin / w;
+            fspan = (hi - lo) + 2.0 * margin / w;
+        }
+        const double extent = fspan * w;
+        int nb = (int)std::floor(extent / (rc * 1.0001));
+        nb = std::max(1, std::min(nb, 4096));
+        int R = (int)std::ceil(rc / (extent / nb) * (1.0 + 1e-6));
+        if (!pbc[d]) R = std::min(R, nb);
+        if (pbc[d] && R > 2 * nb + 1) {
+            set_error("flr_build_neighbors: periodic cell too narrow for r_cut + skin");
+            return FLR_EINVAL;
+        }
+        P.nb[d] = nb;
+        P.R[d] = R;
+        P.flo[d] = (float)flo;
+        P.fspan[d] = (float)fspan;
+        nbins *= nb;
+    }
+    if (nbins > (1ll << 26)) {
+        set_error("flr_build_neighbors: bin grid too large");
+        return FLR_EINVAL;
+    }
+    P.nbins = nbins;
+    if (nbins + 1 > nl->nbins_cap) {
+        cudaFree(nl->bin_start);
+        cudaFree(nl->bin_fill);
+        nl->bin_start = nullptr;
+        nl->bin_fill = nullptr;
+        long long cap = nbins + 1024;
+        cudaError_t e = cudaMalloc(&nl->bin_start, sizeof(int32_t) * (cap + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&nl->bin_fill, sizeof(int32_t) * (cap + 1));
+        if (e != cudaSuccess) return cuda_fail(e, "allocating bins");
+        nl->nbins_cap = cap;
+    }
+    nl->planned = true;
+    return FLR_OK;
+}
+
+int launch_bbox(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, int n, cudaStream_t st)
+{
+    InvArg inv;
+    for (int c = 0; c < 9; ++c) inv.m[c] = nl->plan.inv[c];
+    k_bbox_init<<<1, 32, 0, st>>>(reinterpret_cast<int *>(nl->bbox));
+    int grid = std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));
+    k_bbox<<<grid, 256, 0, st>>>(pos, n, inv, reinterpret_cast<int *>(nl->bbox));
+    k_bbox_finish<<<1, 32, 0, st>>>(reinterpret_cast<int *>(nl->bbox));
+    count_launch(ctx, 3);
+    return cuda_fail(cudaGetLastError(), "bbox");
+}
+
+int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                   cudaStream_t st, bool wrap_positions, float4 *pos_mut)
+{
+    const Plan &P = nl->plan;
+    const Dims &D = ctx->dims;
+    const long long nbins = P.nbins;
+    const int nbb = (int)((nbins + kScanBlock - 1) / kScanBlock);
+    if (nbb > kScanBlock * 64) {
+        set_error("flr_build_neighbors: too many bins");
+        return FLR_EINVAL;
+    }
+    InvArg inv;
+    for (int c = 0; c < 9; ++c) inv.m[c] = P.inv[c];
+    CellArg cell;
+    for (int c = 0; c < 9; ++c) cell.c[c] = P.cell[c];
+
+    k_zero_bins<<<std::max(1, (int)std::min<long long>((nbins + 255) / 256, 65535)), 256, 0, st>>>(
+        nl->bin_fill, nbins, nl->flags);
+
+    BinArgs b;
+    b.pos = pos;
+    b.pos_mut = wrap_positions ? pos_mut : nullptr;
+    b.n = n;
+    b.inv = inv;
+    b.cell = cell;
+    for (int d = 0; d < 3; ++d) {
+        b.nb[d] = P.nb[d];
+        b.pbc[d] = P.pbc[d];
+        b.flo[d] = P.flo[d];
+        b.fspan[d] = P.fspan[d];
+    }
+    b.atom_bin = nl->atom_bin;
+    b.img = nl->img;
+    b.bin_count = nl->bin_fill;
+    b.pos_ref = nl->pos_ref;
+    b.gtab = nl->gtab;
+    b.flags = nl->flags;
+    b.status = ctx->status;
+    k_bin<<<(n + 255) / 256, 256, 0, st>>>(b);
+
+    // bin_start = exclusive scan of counts; block sums live in blk_group's tail
+    int32_t *bsums = nl->blk_group + (size_t)8 * ((nl->n_cap + kGroupBlock - 1) / kGroupBlock + 1);
+    k_scan_blocks<<<nbb, kScanBlock, 0, st>>>(nl->bin_fill, nl->bin_start, bsums, nbins, nl->flags);
+    k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, nl->bin_start + nbins, nl->flags, ctx->status);
+    k_scan_add<<<nbb, kScanBlock, 0, st>>>(nl->bin_start, nl->bin_fill, bsums, nbins, nl->flags);
+    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(nl->atom_bin, nl->bin_fill, nl->bin_atoms, n, nl->flags);
+    k_sort_bins<<<(int)((nbins + 255) / 256), 256, 0, st>>>(nl->bin_start, nl->bin_atoms, nbins, nl->flags);
+
+    RowArgs r;
+    r.pos = wrap_positions ? pos_mut : pos;
+    r.species = species;
+    r.atom_bin = nl->atom_bin;
+    r.img = nl->img;
+    r.bin_start = nl->bin_start;
+    r.bin_atoms = nl->bin_atoms;
+    r.n = n;
+    r.max_nbr = nl->max_nbr;
+    r.compaction = ctx->p.compaction;
+    for (int d = 0; d < 3; ++d) {
+        r.nb[d] = P.nb[d];
+        r.R[d] = P.R[d];
+        r.pbc[d] = P.pbc[d];
+    }
+    r.cell = cell;
+    const double rc = ctx->p.r_cut + ctx->p.skin;
+    r.rc2 = (float)(rc * rc);
+    r.rc2d = rc * rc;
+    r.entries = nl->entries;
+    r.count = nl->count;
+    r.group = nl->group;
+    r.gtab = nl->gtab;
+    r.flags = nl->flags;
+    r.status = ctx->status;
+    k_build_rows<<<(n + 7) / 8, 256, 0, st>>>(r);
+
+    const int nblk = (n + kGroupBlock - 1) / kGroupBlock;
+    k_group_count<<<nblk, kGroupBlock, 0, st>>>(nl->group, n, nl->blk_group, nl->flags);
+    ScanGroupArgs sg;
+    sg.blk = nl->blk_group;
+    sg.nblk = nblk;
+    sg.n = n;
+    sg.gtab = nl->gtab;
+    for (int g = 0; g < kGroups; ++g) {
+        const int reg = group_region(g);
+        sg.ntile_simt[g] = (2 * D.K[reg] + 143) / 144;
+        sg.nchunk_tc[g] = D.nrows_pad[reg] / 288;
+    }
+    sg.flags = nl->flags;
+    k_group_scan<<<1, kScanBlock, 0, st>>>(sg);
+    k_group_rows<<<nblk, kGroupBlock, 0, st>>>(nl->group, n, nl->blk_group, nl->gtab, nl->row,
+                                               nl->atom_of_row, nl->n_cap, nl->flags);
+    k_rebuild_done<<<1, 1, 0, st>>>(nl->flags);
+    count_launch(ctx, 13);
+    return cuda_fail(cudaGetLastError(), "neighbour rebuild");
+}
+
+}  // namespace flr

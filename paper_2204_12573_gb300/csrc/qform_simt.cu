@@ -1,0 +1,154 @@
+// Quadratic-form products on the FP32 SIMT pipes (the plain path).
+//
+// For every compaction group g the rows of D_g (normalized descriptors of
+// that group's atoms, one per row) are multiplied by the group's stacked
+// model block, P_g = D_g [beta_g | Sigma_g] (Eq. 1 and Eq. 2 evaluated for a
+// tile of atoms at once instead of one matrix-vector product per atom).
+// Both operands are stored K-major: D_g[m][k] and Wt_g[n][k] = W_g[k][n]
+// (beta and Sigma are symmetric).  Persistent CTAs walk a device-side tile
+// table, so the launch needs no host knowledge of the group sizes.
+#include "internal.cuh"
+
+namespace flr {
+namespace {
+
+constexpr int BM = 128, BN = 144, BK = 16;
+constexpr int kThreads = 256;
+
+struct SimtArgs {
+    const float *D32[2];
+    int kp32[2], K[2];
+    const float *W32[kGroups];
+    float *P[2];
+    const GroupTab *gtab;
+};
+
+__global__ void __launch_bounds__(kThreads) k_qform_simt(SimtArgs a)
+{
+    __shared__ __align__(16) float As[2][BK][BM + 4];
+    __shared__ __align__(16) float Bs[2][BK][BN + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const GroupTab &T = *a.gtab;
+    const int total = T.tiles_simt[kGroups];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        int g = 0;
+        while (g < kGroups - 1 && t >= T.tiles_simt[g + 1]) ++g;
+        const int reg = group_region(g);
+        const int K = a.K[reg], kp = a.kp32[reg], N2 = 2 * K;
+        const int ntn = (N2 + BN - 1) / BN;
+        const int local = t - T.tiles_simt[g];
+        const int mt = local / ntn, nt = local % ntn;
+        const int r0 = T.off[g] + mt * BM, rend = T.off[g] + T.count[g];
+        const int c0 = nt * BN;
+        const float *Dg = a.D32[reg];
+        const float *Wg = a.W32[g];
+
+        float acc[8][9];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 9; ++j) acc[i][j] = 0.f;
+
+        // register staging of the next K slice
+        float4 ra[2];
+        float4 rb[3];
+        auto load_slice = [&](int k0) {
+            // A: 128 rows x 16 k -> each thread 2 float4 (row = tid/2, k = (tid&1)*8 + 0/4)
+            const int row = r0 + (tid >> 1);
+            const int kk = k0 + (tid & 1) * 8;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                ra[h] = row < rend ? *reinterpret_cast<const float4 *>(Dg + (size_t)row * kp + kk + 4 * h)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            // B: 144 cols x 16 k = 576 float4 -> each thread up to 3
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                const int idx = tid + h * kThreads;
+                const int col = idx >> 2, kq = idx & 3;
+                const int c = c0 + col;
+                rb[h] = (idx < BN * 4 && c < N2)
+                            ? *reinterpret_cast<const float4 *>(Wg + (size_t)c * kp + k0 + 4 * kq)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        auto store_slice = [&](int buf) {
+            const int row = tid >> 1;
+            const int kk = (tid & 1) * 8;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                As[buf][kk + 4 * h + 0][row] = ra[h].x;
+                As[buf][kk + 4 * h + 1][row] = ra[h].y;
+                As[buf][kk + 4 * h + 2][row] = ra[h].z;
+                As[buf][kk + 4 * h + 3][row] = ra[h].w;
+            }
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                const int idx = tid + h * kThreads;
+                if (idx < BN * 4) {
+                    const int col = idx >> 2, kq = idx & 3;
+                    Bs[buf][4 * kq + 0][col] = rb[h].x;
+                    Bs[buf][4 * kq + 1][col] = rb[h].y;
+                    Bs[buf][4 * kq + 2][col] = rb[h].z;
+                    Bs[buf][4 * kq + 3][col] = rb[h].w;
+                }
+            }
+        };
+
+        const int nks = kp / BK;
+        load_slice(0);
+        store_slice(0);
+        __syncthreads();
+        for (int ks = 0; ks < nks; ++ks) {
+            const int buf = ks & 1;
+            if (ks + 1 < nks) load_slice((ks + 1) * BK);
+#pragma unroll
+            for (int k = 0; k < BK; ++k) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8]);
+                const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8 + 4]);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                float bv[9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) bv[j] = Bs[buf][k][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) acc[i][j] += av[i] * bv[j];
+            }
+            if (ks + 1 < nks) store_slice(buf ^ 1);
+            __syncthreads();
+        }
+        float *Pg = a.P[reg];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int row = r0 + ty * 8 + i;
+            if (row < rend) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    const int c = c0 + tx + 16 * j;
+                    if (c < N2) Pg[(size_t)row * N2 + c] = acc[i][j];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st)
+{
+    SimtArgs a;
+    for (int r = 0; r < 2; ++r) {
+        a.D32[r] = ctx->D32[r];
+        a.kp32[r] = ctx->dims.kp32[r];
+        a.K[r] = ctx->dims.K[r];
+        a.P[r] = ctx->P[r];
+    }
+    for (int g = 0; g < kGroups; ++g) a.W32[g] = ctx->W32[g];
+    a.gtab = nl->gtab;
+    k_qform_simt<<<ctx->num_sms * 2, kThreads, 0, st>>>(a);
+    count_launch(ctx);
+    return cuda_fail(cudaGetLastError(), "FP32 quadratic-form GEMM");
+}
+
+}  // namespace flr

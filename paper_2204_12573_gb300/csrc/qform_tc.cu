@@ -1,0 +1,449 @@
+// Quadratic-form products on the 5th-generation tensor cores (tcgen05).
+//
+// Same contraction as the SIMT path, P_g = D_g [beta_g | Sigma_g] (Eq. 1,
+// Eq. 2), for tiles of 128 atoms x 288 output columns:
+//   * TF32: FP32 operands read as TF32 (kind::tf32), FP32 accumulation;
+//   * 3xBF16: both operands split into BF16 hi + lo parts; the K loop runs
+//     three times (hi.hi, hi.lo, lo.hi), the lo.lo term is dropped, so the
+//     product keeps about 16 significant bits (kind::f16, FP32 accumulate).
+// Operand tiles arrive by TMA (128-byte swizzle) into a 4-stage shared
+// memory ring guarded by mbarriers; one thread issues the MMAs, which
+// accumulate in tensor memory (288 of 512 columns); four epilogue warps read
+// the accumulator back with tcgen05.ld and store P rows.  CTAs are
+// persistent, one per SM, and walk the device-side tile table.
+//
+// Every wait on an mbarrier has a deadline (about 2 s of %globaltimer); on
+// expiry the kernel records FLR_ETIMEOUT in the status word, stops issuing
+// work, waits (again bounded) for its own copies and MMAs in flight, frees
+// its tensor memory and returns.
+#include <cuda.h>
+
+#include "internal.cuh"
+
+namespace flr {
+namespace {
+
+constexpr int BM = 128;
+constexpr int NH = 144;            // N of one MMA
+constexpr int NC = 2 * NH;         // columns per tile (one accumulator)
+constexpr int kStages = 4;
+constexpr int kTileA = BM * 128;   // bytes (128-byte rows)
+constexpr int kTileB = NC * 128;
+constexpr int kStageBytes = kTileA + kTileB;
+constexpr int kTmemCols = 512;
+constexpr int kThreads = 192;
+constexpr unsigned long long kDeadlineNs = 2000000000ull;
+
+struct TcArgs {
+    int K[2];
+    float *P[2];
+    int nkb[2];          // K blocks of 128 bytes per part
+    int nch[kGroups];    // 288-column chunks per group
+    const GroupTab *gtab;
+    int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on timeout or when another role already aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kDeadlineNs) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version
+    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+    return d;
+}
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    if (BF16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+struct TileInfo {
+    int g, reg, row0, rend, chunk;
+};
+__device__ __forceinline__ TileInfo decode_tile(const GroupTab &T, const int *nchunks, int t)
+{
+    TileInfo ti;
+    int g = 0;
+    while (g < kGroups - 1 && t >= T.tiles_tc[g + 1]) ++g;
+    const int local = t - T.tiles_tc[g];
+    const int nch = nchunks[g];
+    ti.g = g;
+    ti.reg = group_region(g);
+    ti.row0 = T.off[g] + (local / nch) * BM;
+    ti.chunk = local % nch;
+    ti.rend = T.off[g] + T.count[g];
+    return ti;
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant__ TcMaps maps, TcArgs a)
+{
+    extern __shared__ uint8_t dyn[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = base;
+    uint8_t *sB = base + kStages * kTileA;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + kStages * kStageBytes);
+    // bars: full[kStages], empty[kStages], tfull, tempty, drain
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 3);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
+    const uint32_t tfull = smem_u32(bars + 2 * kStages), tempty = smem_u32(bars + 2 * kStages + 1);
+    const uint32_t drain = smem_u32(bars + 2 * kStages + 2);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_holder)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 4);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+    const GroupTab &T = *a.gtab;
+    const int total = T.tiles_tc[kGroups];
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int last_phase[kStages];
+            for (int s = 0; s < kStages; ++s) last_phase[s] = -1;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const TileInfo ti = decode_tile(T, a.nch, t);
+                const int nkb = a.nkb[ti.reg];
+                const int nkt = BF16 ? 3 * nkb : nkb;
+                for (int kb = 0; kb < nkt; ++kb) {
+                    const int part = BF16 ? kb / nkb : 0;
+                    const int kk = BF16 ? kb % nkb : kb;
+                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
+                    const uint32_t fb = full0 + 8 * stage;
+                    mbar_expect_tx(fb, kStageBytes);
+                    const int x = kk * (BF16 ? 64 : 32);
+                    const CUtensorMap *am = &maps.a[ti.reg][(BF16 && part == 2) ? 1 : 0];
+                    const CUtensorMap *bm = &maps.b[ti.g][(BF16 && part == 1) ? 1 : 0];
+                    const uint32_t da = smem_u32(sA + stage * kTileA);
+                    const uint32_t db = smem_u32(sB + stage * kTileB);
+                    tma_load_2d(da, am, x, ti.row0, fb);
+                    tma_load_2d(db, bm, x, ti.chunk * NC, fb);
+                    tma_load_2d(db + NH * 128, bm, x, ti.chunk * NC + NH, fb);
+                    last_phase[stage] = (int)phase;
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+            }
+            if (!ok) {
+                atomicOr(a.status, kErrTimeout);
+                *abort_flag = 1;
+                // let the copies already issued land before shared memory is released
+                for (int s = 0; s < kStages; ++s)
+                    if (last_phase[s] >= 0) {
+                        const unsigned long long t0 = globaltimer();
+                        while (!mbar_try(full0 + 8 * s, (uint32_t)last_phase[s]) &&
+                               globaltimer() - t0 < kDeadlineNs) {
+                        }
+                    }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t fmt = BF16 ? 1u : 2u;   // BF16 or TF32 operands
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NH >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool ok = true;
+            bool issued = false;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+                const TileInfo ti = decode_tile(T, a.nch, t);
+                const int nkb = a.nkb[ti.reg];
+                const int nkt = BF16 ? 3 * nkb : nkb;
+                if (!mbar_wait(tempty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
+                fence_after();
+                for (int kb = 0; kb < nkt; ++kb) {
+                    if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    const uint32_t da = smem_u32(sA + stage * kTileA);
+                    const uint32_t db = smem_u32(sB + stage * kTileB);
+                    const uint64_t ad = sw128_desc(da);
+                    const uint64_t bd0 = sw128_desc(db), bd1 = sw128_desc(db + NH * 128);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t accum = (kb | ks) != 0;
+                        mma<BF16>(tmem, ad + 2 * ks, bd0 + 2 * ks, idesc, accum);
+                        mma<BF16>(tmem + NH, ad + 2 * ks, bd1 + 2 * ks, idesc, accum);
+                    }
+                    issued = true;
+                    mma_commit(empty0 + 8 * stage);
+                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                }
+                if (ok) mma_commit(tfull);
+            }
+            if (!ok) {
+                atomicOr(a.status, kErrTimeout);
+                *abort_flag = 1;
+            }
+            if (issued) {
+                // drain: wait until every MMA this thread issued has completed
+                mma_commit(drain);
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try(drain, 0) && globaltimer() - t0 < kDeadlineNs) {
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> registers -> P ----------------
+        const int qw = warp & 3;                // TMEM lane quarter of this warp
+        int it = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+            const TileInfo ti = decode_tile(T, a.nch, t);
+            // lane 0 waits and the warp follows its verdict, so the warp stays converged
+            int okw = 1;
+            if (lane == 0) okw = mbar_wait(tfull, (uint32_t)(it & 1), abort_flag) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (lane == 0) {
+                    atomicOr(a.status, kErrTimeout);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            fence_after();
+            const int N2 = 2 * a.K[ti.reg];
+            const int row = ti.row0 + qw * 32 + lane;
+            float *prow = a.P[ti.reg] + (size_t)row * N2;
+            const int c0 = ti.chunk * NC;
+#pragma unroll 1
+            for (int c = 0; c < NC; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)c, v);
+                if (row < ti.rend) {
+                    const int col = c0 + c;
+                    if (col + 16 <= N2) {
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4)
+                            *reinterpret_cast<float4 *>(prow + col + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (col + k < N2) prow[col + k] = v[k];
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encoder()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+int encode(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int box_rows)
+{
+    EncodeTiledFn fn = get_encoder();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return FLR_ECUDA;
+    }
+    const int esz = bf16 ? 2 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+        return FLR_ECUDA;
+    }
+    return FLR_OK;
+}
+
+int ensure_maps(flr_ctx *ctx)
+{
+    const int prec = ctx->p.precision;
+    if (ctx->maps && ctx->maps_n == ctx->ws_n && ctx->maps_prec == prec) return FLR_OK;
+    if (!ctx->maps) ctx->maps = new TcMaps();
+    const bool bf16 = prec == FLR_PREC_BF16X3;
+    const Dims &D = ctx->dims;
+    for (int r = 0; r < 2; ++r) {
+        if (bf16) {
+            int st = encode(&ctx->maps->a[r][0], ctx->Dhi[r], true, D.kp64[r], ctx->ws_n, BM);
+            if (st == FLR_OK) st = encode(&ctx->maps->a[r][1], ctx->Dlo[r], true, D.kp64[r], ctx->ws_n, BM);
+            if (st != FLR_OK) return st;
+        } else {
+            int st = encode(&ctx->maps->a[r][0], ctx->D32[r], false, D.kp32[r], ctx->ws_n, BM);
+            if (st != FLR_OK) return st;
+            ctx->maps->a[r][1] = ctx->maps->a[r][0];
+        }
+    }
+    for (int g = 0; g < kGroups; ++g) {
+        const int r = group_region(g);
+        if (bf16) {
+            int st = encode(&ctx->maps->b[g][0], ctx->Whi[g], true, D.kp64[r], D.nrows_pad[r], NH);
+            if (st == FLR_OK) st = encode(&ctx->maps->b[g][1], ctx->Wlo[g], true, D.kp64[r], D.nrows_pad[r], NH);
+            if (st != FLR_OK) return st;
+        } else {
+            int st = encode(&ctx->maps->b[g][0], ctx->W32[g], false, D.kp32[r], D.nrows_pad[r], NH);
+            if (st != FLR_OK) return st;
+            ctx->maps->b[g][1] = ctx->maps->b[g][0];
+        }
+    }
+    ctx->maps_n = ctx->ws_n;
+    ctx->maps_prec = prec;
+    return FLR_OK;
+}
+
+}  // namespace
+
+int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st)
+{
+    int s = ensure_maps(ctx);
+    if (s != FLR_OK) return s;
+    const bool bf16 = ctx->p.precision == FLR_PREC_BF16X3;
+    TcArgs a;
+    for (int r = 0; r < 2; ++r) {
+        a.K[r] = ctx->dims.K[r];
+        a.P[r] = ctx->P[r];
+        a.nkb[r] = bf16 ? ctx->dims.kp64[r] / 64 : ctx->dims.kp32[r] / 32;
+    }
+    for (int g = 0; g < kGroups; ++g) a.nch[g] = ctx->dims.nrows_pad[group_region(g)] / NC;
+    a.gtab = nl->gtab;
+    a.status = ctx->status;
+    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 256;
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(k_qform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) k_qform_tc<true><<<ctx->num_sms, kThreads, smem, st>>>(*ctx->maps, a);
+    } else {
+        e = cudaFuncSetAttribute(k_qform_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) k_qform_tc<false><<<ctx->num_sms, kThreads, smem, st>>>(*ctx->maps, a);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM attributes");
+    count_launch(ctx);
+    return cuda_fail(cudaGetLastError(), "tensor-core quadratic-form GEMM");
+}
+
+}  // namespace flr

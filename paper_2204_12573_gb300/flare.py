@@ -1,0 +1,236 @@
+"""Python binding of libflare_gb: the calls of include/flare_gb.h with the
+same names, on torch CUDA tensors.
+
+PyTorch supplies device memory and streams; every step of the force field
+runs in the library's CUDA kernels.  On a machine without the built library
+or without a GPU these calls raise instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclasses.dataclass
+class System:
+    """One structure on the device: pos [n, 4] float32 (x, y, z, unused),
+    species [n] int32, cell (3, 3) rows = lattice vectors, pbc (3,)."""
+    pos: torch.Tensor
+    species: torch.Tensor
+    cell: np.ndarray
+    pbc: tuple = (1, 1, 0)
+
+    @property
+    def n_atoms(self):
+        return int(self.pos.shape[0])
+
+    def c_struct(self):
+        s = N.System()
+        s.n_atoms = self.n_atoms
+        s.pos = _ptr(self.pos)
+        s.species = _ptr(self.species)
+        s.cell = (ctypes.c_double * 9)(*np.asarray(self.cell, np.float64).ravel().tolist())
+        s.pbc = (ctypes.c_int32 * 3)(*[int(bool(p)) for p in self.pbc])
+        return s
+
+    @staticmethod
+    def from_numpy(pos4, species, cell, pbc=(1, 1, 0), device="cuda"):
+        return System(torch.as_tensor(pos4, dtype=torch.float32, device=device).contiguous(),
+                      torch.as_tensor(species, dtype=torch.int32, device=device).contiguous(),
+                      np.asarray(cell, np.float64), tuple(pbc))
+
+
+class FlareGB:
+    """A context: hyperparameters, the mapped model (beta, Sigma per species)
+    and the device workspace."""
+
+    def __init__(self, n_species=2, n_max=8, l_max=3, r_cut=4.5, skin=0.5, max_nbr=64,
+                 precision="bf16x3", compaction=True, device=None):
+        self.lib = N.lib()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        p = N.Params(n_species, n_max, l_max, max_nbr, r_cut, skin, N.PREC[precision], int(bool(compaction)))
+        h = ctypes.c_void_p()
+        N.check(self.lib.flr_create(ctypes.byref(p), self.device, ctypes.byref(h)))
+        self.handle = h
+        self.params = p
+        self.r_cut, self.skin, self.max_nbr = r_cut, skin, max_nbr
+        self.n_species, self.n_max, self.l_max = n_species, n_max, l_max
+        df, ds = ctypes.c_int32(), ctypes.c_int32()
+        N.check(self.lib.flr_descriptor_dims(h, ctypes.byref(df), ctypes.byref(ds)))
+        self.d_full, self.d_single = df.value, ds.value
+        self.precision = precision
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                self.lib.flr_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def set_precision(self, precision: str):
+        N.check(self.lib.flr_set_precision(self.handle, N.PREC[precision]))
+        self.precision = precision
+
+    def set_model(self, beta, sigma):
+        """beta, sigma: [n_species, d_full, d_full] float64 (host)."""
+        beta = np.ascontiguousarray(beta, np.float64)
+        sigma = np.ascontiguousarray(sigma, np.float64)
+        for s in range(self.n_species):
+            N.check(self.lib.flr_set_model(self.handle, s, beta[s].ctypes.data_as(ctypes.c_void_p),
+                                           sigma[s].ctypes.data_as(ctypes.c_void_p)))
+
+    def nbrlist(self, n_atoms):
+        return NbrList(self, n_atoms)
+
+    def launch_count(self):
+        return int(self.lib.flr_launch_count(self.handle))
+
+    def sync(self, stream=None):
+        N.check(self.lib.flr_sync(self.handle, _stream(stream)))
+
+
+class NbrList:
+    def __init__(self, ff: FlareGB, n_atoms: int):
+        self.ff = ff
+        h = ctypes.c_void_p()
+        N.check(ff.lib.flr_nbrlist_create(ff.handle, int(n_atoms), ctypes.byref(h)))
+        self.handle = h
+        self.n_cap = int(n_atoms)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                self.ff.lib.flr_nbrlist_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def view(self, n_atoms):
+        """(entries [n, max_nbr], count [n], group [n]) as int32 torch tensors
+        (copies, made after synchronizing the current stream)."""
+        e, c, g = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        m = ctypes.c_int32()
+        N.check(self.ff.lib.flr_nbrlist_view(self.handle, ctypes.byref(e), ctypes.byref(c), ctypes.byref(g),
+                                             ctypes.byref(m)))
+        torch.cuda.current_stream().synchronize()
+        return tuple(_device_view(ptr.value, shape).clone()
+                     for ptr, shape in ((e, (n_atoms, m.value)), (c, (n_atoms,)), (g, (n_atoms,))))
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ wrapper of library-owned int32 memory."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<i4", "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+def _device_view(ptr, shape):
+    if int(np.prod(shape)) == 0:
+        return torch.empty(shape, dtype=torch.int32, device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, shape), device="cuda")
+
+
+def build_neighbors(ff: FlareGB, system: System, nl: NbrList, stream=None):
+    """Cell-list neighbour search and compaction classification (synchronizes)."""
+    s = system.c_struct()
+    N.check(ff.lib.flr_build_neighbors(ff.handle, ctypes.byref(s), nl.handle, _stream(stream)))
+
+
+def compute_descriptors(ff: FlareGB, system: System, nl: NbrList, stream=None):
+    """Normalized B2 descriptors [n, d_full] (float32) and norms ||B|| [n]."""
+    n = system.n_atoms
+    d = torch.empty((n, ff.d_full), dtype=torch.float32, device="cuda")
+    norm = torch.empty((n,), dtype=torch.float32, device="cuda")
+    s = system.c_struct()
+    N.check(ff.lib.flr_compute_descriptors(ff.handle, ctypes.byref(s), nl.handle, _ptr(d), _ptr(norm),
+                                           _stream(stream)))
+    return d, norm
+
+
+def make_outputs(n, device="cuda"):
+    return dict(energy=torch.empty(n, dtype=torch.float32, device=device),
+                forces=torch.empty((n, 3), dtype=torch.float32, device=device),
+                variance=torch.empty(n, dtype=torch.float32, device=device),
+                sigma=torch.empty(n, dtype=torch.float32, device=device),
+                totals=torch.zeros(N.NTOTALS, dtype=torch.float64, device=device))
+
+
+def _outputs_struct(out):
+    o = N.Outputs()
+    o.energy = _ptr(out["energy"])
+    o.forces = _ptr(out["forces"])
+    o.variance = _ptr(out.get("variance"))
+    o.sigma = _ptr(out.get("sigma"))
+    o.totals = _ptr(out.get("totals"))
+    return o
+
+
+def energy_forces_uncertainty(ff: FlareGB, system: System, nl: NbrList, out=None, stream=None):
+    """Per-atom energy, forces, variance, sigma and FP64 totals (asynchronous)."""
+    if out is None:
+        out = make_outputs(system.n_atoms)
+    s = system.c_struct()
+    o = _outputs_struct(out)
+    N.check(ff.lib.flr_energy_forces_uncertainty(ff.handle, ctypes.byref(s), nl.handle, ctypes.byref(o),
+                                                 _stream(stream)))
+    return out
+
+
+class MDState:
+    """Velocity-Verlet state: pos, vel [n, 4] float32 device tensors updated in place."""
+
+    def __init__(self, system: System, vel: torch.Tensor, masses=(195.084, 1.008), dt=0.0005,
+                 rebuild_every=10):
+        self.system = system
+        self.vel = vel
+        self.c = N.MDState()
+        c = self.c
+        c.n_atoms = system.n_atoms
+        c.pos = _ptr(system.pos)
+        c.vel = _ptr(vel)
+        c.species = _ptr(system.species)
+        c.cell = (ctypes.c_double * 9)(*np.asarray(system.cell, np.float64).ravel().tolist())
+        c.pbc = (ctypes.c_int32 * 3)(*[int(bool(p)) for p in system.pbc])
+        m = list(masses) + [1.0] * (8 - len(masses))
+        c.masses = (ctypes.c_double * 8)(*m)
+        c.dt = dt
+        c.rebuild_every = rebuild_every
+        c.forces_valid = 0
+        c.step = 0
+
+    @property
+    def step(self):
+        return int(self.c.step)
+
+
+def md_step(ff: FlareGB, state: MDState, nl: NbrList, n_steps: int, out, stream=None):
+    """n_steps of velocity Verlet with on-device rebuild decisions (asynchronous)."""
+    o = _outputs_struct(out)
+    N.check(ff.lib.flr_md_step(ff.handle, ctypes.byref(state.c), nl.handle, int(n_steps), ctypes.byref(o),
+                               _stream(stream)))
+    return out
+
+
+def sync(ff: FlareGB, stream=None):
+    ff.sync(stream)

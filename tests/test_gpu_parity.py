@@ -1,0 +1,190 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the plain FP32 path must give bit-exact neighbour sets, per-atom
+energy error <= 1e-5 * max(|E_i|, ||beta_s||_2), force error <= 1e-4 eV/A
+and variance relative error <= 1e-4; the TF32 and 3xBF16 tensor-core paths
+must give forces within 1e-3 eV/A.
+"""
+import numpy as np
+import pytest
+
+from paper_2204_12573_gb300 import synth
+
+from gpu_common import (F_TOL_MIXED, compare_efv, decode_entries, gpu_run, oracle_run)
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+BETA, SIGMA = synth.random_model()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_12573_gb300 import build
+    build.build()
+
+
+def _tiny():
+    return synth.tiny_system(0)
+
+
+def _slabs(k=3):
+    return synth.slab_batch(seed=3, n_slabs=k)
+
+
+# ------------------------------------------------------------ neighbours
+
+@pytest.mark.parametrize("which", ["tiny", "slab0", "slab1", "slab2"])
+def test_neighbor_sets_bit_exact(which):
+    s = _tiny() if which == "tiny" else _slabs()[int(which[-1])]
+    g, *_ = gpu_run(s, BETA, SIGMA, max_nbr=96)
+    pos = synth.f32_exact_f64(synth.as_f32_positions(s.pos))
+    ref = O.neighbors(pos, s.cell, s.pbc, 5.0, method="brute" if s.n_atoms < 100 else "cells")
+    got = decode_entries(g["entries"], g["count"])
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref.astype(np.int64))
+
+
+def test_rows_are_deterministic():
+    s = _slabs()[0]
+    g1, *_ = gpu_run(s, BETA, SIGMA)
+    g2, *_ = gpu_run(s, BETA, SIGMA)
+    assert np.array_equal(g1["entries"].cpu().numpy(), g2["entries"].cpu().numpy())
+
+
+# ------------------------------------------------------------ descriptors
+
+def test_descriptors_match_oracle():
+    s = _tiny()
+    g, *_ = gpu_run(s, BETA, SIGMA, want_desc=True)
+    o = oracle_run(s, BETA, SIGMA)
+    assert np.abs(g["norm"] - o["norm"]).max() <= 1e-5 * o["norm"].max()
+    assert np.abs(g["dhat"] - o["dhat"]).max() <= 2e-6
+
+
+def test_descriptors_compaction_zero_blocks():
+    s = _slabs()[1]
+    g, *_ = gpu_run(s, BETA, SIGMA, want_desc=True)
+    o = oracle_run(s, BETA, SIGMA)
+    assert np.abs(g["dhat"] - o["dhat"]).max() <= 2e-6
+
+
+# ------------------------------------------------------------ energy / forces / variance
+
+def test_fp32_tiny_matches_oracle():
+    s = _tiny()
+    g, *_ = gpu_run(s, BETA, SIGMA, precision="fp32")
+    o = oracle_run(s, BETA, SIGMA)
+    compare_efv(g, o)
+    assert abs(g["totals"][0] - o["E_tot"]) <= 1e-5 * max(1.0, abs(o["E_tot"]))
+    W = g["totals"][1:10].reshape(3, 3)
+    assert np.abs(W - o["W"]).max() <= 1e-4 * max(1.0, np.abs(o["W"]).max())
+    assert abs(g["totals"][10] - np.sqrt(o["V"]).max()) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_fp32_slabs_match_oracle(k):
+    s = _slabs()[k]
+    g, *_ = gpu_run(s, BETA, SIGMA, precision="fp32")
+    o = oracle_run(s, BETA, SIGMA)
+    compare_efv(g, o)
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
+def test_mixed_precision_forces(precision):
+    for s in [_tiny()] + _slabs(2):
+        g, *_ = gpu_run(s, BETA, SIGMA, precision=precision)
+        o = oracle_run(s, BETA, SIGMA)
+        dF = np.abs(g["forces"] - o["F"]).max()
+        assert dF <= F_TOL_MIXED, (precision, dF)
+        assert np.abs(g["energy"] - o["E"]).max() <= 1e-2
+
+
+def test_compaction_on_off_agree():
+    s = _slabs()[2]
+    a, *_ = gpu_run(s, BETA, SIGMA, compaction=True)
+    b, *_ = gpu_run(s, BETA, SIGMA, compaction=False)
+    assert np.abs(a["energy"] - b["energy"]).max() <= 2e-6
+    assert np.abs(a["forces"] - b["forces"]).max() <= 2e-5
+    assert (b["group"].cpu().numpy() % 3 == 0).all()
+
+
+def test_forces_bitwise_reproducible():
+    s = _slabs()[0]
+    a, *_ = gpu_run(s, BETA, SIGMA, precision="bf16x3")
+    b, *_ = gpu_run(s, BETA, SIGMA, precision="bf16x3")
+    assert np.array_equal(a["forces"], b["forces"])
+    assert np.array_equal(a["energy"], b["energy"])
+
+
+def test_net_force_zero():
+    s = _slabs()[1]
+    g, *_ = gpu_run(s, BETA, SIGMA)
+    assert np.abs(g["forces"].astype(np.float64).sum(0)).max() <= 1e-4
+
+
+def test_paper_dimensions_n7():
+    """n_max = 7 reproduces the paper's 420 / 112 descriptor sizes on the GPU path."""
+    s = _tiny()
+    b7, s7 = synth.random_model(n_max=7)
+    g, ff, *_ = gpu_run(s, b7, s7, n_max=7)
+    assert (ff.d_full, ff.d_single) == (420, 112)
+    o = oracle_run(s, b7, s7, n_max=7)
+    compare_efv(g, o)
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_isolated_and_empty():
+    import torch
+    from paper_2204_12573_gb300 import flare as F
+    ff = F.FlareGB(precision="fp32")
+    ff.set_model(BETA, SIGMA)
+    pos = np.array([[0, 0, 0, 0], [0, 0, 10, 0], [0, 1.5, 10, 0]], np.float32)
+    sp = np.array([0, 0, 1], np.int32)
+    sysg = F.System.from_numpy(pos, sp, np.diag([30.0, 30.0, 30.0]), (0, 0, 0))
+    nl = ff.nbrlist(3)
+    F.build_neighbors(ff, sysg, nl)
+    out = F.energy_forces_uncertainty(ff, sysg, nl)
+    ff.sync()
+    o = O.energy_forces(O.Hyper(), pos[:, :3].astype(np.float64), sp, np.diag([30.0] * 3), (0, 0, 0), BETA, SIGMA)
+    assert out["energy"][0].item() == 0.0 and out["variance"][0].item() == 0.0
+    assert out["totals"][11].item() == 1.0
+    assert np.abs(out["forces"].cpu().numpy() - o["F"]).max() <= 1e-4
+    # an empty system is accepted and leaves zero totals
+    sys0 = F.System.from_numpy(np.zeros((0, 4), np.float32), np.zeros(0, np.int32), np.eye(3) * 10, (0, 0, 0))
+    nl0 = ff.nbrlist(0)
+    F.build_neighbors(ff, sys0, nl0)
+    out0 = F.energy_forces_uncertainty(ff, sys0, nl0)
+    ff.sync()
+    assert out0["totals"].abs().sum().item() == 0.0
+    torch.cuda.synchronize()
+
+
+def test_overflow_is_reported():
+    from paper_2204_12573_gb300 import flare as F
+    from paper_2204_12573_gb300 import _native as N
+    s = _slabs()[0]
+    ff = F.FlareGB(max_nbr=32, precision="fp32")
+    ff.set_model(BETA, SIGMA)
+    sysg = F.System.from_numpy(synth.as_f32_positions(s.pos), s.species, s.cell, s.pbc)
+    nl = ff.nbrlist(s.n_atoms)
+    with pytest.raises(N.FlareError) as e:
+        F.build_neighbors(ff, sysg, nl)
+    assert e.value.code == N.FLR_ENBR_OVERFLOW
+
+
+def test_model_required():
+    from paper_2204_12573_gb300 import flare as F
+    from paper_2204_12573_gb300 import _native as N
+    s = _tiny()
+    ff = F.FlareGB()
+    sysg = F.System.from_numpy(synth.as_f32_positions(s.pos), s.species, s.cell, s.pbc)
+    nl = ff.nbrlist(s.n_atoms)
+    F.build_neighbors(ff, sysg, nl)
+    with pytest.raises(N.FlareError) as e:
+        F.energy_forces_uncertainty(ff, sysg, nl)
+    assert e.value.code == N.FLR_ENOMODEL
