@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Benchmark: velocity-Verlet MD with the FLARE force field on one GB300.
+
+Workload: a 2,129,920-atom H2/Pt(111) slab (256 x 256 atoms per layer x 32
+layers of Pt plus 16,384 H2 molecules in the gas above), 300 K Maxwell
+velocities, dt = 0.5 fs, neighbour list rebuilt every 10 steps (skin 0.5 A,
+plus a device-side displacement trigger).  One step = half kick + drift +
+(conditional) rebuild + energy / forces / uncertainty + half kick.
+
+Headline `value`: M atom-steps/s with the quadratic forms on the tensor
+cores in 3xBF16 (FP32 accumulate); `plain_fp32` gives the same run with the
+FP32 SIMT quadratic forms, and `force_err_ev_per_A` the force error of each
+against the FP64 oracle on sampled atoms.  Inputs are larger than L2 (the
+neighbour list alone is 545 MB), so no L2 flush is needed between steps.
+
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same
+workload instead (the reference arm).  Under torchrun every rank runs an
+independent replica (the path has no data exchange on one GPU per replica).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("M atom-steps/s (E+F+σ) mixed vs plain FP32 at ≤1e-3 eV/Å force err; p50/p99 ms")
+UNIT = "M atom-steps/s"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_atom(kernel):
+    """DRAM bytes per atom of `kernel` from the committed ncu summary, if it was
+    taken on the current source of that kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("#") or "=" not in line:
+            continue
+        kv = dict(x.split("=", 1) for x in line.split())
+        if kv.get("kernel") == kernel:
+            srcs = kv.get("sources", "").split(",")
+            try:
+                if _source_hash(srcs) != kv.get("hash"):
+                    return None
+            except OSError:
+                return None
+            return float(kv["bytes_per_atom"])
+    return None
+
+
+# algorithmic work per atom ("Kernels and their rooflines")
+def _algorithmic(kernel, groups, n_atoms, d_full, d_single, pairs_per_atom):
+    """(amount, unit, bound) for one launch of `kernel`."""
+    g = np.bincount(groups + 1, minlength=7)[1:]   # counts of the 6 compaction groups
+    n_full = int(g[0] + g[3])
+    n_single = int(g[1] + g[2] + g[4] + g[5])
+    if kernel == "qform":
+        flops = 2.0 * (n_full * d_full * 2 * d_full + n_single * d_single * 2 * d_single)
+        return flops, "TFLOP/s", "tensor"
+    if kernel == "force":
+        # per pair: 2 N 16 (c, c') FMA + ~130 flops gradients/radial; per atom w = G~A
+        per_pair = 2 * (2 * 8 * 16) + 130
+        per_atom_w = 2 * (16 * 8 * 16)
+        flops = n_atoms * pairs_per_atom * per_pair + n_full * 2 * per_atom_w + n_single * per_atom_w
+        return float(flops), "TFLOP/s", "alu"
+    if kernel == "descriptor":
+        per_pair = 2 * 8 * 16 * 2 + 60
+        flops = n_atoms * pairs_per_atom * per_pair + 2 * (n_full * d_full * 2.5 + n_single * d_single * 2.5)
+        return float(flops), "TFLOP/s", "alu"
+    return None, None, None
+
+
+def _pairs_within_cutoff(nl, sysg, n, r_cut):
+    """Number of list entries with |r_ij| < r_cut (the pairs the descriptor
+    and force kernels evaluate), counted with torch from the list view."""
+    import torch
+    entries, count, _ = nl.view(n)
+    pos = sysg.pos[:, :3]
+    cell = torch.as_tensor(np.asarray(sysg.cell), dtype=torch.float64, device="cuda")
+    total = 0
+    for a in range(0, n, 1 << 18):
+        b = min(n, a + (1 << 18))
+        e = entries[a:b].long()
+        valid = torch.arange(e.shape[1], device="cuda")[None, :] < count[a:b, None]
+        j = e >> 7
+        code = e & 127
+        s = torch.stack([code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2], -1).double()
+        r = (pos[j.clamp(0, n - 1)].double() + s @ cell - pos[a:b, None, :].double())
+        d2 = (r * r).sum(-1)
+        total += int(((d2 < r_cut * r_cut) & valid).sum().item())
+    return total
+
+
+def _fp32_peak_tflops(peaks):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
+    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+class OracleSample:
+    """The FP64 oracle (cell-list neighbours + E/F/sigma) timed on a compact
+    column of the slab, sized from a pilot run to take about target_s."""
+
+    def __init__(self, struct, beta, sigma):
+        import oracle as O
+        from paper_2204_12573_gb300 import synth
+        self.O = O
+        self.struct, self.beta, self.sigma = struct, beta, sigma
+        self.pos = synth.f32_exact_f64(synth.as_f32_positions(struct.pos))
+        self.h = O.Hyper()
+        pilot = self._block(10.0)
+        t0 = time.time()
+        self._run(pilot)
+        self.rate = len(pilot) / max(time.time() - t0, 1e-3)
+
+    def _block(self, side):
+        return np.nonzero((self.pos[:, 0] < side) & (self.pos[:, 1] < side))[0]
+
+    def _run(self, atoms):
+        s = self.struct
+        self.O.forces_subset(self.h, self.pos, s.species, s.cell, s.pbc, self.beta, self.sigma, atoms, skin=0.5)
+
+    def step(self, target_s):
+        pilot_n = len(self._block(10.0))
+        side = float(np.clip(10.0 * np.sqrt(self.rate * target_s / max(pilot_n, 1)), 10.0, 300.0))
+        blk = self._block(side)
+        t0 = time.time()
+        self._run(blk)
+        dt = time.time() - t0
+        return {"value": len(blk) / dt / 1e6, "unit": UNIT, "cores": self.O.max_threads(), "kind": "oracle",
+                "seconds": round(dt, 2),
+                "sample": f"{len(blk)} atoms (x,y < {side:.1f} A column of the slab, Pt and H): cell-list "
+                          f"neighbours over all atoms + FP64 E/F/sigma of the column, one step"}
+
+
+def cpu_baseline_sample(struct, beta, sigma, target_s=12.0):
+    return OracleSample(struct, beta, sigma).step(target_s)
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    from paper_2204_12573_gb300 import synth
+    struct = synth.big_slab(seed=1)
+    beta, sigma = synth.random_model()
+    samp = OracleSample(struct, beta, sigma)          # pilot run doubles as warm-up
+    per_step = float(np.clip(150.0 / max(args.steps + args.warmup, 1), 1.0, args.ref_seconds))
+    for _ in range(args.warmup):
+        samp.step(0.25 * per_step)
+    vals = []
+    cb = None
+    for k in range(max(args.steps, 1)):
+        cb = samp.step(per_step)
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    cb["sample"] += f"; median of {len(vals)} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(struct.n_atoms, "f64 oracle"), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(n_atoms, precision):
+    return {"workload": f"H2/Pt(111) slab 256x256 atoms/layer x 32 layers + 16384 H2 = {n_atoms} atoms; "
+                        "velocity Verlet dt=0.5 fs, 300 K, rebuild every 10 steps, skin 0.5 A, r_cut 4.5 A, "
+                        "n_max 8, l_max 3 (d=544/144)",
+            "n_atoms": n_atoms, "precision": precision, "l2": "inputs larger than L2 (no flush)",
+            "parallelism": "replicas"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2204_12573_gb300 import build
+    build.build()
+    import oracle as O
+    from paper_2204_12573_gb300 import flare as F
+    from paper_2204_12573_gb300 import synth
+
+    if args.small:
+        struct = synth.big_slab(seed=1, nx=64, n_rows=64, n_layers=32, n_h2=1024)
+    else:
+        struct = synth.big_slab(seed=1)
+    n = struct.n_atoms
+    beta, sigma = synth.random_model()
+    pos0 = synth.as_f32_positions(struct.pos)
+    vel0 = synth.maxwell_velocities(struct.species, 300.0, seed=1)
+    ff = F.FlareGB(precision="bf16x3", max_nbr=64)
+    ff.set_model(beta, sigma)
+    sysg = F.System.from_numpy(pos0, struct.species, struct.cell, struct.pbc)
+    vel = torch.as_tensor(vel0, device="cuda")
+    nl = ff.nbrlist(n)
+    out = F.make_outputs(n)
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        sysg.pos.copy_(torch.as_tensor(pos0, device="cuda"))
+        vel.copy_(torch.as_tensor(vel0, device="cuda"))
+        F.build_neighbors(ff, sysg, nl)
+        return F.MDState(sysg, vel)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(precision, profile=False, clocks=None):
+        ff.set_precision(precision)
+        st = reset()
+        F.md_step(ff, st, nl, args.warmup, out)
+        ff.sync()
+        if profile:
+            ff.profile(True)
+        l0 = ff.launch_count()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.__enter__()
+        e0.record(stream)
+        F.md_step(ff, st, nl, args.steps, out)
+        e1.record(stream)
+        barrier()
+        if clocks:
+            clocks.__exit__()
+        ms = e0.elapsed_time(e1)
+        launches = ff.launch_count() - l0
+        prof = None
+        if profile:
+            prof = ff.profile_read()
+            ff.profile(False)
+        ff.sync()
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, prof, st
+
+    if args.profile_run:
+        # the mixed-precision timed region only (for launch lists and ncu captures)
+        ms, launches, _, _ = timed(args.precision)
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "n_atoms": n, "precision": args.precision,
+                              "ms_per_step": ms / args.steps, "launches": launches}), flush=True)
+        return
+    clocks = Clocks(torch.cuda.current_device())
+    ms_mix, launches, _, st_mix = timed("bf16x3", clocks=clocks)
+    clk = clocks.summary()
+    _, _, prof_mix, _ = timed("bf16x3", profile=True)
+    ms_fp32, _, prof_fp32, _ = timed("fp32", profile=False)
+
+    value = world * n * args.steps / (ms_mix / 1e3) / 1e6
+    value_fp32 = world * n * args.steps / (ms_fp32 / 1e3) / 1e6
+
+    # force error of each precision against the FP64 oracle on sampled atoms (same positions)
+    ff.set_precision("bf16x3")
+    F.build_neighbors(ff, sysg, nl)
+    _, _, groups = nl.view(n)
+    groups = groups.cpu().numpy()
+    rng = np.random.default_rng(2)
+    mixed = np.nonzero(groups % 3 == 0)[0]
+    rest = np.nonzero(groups % 3 != 0)[0]
+    sample = np.concatenate([rng.choice(mixed, min(16, len(mixed)), replace=False),
+                             rng.choice(rest, 48, replace=False)])
+    pos_now = sysg.pos.detach().cpu().numpy()
+    o = O.forces_subset(O.Hyper(), pos_now[:, :3].astype(np.float64), struct.species, struct.cell,
+                        struct.pbc, beta, sigma, sample, skin=0.5)
+    ferr = {}
+    for prec in ("bf16x3", "tf32", "fp32"):
+        ff.set_precision(prec)
+        r = F.energy_forces_uncertainty(ff, sysg, nl, F.make_outputs(n))
+        ff.sync()
+        ferr[prec] = float(np.abs(r["forces"].cpu().numpy()[sample] - o["F"]).max())
+    ff.set_precision("bf16x3")
+
+    # roofline of the dominant kernel (mixed run)
+    peaks, peak_kind = _peaks()
+    per_step = {k: v[0] / max(args.steps, 1) for k, v in prof_mix.items()}
+    dom = max(("descriptor", "qform", "force"), key=lambda k: prof_mix[k][0])
+    cnt = out["energy"].numel()
+    pairs_per_atom = _pairs_within_cutoff(nl, sysg, n, ff.r_cut) / n
+    amount, unit, bound = _algorithmic(dom, groups, n, ff.d_full, ff.d_single, pairs_per_atom)
+    avg_ms = prof_mix[dom][0] / max(prof_mix[dom][1], 1)
+    achieved = amount / (avg_ms / 1e3) / 1e12
+    if bound == "tensor":
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak_note = f"bf16 dense, sustained, {peak_kind}"
+    else:
+        peak = _fp32_peak_tflops(peaks)
+        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock (derived)"
+    tpa = _traffic_per_atom(dom)
+    roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1),
+                "unit": unit, "frac": round(achieved / peak, 4), "peak_source": peak_note,
+                "traffic": None if tpa is None else tpa * cnt, "avg_launch_ms": round(avg_ms, 4),
+                "algorithmic_per_launch": amount}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ff.set_precision("bf16x3")
+        st = reset()
+        hpos = torch.empty_like(sysg.pos, device="cpu").pin_memory()
+        hvel = torch.empty_like(vel, device="cpu").pin_memory()
+        hpos.copy_(sysg.pos)
+        hvel.copy_(vel)
+        hout = {k: torch.empty_like(out[k], device="cpu").pin_memory() for k in ("energy", "forces", "sigma")}
+        F.md_step(ff, st, nl, 1, out)
+        ff.sync()
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sysg.pos.copy_(hpos, non_blocking=True)
+            vel.copy_(hvel, non_blocking=True)
+            F.md_step(ff, st, nl, 1, out)
+            for k in hout:
+                hout[k].copy_(out[k], non_blocking=True)
+            hpos.copy_(sysg.pos, non_blocking=True)
+            hvel.copy_(vel, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        ms_e2e = max(e0.elapsed_time(e1), wall * 1e3)
+        bi = 2 * n * 16
+        bo = 2 * n * 16 + sum(hout[k].numel() * 4 for k in hout)
+        e2e = {"value": world * n * args.steps / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "note": "per step: H2D pos+vel (pinned), md_step, D2H energy, forces, sigma, pos, vel"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(struct, beta, sigma, target_s=args.ref_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_mix / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
+                "config": _config(n, "3xBF16 tcgen05 quadratic forms, FP32 elsewhere, FP64 totals"),
+                "plain_fp32": {"value": round(value_fp32, 3), "ms_per_step": round(ms_fp32 / args.steps, 4)},
+                "force_err_ev_per_A": ferr,
+                "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
+                "kernels_ms_per_step_fp32": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_fp32.items()}
+                if prof_fp32 else None,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="time only the MD steps at --precision (for ncu launch lists)")
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--small", action="store_true",
+                    help="64x64x32 slab + 1024 H2 (132k atoms) instead of the 2.1M-atom slab")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

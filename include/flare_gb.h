@@ -201,6 +201,24 @@ int flr_sync(flr_ctx *ctx, flr_stream_t stream);
 /* Number of kernels the library launched on this context so far. */
 int64_t flr_launch_count(const flr_ctx *ctx);
 
+/* Kernel classes of flr_profile_read. */
+#define FLR_KERNEL_DESCRIPTOR 0   /* A, B2, normalization (one launch per evaluation) */
+#define FLR_KERNEL_QFORM 1        /* quadratic-form GEMM (SIMT or tcgen05) */
+#define FLR_KERNEL_FORCE 2        /* E, V, sigma, reordered back-propagation, per-pair forces */
+#define FLR_KERNEL_FINALIZE 3     /* fixed point -> forces, half kick, FP64 totals */
+#define FLR_KERNEL_DRIFT 4        /* MD half kick + drift + displacement check */
+#define FLR_KERNEL_REBUILD 5      /* the (conditional) neighbour rebuild sequence */
+#define FLR_KERNEL_CLASSES 6
+
+/* Per-kernel device timing: when on, every launch of the classes above is
+ * bracketed by CUDA events recorded on its own stream (off by default;
+ * turning it on clears the accumulated totals). */
+int flr_profile_enable(flr_ctx *ctx, int32_t on);
+
+/* Accumulated device time (ms) and launch count of one kernel class since
+ * profiling was enabled.  Waits for the recorded events. */
+int flr_profile_read(flr_ctx *ctx, int32_t kernel_class, double *total_ms, int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,10 @@ EXPORTED = [
     "flr_set_precision", "flr_set_model", "flr_nbrlist_create", "flr_nbrlist_destroy",
     "flr_nbrlist_view", "flr_build_neighbors", "flr_compute_descriptors",
     "flr_energy_forces_uncertainty", "flr_md_step", "flr_sync", "flr_launch_count",
+    "flr_profile_enable", "flr_profile_read",
 ]
+
+KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
 
 
 class Params(ctypes.Structure):
@@ -98,6 +101,9 @@ def lib():
             "flr_md_step": (ctypes.c_int, [P, ctypes.POINTER(MDState), P, ctypes.c_int32, ctypes.POINTER(Outputs), P]),
             "flr_sync": (ctypes.c_int, [P, P]),
             "flr_launch_count": (ctypes.c_int64, [P]),
+            "flr_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
+            "flr_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_int64)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -21,6 +21,68 @@ int cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? FLR_ENOMEM : FLR_ECUDA;
 }
 
+static cudaEvent_t prof_event(ProfState *p)
+{
+    if (p->n_pool > 0) return p->pool[--p->n_pool];
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(flr_ctx *ctx, int cls, cudaStream_t st)
+{
+    ProfState *p = ctx->prof;
+    if (!p || !p->on) return;
+    if (p->n_recs == p->cap) {
+        int cap = p->cap ? 2 * p->cap : 1024;
+        ProfState::Rec *r = new ProfState::Rec[cap];
+        for (int k = 0; k < p->n_recs; ++k) r[k] = p->recs[k];
+        delete[] p->recs;
+        p->recs = r;
+        p->cap = cap;
+    }
+    ProfState::Rec &r = p->recs[p->n_recs];
+    r.a = prof_event(p);
+    r.b = nullptr;
+    r.cls = cls;
+    cudaEventRecord(r.a, st);
+}
+
+void prof_end(flr_ctx *ctx, int cls, cudaStream_t st)
+{
+    ProfState *p = ctx->prof;
+    if (!p || !p->on) return;
+    ProfState::Rec &r = p->recs[p->n_recs];
+    if (r.cls != cls) return;
+    r.b = prof_event(p);
+    cudaEventRecord(r.b, st);
+    ++p->n_recs;
+}
+
+static void prof_drain(ProfState *p)
+{
+    for (int k = 0; k < p->n_recs; ++k) {
+        ProfState::Rec &r = p->recs[k];
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        p->ms[r.cls] += ms;
+        p->count[r.cls] += 1;
+        for (cudaEvent_t e : {r.a, r.b}) {
+            if (p->n_pool == p->pool_cap) {
+                int cap = p->pool_cap ? 2 * p->pool_cap : 2048;
+                cudaEvent_t *q = new cudaEvent_t[cap];
+                for (int i = 0; i < p->n_pool; ++i) q[i] = p->pool[i];
+                delete[] p->pool;
+                p->pool = q;
+                p->pool_cap = cap;
+            }
+            p->pool[p->n_pool++] = e;
+        }
+    }
+    p->n_recs = 0;
+}
+
 int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc, const float *bb, double margin);
 int launch_set_rebuild(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
 int launch_clear_rebuild_counter(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
@@ -174,13 +236,22 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
     if (n == 0) return FLR_OK;
     cudaError_t e = cudaMemsetAsync(ctx->Facc, 0, sizeof(long long) * 3 * (size_t)n, st);
     if (e != cudaSuccess) return cuda_fail(e, "clear force accumulators");
+    prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
     int s = launch_desc(ctx, nl, pos, species, n, st);
+    prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
     if (s != FLR_OK) return s;
+    prof_begin(ctx, FLR_KERNEL_QFORM, st);
     s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, st) : launch_qform_tc(ctx, nl, st);
+    prof_end(ctx, FLR_KERNEL_QFORM, st);
     if (s != FLR_OK) return s;
+    prof_begin(ctx, FLR_KERNEL_FORCE, st);
     s = launch_force(ctx, nl, pos, species, n, out, st);
+    prof_end(ctx, FLR_KERNEL_FORCE, st);
     if (s != FLR_OK) return s;
-    return launch_finalize(ctx, nl, n, out, kick, st);
+    prof_begin(ctx, FLR_KERNEL_FINALIZE, st);
+    s = launch_finalize(ctx, nl, n, out, kick, st);
+    prof_end(ctx, FLR_KERNEL_FINALIZE, st);
+    return s;
 }
 
 }  // namespace
@@ -280,6 +351,13 @@ int flr_destroy(flr_ctx *c)
     cudaFree(c->tab_single);
     cudaFree(c->status);
     delete c->maps;
+    if (c->prof) {
+        prof_drain(c->prof);
+        for (int k = 0; k < c->prof->n_pool; ++k) cudaEventDestroy(c->prof->pool[k]);
+        delete[] c->prof->pool;
+        delete[] c->prof->recs;
+        delete c->prof;
+    }
     delete c;
     return FLR_OK;
 }
@@ -600,9 +678,13 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
     }
     kick.enabled = 1;
     for (int k = 0; k < n_steps; ++k) {
+        prof_begin(c, FLR_KERNEL_DRIFT, st);
         s = launch_md_drift(c, nl, pos, kick.vel, out->forces, md->species, n, kick, (float)md->dt, disp2, st);
+        prof_end(c, FLR_KERNEL_DRIFT, st);
         if (s == FLR_OK && (md->step + 1) % md->rebuild_every == 0) s = launch_set_rebuild(c, nl, st);
+        prof_begin(c, FLR_KERNEL_REBUILD, st);
         if (s == FLR_OK) s = launch_rebuild(c, nl, pos, md->species, n, st, true, pos);
+        prof_end(c, FLR_KERNEL_REBUILD, st);
         if (s == FLR_OK) s = evaluate(c, nl, pos, md->species, n, out, kick, st);
         if (s != FLR_OK) return s;
         md->step += 1;
@@ -628,5 +710,43 @@ int flr_sync(flr_ctx *c, flr_stream_t stream)
 }
 
 int64_t flr_launch_count(const flr_ctx *c) { return c ? c->launches : 0; }
+
+int flr_profile_enable(flr_ctx *c, int32_t on)
+{
+    if (!c) return FLR_EINVAL;
+    cudaSetDevice(c->device);
+    if (!c->prof) {
+        c->prof = new ProfState();
+        std::memset(static_cast<void *>(c->prof), 0, sizeof(ProfState));
+    }
+    ProfState *p = c->prof;
+    prof_drain(p);
+    if (on) {
+        for (int k = 0; k < FLR_KERNEL_CLASSES; ++k) {
+            p->ms[k] = 0.0;
+            p->count[k] = 0;
+        }
+    }
+    p->on = on != 0;
+    return FLR_OK;
+}
+
+int flr_profile_read(flr_ctx *c, int32_t cls, double *total_ms, int64_t *launches)
+{
+    if (!c || cls < 0 || cls >= FLR_KERNEL_CLASSES) {
+        set_error("flr_profile_read: invalid argument");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    if (!c->prof) {
+        if (total_ms) *total_ms = 0.0;
+        if (launches) *launches = 0;
+        return FLR_OK;
+    }
+    prof_drain(c->prof);
+    if (total_ms) *total_ms = c->prof->ms[cls];
+    if (launches) *launches = c->prof->count[cls];
+    return FLR_OK;
+}
 
 }  // extern "C"

@@ -132,7 +132,29 @@ struct flr_ctx {
     TcMaps *maps;              // host copy of the current tensor maps
     int maps_n;                // workspace size the maps were encoded for
     int maps_prec;
+    // per-kernel event timing (flr_profile_*)
+    struct ProfState *prof;
 };
+
+struct ProfState {
+    struct Rec {
+        cudaEvent_t a, b;
+        int cls;
+    };
+    bool on;
+    Rec *recs;
+    int n_recs, cap;
+    cudaEvent_t *pool;
+    int n_pool, pool_cap;
+    double ms[FLR_KERNEL_CLASSES];
+    long long count[FLR_KERNEL_CLASSES];
+};
+
+namespace flr {
+// Bracket a launch with events when profiling is on (no-ops otherwise).
+void prof_begin(flr_ctx *ctx, int cls, cudaStream_t st);
+void prof_end(flr_ctx *ctx, int cls, cudaStream_t st);
+}  // namespace flr
 
 namespace flr {
 

@@ -107,6 +107,19 @@ class FlareGB:
     def sync(self, stream=None):
         N.check(self.lib.flr_sync(self.handle, _stream(stream)))
 
+    def profile(self, on: bool):
+        """Per-kernel CUDA-event timing on the launching stream (clears totals when turned on)."""
+        N.check(self.lib.flr_profile_enable(self.handle, int(bool(on))))
+
+    def profile_read(self):
+        """{kernel class: (total ms, launches)} accumulated since profiling was enabled."""
+        out = {}
+        for k, name in enumerate(N.KERNEL_CLASSES):
+            ms, cnt = ctypes.c_double(), ctypes.c_int64()
+            N.check(self.lib.flr_profile_read(self.handle, k, ctypes.byref(ms), ctypes.byref(cnt)))
+            out[name] = (ms.value, cnt.value)
+        return out
+
 
 class NbrList:
     def __init__(self, ff: FlareGB, n_atoms: int):
