@@ -160,8 +160,7 @@ int ensure_workspace(flr_ctx *ctx, int n)
         if (s == FLR_OK) s = dev_alloc(&ctx->P[r], N * 2 * D.K[r], "workspace P");
     }
     if (s == FLR_OK) s = dev_alloc(&ctx->Facc, N * 3, "workspace forces");
-    const size_t nvir = (N + kWarpsDesc - 1) / kWarpsDesc, nfin = (N + 255) / 256;
-    if (s == FLR_OK) s = dev_alloc(&ctx->partials, nvir * 9 + nfin * 4 + 16, "workspace partials");
+    if (s == FLR_OK) s = dev_alloc(&ctx->partials, (size_t)kMaxPartials * 13 + 16, "workspace partials");
     if (s != FLR_OK) {
         free_workspace(ctx);
         return s;
@@ -602,7 +601,7 @@ int flr_compute_descriptors(flr_ctx *c, const flr_system *sys, const flr_nbrlist
 int flr_energy_forces_uncertainty(flr_ctx *c, const flr_system *sys, const flr_nbrlist *nl, flr_outputs *out,
                                   flr_stream_t stream)
 {
-    if (!c || !out || !out->forces || !out->energy) {
+    if (!c || !out || (sys && sys->n_atoms > 0 && (!out->forces || !out->energy))) {
         set_error("flr_energy_forces_uncertainty: null argument (energy and forces are required)");
         return FLR_EINVAL;
     }

@@ -49,12 +49,12 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
     constexpr int NK = (KF + 31) / 32;
     __shared__ __align__(16) DescSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * kWarpsDesc + w;
-    if (i >= a.n) return;
+    // persistent warps: a fixed grid walks the atoms
+    for (int i = blockIdx.x * kWarpsDesc + w; i < a.n; i += gridDim.x * kWarpsDesc) {
     const int g = a.group[i];
     if (g < 0) {
         if (lane == 0) a.norm[i] = 0.f;
-        return;
+        continue;
     }
     const int cls = group_cls(g);
     const int reg = group_region(g);
@@ -181,6 +181,8 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
             dl[o] = __float2bfloat16_rn(0.f);
         }
     }
+    __syncwarp();
+    }  // atoms
 }
 
 // Scatter compact rows back to the full layout (for flr_compute_descriptors).
@@ -239,11 +241,13 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.A = ctx->A;
     a.norm = ctx->norm;
     a.bf16 = ctx->p.precision == FLR_PREC_BF16X3;
-    const int grid = (n + kWarpsDesc - 1) / kWarpsDesc;
-    if (ctx->dims.N == 8)
+    if (ctx->dims.N == 8) {
+        const int grid = persistent_grid(k_desc<8>, kWarpsDesc * 32, ctx->num_sms, (n + kWarpsDesc - 1) / kWarpsDesc);
         k_desc<8><<<grid, kWarpsDesc * 32, 0, st>>>(a);
-    else
+    } else {
+        const int grid = persistent_grid(k_desc<7>, kWarpsDesc * 32, ctx->num_sms, (n + kWarpsDesc - 1) / kWarpsDesc);
         k_desc<7><<<grid, kWarpsDesc * 32, 0, st>>>(a);
+    }
     count_launch(ctx);
     return cuda_fail(cudaGetLastError(), "descriptor kernel");
 }

@@ -66,11 +66,12 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_force(ForceArgs a)
     constexpr int NK = (KF + 31) / 32;
     __shared__ __align__(16) ForceSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x * kWarpsDesc + w;
     float vir[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
-    const int g = i < a.n ? a.group[i] : -2;
+    // persistent warps: a fixed grid walks the atoms (and keeps the virial partials few)
+    for (int i = blockIdx.x * kWarpsDesc + w; i < a.n; i += gridDim.x * kWarpsDesc) {
+    const int g = a.group[i];
 
     if (g >= 0) {
         const int cls = group_cls(g), reg = group_region(g);
@@ -214,13 +215,15 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_force(ForceArgs a)
                 fix_add(dst + 2, fi[2], a.status);
             }
         }
-    } else if (g == -1) {
+    } else {
         if (lane == 0) {
             a.energy[i] = 0.f;
             if (a.variance) a.variance[i] = 0.f;
             if (a.sigma) a.sigma[i] = 0.f;
         }
     }
+    __syncwarp();
+    }  // atoms
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
     for (int k = 0; k < 9; ++k)
@@ -252,11 +255,10 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
     __shared__ double sE[8], sK[8];
     __shared__ float sS[8];
     __shared__ int sI[8];
-    const int i = blockIdx.x * 256 + threadIdx.x;
     double e = 0.0, ke = 0.0;
     float smax = 0.f;
     int iso = 0;
-    if (i < a.n) {
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < a.n; i += gridDim.x * 256) {
         float f[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -264,9 +266,9 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
         a.forces[3 * (size_t)i + 0] = f[0];
         a.forces[3 * (size_t)i + 1] = f[1];
         a.forces[3 * (size_t)i + 2] = f[2];
-        e = (double)a.energy[i];
-        if (a.sigma) smax = a.sigma[i];
-        iso = a.norm[i] > 0.f ? 0 : 1;
+        e += (double)a.energy[i];
+        if (a.sigma) smax = fmaxf(smax, a.sigma[i]);
+        iso += a.norm[i] > 0.f ? 0 : 1;
         if (a.kick.enabled) {
             const int s = min(max(a.kick.species[i], 0), kSpecies - 1);
             float4 v = a.kick.vel[i];
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
             v.y += h * f[1];
             v.z += h * f[2];
             a.kick.vel[i] = v;
-            ke = (double)a.kick.half_m[s] * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+            ke += (double)a.kick.half_m[s] * (double)(v.x * v.x + v.y * v.y + v.z * v.z);
         }
     }
     for (int o = 16; o; o >>= 1) {
@@ -396,11 +398,16 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.Facc = reinterpret_cast<unsigned long long *>(ctx->Facc);
     a.vir_part = ctx->partials;
     a.status = ctx->status;
-    const int grid = (n + kWarpsDesc - 1) / kWarpsDesc;
-    if (ctx->dims.N == 8)
+    const long long work = (n + kWarpsDesc - 1) / kWarpsDesc;
+    int grid;
+    if (ctx->dims.N == 8) {
+        grid = std::min(kMaxPartials, persistent_grid(k_force<8>, kWarpsDesc * 32, ctx->num_sms, work));
         k_force<8><<<grid, kWarpsDesc * 32, 0, st>>>(a);
-    else
+    } else {
+        grid = std::min(kMaxPartials, persistent_grid(k_force<7>, kWarpsDesc * 32, ctx->num_sms, work));
         k_force<7><<<grid, kWarpsDesc * 32, 0, st>>>(a);
+    }
+    ctx->n_part = grid;
     count_launch(ctx);
     return cuda_fail(cudaGetLastError(), "force kernel");
 }
@@ -409,8 +416,8 @@ int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out
                     cudaStream_t st)
 {
     (void)nl;
-    const int n_vir = (n + kWarpsDesc - 1) / kWarpsDesc;
-    const int nfin = (n + 255) / 256;
+    const int n_vir = ctx->n_part;
+    const int nfin = std::min(kMaxPartials, persistent_grid(k_finalize, 256, ctx->num_sms, (n + 255) / 256));
     FinArgs f;
     f.Facc = reinterpret_cast<const unsigned long long *>(ctx->Facc);
     f.energy = out->energy;
@@ -418,7 +425,7 @@ int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out
     f.norm = ctx->norm;
     f.forces = out->forces;
     f.n = n;
-    f.part = ctx->partials + (size_t)n_vir * 9;
+    f.part = ctx->partials + (size_t)kMaxPartials * 9;
     f.kick = kick;
     k_finalize<<<nfin, 256, 0, st>>>(f);
     TotArgs t;

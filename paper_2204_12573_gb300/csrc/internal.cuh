@@ -187,6 +187,20 @@ int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, con
                     const int *species, int n, const KickArgs &kick, float dt, float disp2_max,
                     cudaStream_t st);
 
+// Grid of a persistent kernel: every SM filled to its occupancy limit, but
+// never more blocks than there is work for.
+template <typename K>
+inline int persistent_grid(K kernel, int threads, int num_sms, long long work_blocks)
+{
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    long long g = (long long)per_sm * num_sms;
+    if (work_blocks < g) g = work_blocks;
+    return (int)(g < 1 ? 1 : g);
+}
+constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
+
 // ---- shared device helpers ----
 
 // Decode a neighbour entry: (j << 7) | code, code = (sx+2)*25 + (sy+2)*5 + (sz+2).

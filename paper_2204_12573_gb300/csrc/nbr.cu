@@ -104,9 +104,8 @@ __global__ void k_zero_bins(int32_t *cnt, long long nbins, const int32_t *flags)
 __global__ void k_bin(BinArgs a)
 {
     if (a.flags[0] == 0) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) a.gtab->max_count = 0;
-    if (i >= a.n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.gtab->max_count = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
     float4 p = a.pos_mut ? a.pos_mut[i] : a.pos[i];
     double f[3];
     frac_of(p, a.inv, f);
@@ -140,6 +139,7 @@ __global__ void k_bin(BinArgs a)
     a.img[i] = (im[0] & 0xFF) | ((im[1] & 0xFF) << 8) | ((im[2] & 0xFF) << 16);
     a.pos_ref[i] = p;
     atomicAdd(a.bin_count + bin, 1);
+    }
 }
 
 // exclusive scan, three passes: per-block scan -> scan of block sums -> add
@@ -217,10 +217,10 @@ __global__ void k_scatter(const int32_t *atom_bin, int32_t *fill, int32_t *bin_a
                           const int32_t *flags)
 {
     if (flags[0] == 0) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int slot = atomicAdd(fill + atom_bin[i], 1);
-    bin_atoms[slot] = i;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int slot = atomicAdd(fill + atom_bin[i], 1);
+        bin_atoms[slot] = i;
+    }
 }
 
 // order each bin's atoms by index so that rows come out deterministic
@@ -228,17 +228,18 @@ __global__ void k_sort_bins(const int32_t *bin_start, int32_t *bin_atoms, long l
                             const int32_t *flags)
 {
     if (flags[0] == 0) return;
-    long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (b >= nbins) return;
-    int s = bin_start[b], e = bin_start[b + 1];
-    for (int k = s + 1; k < e; ++k) {
-        int v = bin_atoms[k];
-        int q = k - 1;
-        while (q >= s && bin_atoms[q] > v) {
-            bin_atoms[q + 1] = bin_atoms[q];
-            --q;
+    for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nbins;
+         b += (long long)gridDim.x * blockDim.x) {
+        int s = bin_start[b], e = bin_start[b + 1];
+        for (int k = s + 1; k < e; ++k) {
+            int v = bin_atoms[k];
+            int q = k - 1;
+            while (q >= s && bin_atoms[q] > v) {
+                bin_atoms[q + 1] = bin_atoms[q];
+                --q;
+            }
+            bin_atoms[q + 1] = v;
         }
-        bin_atoms[q + 1] = v;
     }
 }
 
@@ -264,8 +265,8 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
 {
     if (a.flags[0] == 0) return;
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= a.n) return;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < a.n; i += warps) {
     const float4 pi = a.pos[i];
     const int bin = a.atom_bin[i];
     const int bi[3] = {bin / (a.nb[1] * a.nb[2]), (bin / a.nb[2]) % a.nb[1], bin % a.nb[2]};
@@ -353,6 +354,8 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
         }
         a.group[i] = g;
     }
+    __syncwarp();
+    }  // atoms
 }
 
 // ---- stable partition of atoms into compaction groups ----
@@ -626,15 +629,17 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     b.gtab = nl->gtab;
     b.flags = nl->flags;
     b.status = ctx->status;
-    k_bin<<<(n + 255) / 256, 256, 0, st>>>(b);
+    k_bin<<<std::min((n + 255) / 256, ctx->num_sms * 8), 256, 0, st>>>(b);
 
     // bin_start = exclusive scan of counts; block sums live in blk_group's tail
     int32_t *bsums = nl->blk_group + (size_t)8 * ((nl->n_cap + kGroupBlock - 1) / kGroupBlock + 1);
     k_scan_blocks<<<nbb, kScanBlock, 0, st>>>(nl->bin_fill, nl->bin_start, bsums, nbins, nl->flags);
     k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, nl->bin_start + nbins, nl->flags, ctx->status);
     k_scan_add<<<nbb, kScanBlock, 0, st>>>(nl->bin_start, nl->bin_fill, bsums, nbins, nl->flags);
-    k_scatter<<<(n + 255) / 256, 256, 0, st>>>(nl->atom_bin, nl->bin_fill, nl->bin_atoms, n, nl->flags);
-    k_sort_bins<<<(int)((nbins + 255) / 256), 256, 0, st>>>(nl->bin_start, nl->bin_atoms, nbins, nl->flags);
+    k_scatter<<<std::min((n + 255) / 256, ctx->num_sms * 8), 256, 0, st>>>(nl->atom_bin, nl->bin_fill,
+                                                                          nl->bin_atoms, n, nl->flags);
+    k_sort_bins<<<(int)std::min<long long>((nbins + 255) / 256, ctx->num_sms * 8), 256, 0, st>>>(
+        nl->bin_start, nl->bin_atoms, nbins, nl->flags);
 
     RowArgs r;
     r.pos = wrap_positions ? pos_mut : pos;
@@ -661,7 +666,7 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.gtab = nl->gtab;
     r.flags = nl->flags;
     r.status = ctx->status;
-    k_build_rows<<<(n + 7) / 8, 256, 0, st>>>(r);
+    k_build_rows<<<persistent_grid(k_build_rows, 256, ctx->num_sms, (n + 7) / 8), 256, 0, st>>>(r);
 
     const int nblk = (n + kGroupBlock - 1) / kGroupBlock;
     k_group_count<<<nblk, kGroupBlock, 0, st>>>(nl->group, n, nl->blk_group, nl->flags);
