@@ -296,6 +296,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    rebuild_count = {}
+
     def timed(precision, profile=False, clocks=None):
         ff.set_precision(precision)
         st = reset()
@@ -316,6 +318,7 @@ def run_ours(args):
             clocks.__exit__()
         ms = e0.elapsed_time(e1)
         launches = ff.launch_count() - l0
+        rebuild_count[precision] = int(out["totals"][13].item())
         prof = None
         if profile:
             prof = ff.profile_read()
@@ -430,6 +433,7 @@ def run_ours(args):
                 "config": _config(n, "3xBF16 tcgen05 quadratic forms, FP32 elsewhere, FP64 totals"),
                 "plain_fp32": {"value": round(value_fp32, 3), "ms_per_step": round(ms_fp32 / args.steps, 4)},
                 "force_err_ev_per_A": ferr,
+                "rebuilds_in_timed_steps": rebuild_count,
                 "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
                 "kernels_ms_per_step_fp32": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_fp32.items()}
                 if prof_fp32 else None,

@@ -76,6 +76,40 @@ __device__ __forceinline__ void ylm_grad_contract(float x, float y, float z, con
                   c[14] * Y[14] + c[15] * Y[15]);
 }
 
+// One harmonic: Y_lm(u) and grad P_lm(u) for a compile-time lm (after
+// unrolling, the switch folds away).
+__device__ __forceinline__ void ylm_one(int lm, float x, float y, float z, float xx, float yy, float zz,
+                                        float &Y, float &dx, float &dy, float &dz)
+{
+    switch (lm) {
+    case 0: Y = kY00; dx = 0.f; dy = 0.f; dz = 0.f; break;
+    case 1: Y = kY1 * y; dx = 0.f; dy = kY1; dz = 0.f; break;
+    case 2: Y = kY1 * z; dx = 0.f; dy = 0.f; dz = kY1; break;
+    case 3: Y = kY1 * x; dx = kY1; dy = 0.f; dz = 0.f; break;
+    case 4: Y = kY2a * x * y; dx = kY2a * y; dy = kY2a * x; dz = 0.f; break;
+    case 5: Y = kY2a * y * z; dx = 0.f; dy = kY2a * z; dz = kY2a * y; break;
+    case 6: Y = kY20 * (2.f * zz - xx - yy); dx = -2.f * kY20 * x; dy = -2.f * kY20 * y; dz = 4.f * kY20 * z; break;
+    case 7: Y = kY2a * x * z; dx = kY2a * z; dy = 0.f; dz = kY2a * x; break;
+    case 8: Y = kY22 * (xx - yy); dx = 2.f * kY22 * x; dy = -2.f * kY22 * y; dz = 0.f; break;
+    case 9: Y = kY33 * y * (3.f * xx - yy); dx = 6.f * kY33 * x * y; dy = kY33 * (3.f * xx - 3.f * yy); dz = 0.f; break;
+    case 10: Y = kY32 * x * y * z; dx = kY32 * y * z; dy = kY32 * x * z; dz = kY32 * x * y; break;
+    case 11:
+        Y = kY31 * y * (4.f * zz - xx - yy);
+        dx = -2.f * kY31 * x * y; dy = kY31 * (4.f * zz - xx - 3.f * yy); dz = 8.f * kY31 * y * z;
+        break;
+    case 12:
+        Y = kY30 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+        dx = -6.f * kY30 * x * z; dy = -6.f * kY30 * y * z; dz = kY30 * (6.f * zz - 3.f * xx - 3.f * yy);
+        break;
+    case 13:
+        Y = kY31 * x * (4.f * zz - xx - yy);
+        dx = kY31 * (4.f * zz - 3.f * xx - yy); dy = -2.f * kY31 * x * y; dz = 8.f * kY31 * x * z;
+        break;
+    case 14: Y = kY32b * z * (xx - yy); dx = 2.f * kY32b * x * z; dy = -2.f * kY32b * y * z; dz = kY32b * (xx - yy); break;
+    default: Y = kY33 * x * (xx - 3.f * yy); dx = kY33 * (3.f * xx - 3.f * yy); dy = -6.f * kY33 * x * y; dz = 0.f; break;
+    }
+}
+
 // l of harmonic index lm
 __host__ __device__ constexpr int l_of(int lm) { return lm < 1 ? 0 : (lm < 4 ? 1 : (lm < 9 ? 2 : 3)); }
 

@@ -1,13 +1,15 @@
 // Per-atom normalized ACE-B2 descriptor (Sec. V-B "Local structure
 // descriptors" and "Acceleration of heterogeneous multi-element system").
 //
-// One warp per atom.  Lanes first take the neighbour-list entries 32 at a
-// time (coalesced row loads), evaluate the basis of the pairs inside r_cut
-// and stage it in shared memory; then every lane owns 8 coefficients of A
+// One warp per atom (persistent warps).  Lanes take the neighbour-list
+// entries 32 at a time (coalesced row loads) and compact the pairs inside
+// r_cut into a per-warp queue, so the basis is evaluated only for those
+// pairs with the lanes full; then every lane owns 8 coefficients of A
 // (radial index n = lane / 4, four harmonics, both neighbour species) and
-// accumulates them over the staged pairs, so no cross-lane reduction of A is
+// accumulates them over the queued pairs, so no cross-lane reduction of A is
 // needed.  B2 = sum_m A_a A_b is contracted for the atom's compaction class
-// only (both species blocks, or the one block its neighbours occupy),
+// only (both species blocks, or the one block its neighbours occupy), one
+// radial-channel pair (all four l) per lane from float4 rows of A,
 // normalized, and written as one row of the class's GEMM operand (FP32, and
 // for the 3xBF16 path also BF16 hi and lo parts).
 #include "basis.cuh"
@@ -16,7 +18,7 @@
 namespace flr {
 namespace {
 
-constexpr int kAStride = 17;   // padded channel stride of A in shared memory
+constexpr int kAStride = 20;   // padded channel stride of A in shared memory (conflict-free float4 rows)
 
 struct DescArgs {
     const float4 *pos;
@@ -36,152 +38,188 @@ struct DescArgs {
 
 template <int N>
 struct DescSmem {
-    float Rf[kWarpsDesc][32][N];
-    float Y[kWarpsDesc][32][16];
-    int sp[kWarpsDesc][32];
+    float4 rec[kWarpsDesc][64];          // compacted pairs inside r_cut: r_ij, species of j
+    float Rf[kWarpsDesc][32][N];         // staged radial values of up to 32 pairs
+    float Y[kWarpsDesc][32][16];         // staged harmonics
     float A[kWarpsDesc][2 * N * kAStride];
 };
+
+// Basis of up to 32 staged pairs (lane p evaluates pair p), then the lanes
+// that own A coefficients accumulate over them.
+template <int N>
+__device__ __forceinline__ void desc_batch(DescSmem<N> &sm, int w, int lane, int m, float rc, float acc0[4],
+                                           float acc1[4])
+{
+    if (lane < m) {
+        const float4 r = sm.rec[w][lane];
+        const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+        const float rr = sqrtf(d2), inv = 1.f / rr;
+        float Rf[N], dummy[N];
+        radial<N, false>(rr, rc, Rf, dummy);
+        float Y[16];
+        real_ylm(r.x * inv, r.y * inv, r.z * inv, Y);
+#pragma unroll
+        for (int n = 0; n < N; ++n) sm.Rf[w][lane][n] = Rf[n];
+#pragma unroll
+        for (int k = 0; k < 16; k += 4)
+            *reinterpret_cast<float4 *>(&sm.Y[w][lane][k]) = make_float4(Y[k], Y[k + 1], Y[k + 2], Y[k + 3]);
+    }
+    __syncwarp();
+    const int my_n = lane >> 2, quad = lane & 3;
+    if (my_n < N) {
+        for (int p = 0; p < m; ++p) {
+            const float rf = sm.Rf[w][p][my_n];
+            const float4 y = *reinterpret_cast<const float4 *>(&sm.Y[w][p][4 * quad]);
+            if (__float_as_int(sm.rec[w][p].w) == 0) {
+                acc0[0] += rf * y.x; acc0[1] += rf * y.y; acc0[2] += rf * y.z; acc0[3] += rf * y.w;
+            } else {
+                acc1[0] += rf * y.x; acc1[1] += rf * y.y; acc1[2] += rf * y.z; acc1[3] += rf * y.w;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// B2 for one radial-channel pair (a, b): all four l at once from two rows of A.
+__device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
+{
+    const float4 *pa = reinterpret_cast<const float4 *>(sA + a * kAStride);
+    const float4 *pb = reinterpret_cast<const float4 *>(sA + b * kAStride);
+    const float4 a0 = pa[0], a1 = pa[1], a2 = pa[2], a3 = pa[3];
+    const float4 b0 = pb[0], b1 = pb[1], b2 = pb[2], b3 = pb[3];
+    float4 o;
+    o.x = a0.x * b0.x;                                                      // l = 0
+    o.y = a0.y * b0.y + a0.z * b0.z + a0.w * b0.w;                          // l = 1
+    o.z = a1.x * b1.x + a1.y * b1.y + a1.z * b1.z + a1.w * b1.w + a2.x * b2.x;   // l = 2
+    o.w = a2.y * b2.y + a2.z * b2.z + a2.w * b2.w + a3.x * b3.x + a3.y * b3.y + a3.z * b3.z +
+          a3.w * b3.w;                                                      // l = 3
+    return o;
+}
 
 template <int N>
 __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
 {
-    constexpr int KF = (2 * N) * (2 * N + 1) / 2 * 4;   // full descriptor dimension
-    constexpr int NK = (KF + 31) / 32;
+    constexpr int C = 2 * N;
+    constexpr int NPF = C * (C + 1) / 2;          // channel pairs of the full descriptor
+    constexpr int NPS = N * (N + 1) / 2;          // channel pairs of a one-species block
+    constexpr int MAXP = (NPF + 31) / 32;
     __shared__ __align__(16) DescSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float rc = a.rcut, rc2 = rc * rc;
     // persistent warps: a fixed grid walks the atoms
     for (int i = blockIdx.x * kWarpsDesc + w; i < a.n; i += gridDim.x * kWarpsDesc) {
-    const int g = a.group[i];
-    if (g < 0) {
-        if (lane == 0) a.norm[i] = 0.f;
-        continue;
-    }
-    const int cls = group_cls(g);
-    const int reg = group_region(g);
-    const float4 pi = a.pos[i];
-    const int cnt = a.count[i];
-    const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
-    const float rc = a.rcut, rc2 = rc * rc;
-
-    const int my_n = lane >> 2, quad = lane & 3;
-    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
-
-    for (int base = 0; base < cnt; base += 32) {
-        const int q = base + lane;
-        bool ok = false;
-        float3 r = make_float3(0.f, 0.f, 0.f);
-        float d2 = 0.f;
-        int sj = 0;
-        if (q < cnt) {
-            int j, sx, sy, sz;
-            decode_entry(rowp[q], j, sx, sy, sz);
-            const float4 pj = a.pos[j];
-            r = pair_vector(pi, pj, sx, sy, sz, a.cell);
-            d2 = r.x * r.x + r.y * r.y + r.z * r.z;
-            ok = d2 < rc2;
-            sj = a.species[j];
+        const int g = a.group[i];
+        if (g < 0) {
+            if (lane == 0) a.norm[i] = 0.f;
+            continue;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        const int slot = __popc(m & ((1u << lane) - 1u));
-        if (ok) {
-            const float rr = sqrtf(d2);
-            const float inv = 1.f / rr;
-            float Rf[N], dummy[N];
-            radial<N, false>(rr, rc, Rf, dummy);
-            float Y[16];
-            real_ylm(r.x * inv, r.y * inv, r.z * inv, Y);
-#pragma unroll
-            for (int n = 0; n < N; ++n) sm.Rf[w][slot][n] = Rf[n];
-#pragma unroll
-            for (int k = 0; k < 16; k += 4)
-                *reinterpret_cast<float4 *>(&sm.Y[w][slot][k]) = make_float4(Y[k], Y[k + 1], Y[k + 2], Y[k + 3]);
-            sm.sp[w][slot] = sj;
+        const int cls = group_cls(g);
+        const int reg = group_region(g);
+        const float4 pi = a.pos[i];
+        const int cnt = a.count[i];
+        const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
+
+        float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+        int nv = 0;   // staged pairs
+        for (int base = 0; base < cnt; base += 32) {
+            const int q = base + lane;
+            bool ok = false;
+            float3 r = make_float3(0.f, 0.f, 0.f);
+            int sj = 0;
+            if (q < cnt) {
+                int j, sx, sy, sz;
+                decode_entry(rowp[q], j, sx, sy, sz);
+                const float4 pj = a.pos[j];
+                r = pair_vector(pi, pj, sx, sy, sz, a.cell);
+                ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
+                sj = a.species[j];
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) sm.rec[w][nv + __popc(m & ((1u << lane) - 1u))] = make_float4(r.x, r.y, r.z, __int_as_float(sj));
+            nv += __popc(m);
+            __syncwarp();
+            if (nv >= 32) {
+                desc_batch<N>(sm, w, lane, 32, rc, acc0, acc1);
+                if (lane < nv - 32) sm.rec[w][lane] = sm.rec[w][32 + lane];
+                nv -= 32;
+                __syncwarp();
+            }
+        }
+        if (nv > 0) desc_batch<N>(sm, w, lane, nv, rc, acc0, acc1);
+
+        // A to shared memory (padded rows) and to global memory (blocks in use only)
+        float *sA = sm.A[w];
+        const int my_n = lane >> 2, quad = lane & 3;
+        if (my_n < N) {
+            *reinterpret_cast<float4 *>(sA + my_n * kAStride + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
+            *reinterpret_cast<float4 *>(sA + (N + my_n) * kAStride + 4 * quad) =
+                make_float4(acc1[0], acc1[1], acc1[2], acc1[3]);
+            float *Ag = a.A + (size_t)i * (C * 16);
+            if (cls != 2)
+                *reinterpret_cast<float4 *>(Ag + my_n * 16 + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
+            if (cls != 1)
+                *reinterpret_cast<float4 *>(Ag + (N + my_n) * 16 + 4 * quad) =
+                    make_float4(acc1[0], acc1[1], acc1[2], acc1[3]);
         }
         __syncwarp();
-        const int nv = __popc(m);
-        if (my_n < N) {
-            for (int p = 0; p < nv; ++p) {
-                const float rf = sm.Rf[w][p][my_n];
-                const float4 y = *reinterpret_cast<const float4 *>(&sm.Y[w][p][4 * quad]);
-                if (sm.sp[w][p] == 0) {
-                    acc0[0] += rf * y.x; acc0[1] += rf * y.y; acc0[2] += rf * y.z; acc0[3] += rf * y.w;
-                } else {
-                    acc1[0] += rf * y.x; acc1[1] += rf * y.y; acc1[2] += rf * y.z; acc1[3] += rf * y.w;
+
+        // B2 of the class's channel pairs, four l per pair
+        const int npairs = cls == 0 ? NPF : NPS;
+        const int choff = cls == 0 ? 0 : (cls - 1) * N;
+        const int32_t *tab = a.tab[reg];
+        float4 b[MAXP];
+        float ss = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAXP; ++k) {
+            const int t = lane + 32 * k;
+            b[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < npairs) {
+                const int e = __ldg(tab + 4 * t);
+                b[k] = b2_pair(sA, choff + (e & 255), choff + ((e >> 8) & 255));
+                ss += b[k].x * b[k].x + b[k].y * b[k].y + b[k].z * b[k].z + b[k].w * b[k].w;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const float nrm = sqrtf(ss);
+        const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+        if (lane == 0) a.norm[i] = nrm;
+
+        const int r = a.row[i];
+        const int K = 4 * npairs;
+        float *d32 = a.D32[reg] + (size_t)r * a.kp32[reg];
+        __nv_bfloat16 *dh = a.bf16 ? a.Dhi[reg] + (size_t)r * a.kp64[reg] : nullptr;
+        __nv_bfloat16 *dl = a.bf16 ? a.Dlo[reg] + (size_t)r * a.kp64[reg] : nullptr;
+#pragma unroll
+        for (int k = 0; k < MAXP; ++k) {
+            const int t = lane + 32 * k;
+            if (t < npairs) {
+                const float4 v = make_float4(b[k].x * inv, b[k].y * inv, b[k].z * inv, b[k].w * inv);
+                *reinterpret_cast<float4 *>(d32 + 4 * t) = v;
+                if (dh) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+                    const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+                    __nv_bfloat162 hi01, hi23, lo01, lo23;
+                    hi01.x = h0; hi01.y = h1; hi23.x = h2; hi23.y = h3;
+                    lo01.x = __float2bfloat16_rn(v.x - __bfloat162float(h0));
+                    lo01.y = __float2bfloat16_rn(v.y - __bfloat162float(h1));
+                    lo23.x = __float2bfloat16_rn(v.z - __bfloat162float(h2));
+                    lo23.y = __float2bfloat16_rn(v.w - __bfloat162float(h3));
+                    uint2 hv, lv;
+                    hv.x = *reinterpret_cast<uint32_t *>(&hi01); hv.y = *reinterpret_cast<uint32_t *>(&hi23);
+                    lv.x = *reinterpret_cast<uint32_t *>(&lo01); lv.y = *reinterpret_cast<uint32_t *>(&lo23);
+                    *reinterpret_cast<uint2 *>(dh + 4 * t) = hv;
+                    *reinterpret_cast<uint2 *>(dl + 4 * t) = lv;
                 }
             }
         }
-        __syncwarp();
-    }
-
-    // A to shared memory (padded) and to global memory (blocks in use only)
-    float *sA = sm.A[w];
-    if (my_n < N) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            sA[my_n * kAStride + 4 * quad + k] = acc0[k];
-            sA[(N + my_n) * kAStride + 4 * quad + k] = acc1[k];
-        }
-        float *Ag = a.A + (size_t)i * (2 * N * 16);
-        if (cls != 2)
-            *reinterpret_cast<float4 *>(Ag + my_n * 16 + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
-        if (cls != 1)
-            *reinterpret_cast<float4 *>(Ag + (N + my_n) * 16 + 4 * quad) =
-                make_float4(acc1[0], acc1[1], acc1[2], acc1[3]);
-    }
-    __syncwarp();
-
-    // B2 for the compaction class
-    const int K = a.K[reg];
-    const int32_t *tab = a.tab[reg];
-    const int choff = cls == 0 ? 0 : (cls - 1) * N;
-    float b[NK];
-    float ss = 0.f;
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        const int o = lane + 32 * k;
-        float v = 0.f;
-        if (o < K) {
-            const int t = __ldg(tab + o);
-            const int ca = choff + (t & 255), cb = choff + ((t >> 8) & 255), l = t >> 16;
-            const float *pa = sA + ca * kAStride + l * l, *pb = sA + cb * kAStride + l * l;
-            for (int mm = 0; mm < 2 * l + 1; ++mm) v += pa[mm] * pb[mm];
-        }
-        b[k] = v;
-        ss += v * v;
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const float nrm = sqrtf(ss);
-    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
-    if (lane == 0) a.norm[i] = nrm;
-
-    const int r = a.row[i];
-    float *d32 = a.D32[reg] + (size_t)r * a.kp32[reg];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        const int o = lane + 32 * k;
-        if (o < a.kp32[reg]) d32[o] = o < K ? b[k] * inv : 0.f;
-    }
-    for (int o = NK * 32 + lane; o < a.kp32[reg]; o += 32) d32[o] = 0.f;
-    if (a.bf16) {
-        __nv_bfloat16 *dh = a.Dhi[reg] + (size_t)r * a.kp64[reg];
-        __nv_bfloat16 *dl = a.Dlo[reg] + (size_t)r * a.kp64[reg];
-#pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            const int o = lane + 32 * k;
-            if (o < a.kp64[reg]) {
-                const float v = o < K ? b[k] * inv : 0.f;
-                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                dh[o] = hi;
-                dl[o] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        for (int o = K + lane; o < a.kp32[reg]; o += 32) d32[o] = 0.f;
+        if (dh)
+            for (int o = K + lane; o < a.kp64[reg]; o += 32) {
+                dh[o] = __float2bfloat16_rn(0.f);
+                dl[o] = __float2bfloat16_rn(0.f);
             }
-        }
-        for (int o = NK * 32 + lane; o < a.kp64[reg]; o += 32) {
-            dh[o] = __float2bfloat16_rn(0.f);
-            dl[o] = __float2bfloat16_rn(0.f);
-        }
-    }
-    __syncwarp();
+        __syncwarp();
     }  // atoms
 }
 

@@ -9,18 +9,28 @@
 //   w_{a,lm} = dE/dA_{a,lm} = sum_b G_{ab,l} A_{b,lm},  G_aa = 2 g_aa,
 // and each neighbour pair then needs only
 //   f_ij = dE_i/dr_ij = sum_{n,lm} w_{(s_j,n),lm} grad phi_{n,lm}(r_ij),
-// which costs O(N L^2) per pair instead of O(d).  F_i += f_ij, F_j -= f_ij;
-// the scatter to j goes through 64-bit fixed-point atomics (2^-32 eV/A
-// resolution), whose integer sums do not depend on arrival order, so the
-// forces are bitwise reproducible.
+// which costs O(N L^2) per pair instead of O(d).  F_i += f_ij, F_j -= f_ij.
+//
+// Work layout: persistent warps walk the atoms.  For each atom a warp forms
+// E, V, g and w (w goes to one of four shared-memory slots), then appends
+// the atom's pairs inside r_cut to a per-warp FIFO queue; whenever 32 pairs
+// are queued they are evaluated with one pair per lane, whatever atoms they
+// belong to, so the expensive per-pair path always runs with full lanes.
+// Forces are accumulated as 64-bit fixed point (2^-32 eV/A): F_j through
+// global atomics, F_i through per-slot shared-memory atomics flushed once per
+// atom.  Integer sums do not depend on order, so forces are bitwise
+// reproducible; the virial is accumulated per lane in a fixed order.
 #include "basis.cuh"
 #include "internal.cuh"
 
 namespace flr {
 namespace {
 
-constexpr int kAStride = 17;
-constexpr float kFixScale = 4294967296.0f;   // 2^32
+constexpr int kWarpsForce = 4;                // warps per CTA (shared memory: 36 KB)
+constexpr int kAStride = 20;                  // float4-aligned, conflict-free A rows
+constexpr int kSlots = 4;                     // atoms whose w may be referenced by queued pairs
+constexpr int kWSlot = 2 * 16 * 8 + 4;        // floats per w slot: [species][lm][n (8, padded)] + pad
+constexpr float kFixScale = 4294967296.0f;    // 2^32
 
 struct ForceArgs {
     const float4 *pos;
@@ -41,56 +51,173 @@ struct ForceArgs {
 
 template <int N>
 struct ForceSmem {
-    float G[kWarpsDesc][(2 * N) * (2 * N + 1) / 2 * 4];
-    float A[kWarpsDesc][2 * N * kAStride];
-    float W[kWarpsDesc][2 * N * kAStride];
-    float vir[kWarpsDesc][9];
+    float G[kWarpsForce][(2 * N) * (2 * N + 1) / 2 * 4];
+    float A[kWarpsForce][2 * N * kAStride];
+    float W[kWarpsForce][kSlots * kWSlot];
+    float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
+    unsigned long long F[kWarpsForce][kSlots][3];
+    int atom[kWarpsForce][kSlots];
+    int qseq[kWarpsForce][64];                  // atom sequence number of each queued pair
+    float vir[kWarpsForce][9];
 };
 
 __device__ __forceinline__ int tri(int a, int b, int C) { return a * C - a * (a - 1) / 2 + (b - a); }
 
-__device__ __forceinline__ void fix_add(unsigned long long *dst, float v, int *status)
+__device__ __forceinline__ long long to_fix(float v, int *status)
 {
     const float s = v * kFixScale;
     if (!(fabsf(s) < 9.0e18f)) {   // also catches NaN
         atomicOr(status, kErrNonFinite);
-        return;
+        return 0;
     }
-    atomicAdd(dst, (unsigned long long)__float2ll_rn(s));
+    return __float2ll_rn(s);
+}
+
+// Evaluate m <= 32 queued pairs, one per lane.
+template <int N>
+__device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, int m, float rc,
+                                            unsigned long long *Facc, int *status, float vir[9])
+{
+    if (lane < m) {
+        const float4 rec = sm.q[w][lane];
+        const int packed = __float_as_int(rec.w);
+        const int j = packed & 0x1FFFFFF;
+        const int sj = (packed >> 25) & 1;
+        const int slot = (packed >> 26) & 3;
+        const float d2 = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z;
+        const float rr = sqrtf(d2), inv = 1.f / rr;
+        const float ux = rec.x * inv, uy = rec.y * inv, uz = rec.z * inv;
+        float Rf[N], dRf[N];
+        radial<N, true>(rr, rc, Rf, dRf);
+        const float *wp = sm.W[w] + slot * kWSlot + sj * 128;
+        const float xx = ux * ux, yy = uy * uy, zz = uz * uz;
+        // f = u (sum_lm c'_lm Y_lm - (1/r) sum_lm l c_lm Y_lm) + (1/r) sum_lm c_lm grad P_lm(u),
+        // c_lm = sum_n w_{n,lm} R_n f_c,  c'_lm = sum_n w_{n,lm} (R_n f_c)'
+        float radial_part = 0.f, lsum = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+        for (int lm = 0; lm < 16; ++lm) {
+            const float4 w0 = *reinterpret_cast<const float4 *>(wp + lm * 8);
+            const float4 w1 = *reinterpret_cast<const float4 *>(wp + lm * 8 + 4);
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float c = 0.f, cp = 0.f;
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                c += wv[n] * Rf[n];
+                cp += wv[n] * dRf[n];
+            }
+            float Y, dx, dy, dz;
+            ylm_one(lm, ux, uy, uz, xx, yy, zz, Y, dx, dy, dz);
+            radial_part += cp * Y;
+            lsum += (float)l_of(lm) * c * Y;
+            gx += c * dx;
+            gy += c * dy;
+            gz += c * dz;
+        }
+        const float coef = radial_part - lsum * inv;
+        const float fx = coef * ux + gx * inv;
+        const float fy = coef * uy + gy * inv;
+        const float fz = coef * uz + gz * inv;
+        const long long ix = to_fix(fx, status), iy = to_fix(fy, status), iz = to_fix(fz, status);
+        unsigned long long *dj = Facc + 3 * (size_t)j;
+        atomicAdd(dj + 0, (unsigned long long)(-ix));
+        atomicAdd(dj + 1, (unsigned long long)(-iy));
+        atomicAdd(dj + 2, (unsigned long long)(-iz));
+        atomicAdd(&sm.F[w][slot][0], (unsigned long long)ix);
+        atomicAdd(&sm.F[w][slot][1], (unsigned long long)iy);
+        atomicAdd(&sm.F[w][slot][2], (unsigned long long)iz);
+        vir[0] -= rec.x * fx; vir[1] -= rec.x * fy; vir[2] -= rec.x * fz;
+        vir[3] -= rec.y * fx; vir[4] -= rec.y * fy; vir[5] -= rec.y * fz;
+        vir[6] -= rec.z * fx; vir[7] -= rec.z * fy; vir[8] -= rec.z * fz;
+    }
+    __syncwarp();
+}
+
+// Evaluate every queued pair and compact the queue.
+template <int N>
+__device__ __forceinline__ void drain(ForceSmem<N> &sm, int w, int lane, int &nq, bool all, float rc,
+                                      unsigned long long *Facc, int *status, float vir[9])
+{
+    while (nq >= 32 || (all && nq > 0)) {
+        const int m = nq < 32 ? nq : 32;
+        force_batch<N>(sm, w, lane, m, rc, Facc, status, vir);
+        const int rest = nq - m;
+        float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int sq = 0;
+        if (lane < rest) {
+            r4 = sm.q[w][m + lane];
+            sq = sm.qseq[w][m + lane];
+        }
+        __syncwarp();
+        if (lane < rest) {
+            sm.q[w][lane] = r4;
+            sm.qseq[w][lane] = sq;
+        }
+        __syncwarp();
+        nq = rest;
+    }
+}
+
+// Move a slot's accumulated F_i to the global accumulator and clear it.
+template <int N>
+__device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, int slot,
+                                           unsigned long long *Facc)
+{
+    const int i = sm.atom[w][slot];
+    if (lane < 3 && i >= 0) {
+        atomicAdd(Facc + 3 * (size_t)i + lane, sm.F[w][slot][lane]);
+        sm.F[w][slot][lane] = 0ull;
+    }
+    __syncwarp();
+    if (lane == 0) sm.atom[w][slot] = -1;
+    __syncwarp();
 }
 
 template <int N>
-__global__ void __launch_bounds__(kWarpsDesc * 32) k_force(ForceArgs a)
+__global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 {
-    constexpr int KF = (2 * N) * (2 * N + 1) / 2 * 4;
-    constexpr int NK = (KF + 31) / 32;
+    constexpr int C = 2 * N;
+    constexpr int KF = C * (C + 1) / 2 * 4;
+    constexpr int NK4 = (KF / 4 + 31) / 32;        // float4 groups per lane of a descriptor row
     __shared__ __align__(16) ForceSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float rc = a.rcut, rc2 = rc * rc;
     float vir[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
-    // persistent warps: a fixed grid walks the atoms (and keeps the virial partials few)
-    for (int i = blockIdx.x * kWarpsDesc + w; i < a.n; i += gridDim.x * kWarpsDesc) {
-    const int g = a.group[i];
+    if (lane < kSlots) sm.atom[w][lane] = -1;
+    if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0ull;
+    __syncwarp();
+    int nq = 0;        // queued pairs
+    int seq = 0;       // atoms given a w slot so far by this warp
 
-    if (g >= 0) {
+    for (int i = blockIdx.x * kWarpsForce + w; i < a.n; i += gridDim.x * kWarpsForce) {
+        const int g = a.group[i];
+        if (g < 0) {
+            if (lane == 0) {
+                a.energy[i] = 0.f;
+                if (a.variance) a.variance[i] = 0.f;
+                if (a.sigma) a.sigma[i] = 0.f;
+            }
+            continue;
+        }
         const int cls = group_cls(g), reg = group_region(g);
         const int K = a.K[reg];
         const int r = a.row[i];
-        const float *d = a.D32[reg] + (size_t)r * a.kp32[reg];
-        const float *pr = a.P[reg] + (size_t)r * (2 * K);
-        float dv[NK], pb[NK];
+        const float4 *d4 = reinterpret_cast<const float4 *>(a.D32[reg] + (size_t)r * a.kp32[reg]);
+        const float4 *p4 = reinterpret_cast<const float4 *>(a.P[reg] + (size_t)r * (2 * K));
+        float4 dv[NK4], pb[NK4];
         float E = 0.f, V = 0.f;
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            const int o = lane + 32 * k;
-            dv[k] = 0.f;
-            pb[k] = 0.f;
-            if (o < K) {
-                dv[k] = d[o];
-                pb[k] = pr[o];
-                E += dv[k] * pb[k];
-                V += dv[k] * pr[K + o];
+        for (int k = 0; k < NK4; ++k) {
+            const int o = lane + 32 * k;          // float4 index
+            dv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            pb[k] = dv[k];
+            if (4 * o < K) {
+                dv[k] = d4[o];
+                pb[k] = p4[o];
+                const float4 ps = p4[K / 4 + o];
+                E += dv[k].x * pb[k].x + dv[k].y * pb[k].y + dv[k].z * pb[k].z + dv[k].w * pb[k].w;
+                V += dv[k].x * ps.x + dv[k].y * ps.y + dv[k].z * ps.z + dv[k].w * ps.w;
             }
         }
 #pragma unroll
@@ -104,126 +231,102 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_force(ForceArgs a)
             if (a.sigma) a.sigma[i] = sqrtf(fmaxf(V, 0.f));
         }
         const float nrm = a.norm[i];
-        if (nrm > 0.f) {
-            // g = (2/||B||)(beta d - E d) in the class's compact order
-            const float s2 = 2.f / nrm;
-            float *sG = sm.G[w];
+        if (!(nrm > 0.f)) continue;
+
+        // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
+        const int slot = seq & (kSlots - 1);
+        if (nq > 0 && sm.qseq[w][0] <= seq - kSlots) drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
+        flush_slot<N>(sm, w, lane, slot, a.Facc);
+        if (lane == 0) sm.atom[w][slot] = i;
+
+        // g = (2/||B||)(beta d - E d), compact order of the class
+        const float s2 = 2.f / nrm;
+        float *sG = sm.G[w];
 #pragma unroll
-            for (int k = 0; k < NK; ++k) {
-                const int o = lane + 32 * k;
-                if (o < K) sG[o] = s2 * (pb[k] - E * dv[k]);
-            }
-            // A of the blocks in use (zeros elsewhere)
-            float *sA = sm.A[w];
-            const float *Ag = a.A + (size_t)i * (2 * N * 16);
-            for (int k = lane; k < 2 * N * 16; k += 32) {
-                const int c = k >> 4, lm = k & 15;
-                const bool used = cls == 0 || (c / N) == (cls - 1);
-                sA[c * kAStride + lm] = used ? Ag[k] : 0.f;
-            }
-            __syncwarp();
-            // w = G~ A over the class's channels
-            const int Cg = cls == 0 ? 2 * N : N;
+        for (int k = 0; k < NK4; ++k) {
+            const int o = lane + 32 * k;
+            if (4 * o < K)
+                *reinterpret_cast<float4 *>(sG + 4 * o) =
+                    make_float4(s2 * (pb[k].x - E * dv[k].x), s2 * (pb[k].y - E * dv[k].y),
+                                s2 * (pb[k].z - E * dv[k].z), s2 * (pb[k].w - E * dv[k].w));
+        }
+        // A of the blocks in use (zero elsewhere)
+        float *sA = sm.A[w];
+        const float4 *Ag = reinterpret_cast<const float4 *>(a.A + (size_t)i * (C * 16));
+        for (int k = lane; k < C * 4; k += 32) {
+            const int ch = k >> 2;
+            const bool used = cls == 0 || (ch / N) == (cls - 1);
+            *reinterpret_cast<float4 *>(sA + ch * kAStride + 4 * (k & 3)) = used ? Ag[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        // w = G~ A over the class's channels -> slot layout [species][lm][n]
+        {
+            const int Cg = cls == 0 ? C : N;
             const int choff = cls == 0 ? 0 : (cls - 1) * N;
-            float *sW = sm.W[w];
+            float *ws = sm.W[w] + slot * kWSlot;
             const int my_n = lane >> 2, quad = lane & 3;
-            for (int k = lane; k < 2 * N * kAStride; k += 32) sW[k] = 0.f;
-            __syncwarp();
-            if (my_n < N) {
-                for (int blk = 0; blk < (cls == 0 ? 2 : 1); ++blk) {
-                    const int aloc = blk * N + my_n;   // channel inside the class
-                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            // l of the four harmonics owned by this lane: quad 0 -> 0,1,1,1; 1 -> 2,2,2,2; 2 -> 2,3,3,3; 3 -> 3
+            for (int blk = 0; blk < 2; ++blk) {
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                const bool active = my_n < N && (cls == 0 || blk == cls - 1);
+                if (active) {
+                    const int aloc = (cls == 0 ? blk * N : 0) + my_n;
                     for (int bloc = 0; bloc < Cg; ++bloc) {
                         const int lo = min(aloc, bloc), hi = max(aloc, bloc);
-                        const float *gp = sG + tri(lo, hi, Cg) * 4;
+                        const float4 gl = *reinterpret_cast<const float4 *>(sG + 4 * tri(lo, hi, Cg));
+                        const float4 av = *reinterpret_cast<const float4 *>(sA + (choff + bloc) * kAStride + 4 * quad);
                         const float dbl = aloc == bloc ? 2.f : 1.f;
-                        const float *ap = sA + (choff + bloc) * kAStride + 4 * quad;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[k] += dbl * gp[l_of(4 * quad + k)] * ap[k];
+                        float g0, g1, g2, g3;
+                        if (quad == 0) { g0 = gl.x; g1 = gl.y; g2 = gl.y; g3 = gl.y; }
+                        else if (quad == 1) { g0 = gl.z; g1 = gl.z; g2 = gl.z; g3 = gl.z; }
+                        else if (quad == 2) { g0 = gl.z; g1 = gl.w; g2 = gl.w; g3 = gl.w; }
+                        else { g0 = gl.w; g1 = gl.w; g2 = gl.w; g3 = gl.w; }
+                        acc[0] += dbl * g0 * av.x;
+                        acc[1] += dbl * g1 * av.y;
+                        acc[2] += dbl * g2 * av.z;
+                        acc[3] += dbl * g3 * av.w;
                     }
+                }
+                if (my_n < 8) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) sW[(choff + aloc) * kAStride + 4 * quad + k] = acc[k];
+                    for (int k = 0; k < 4; ++k) ws[blk * 128 + (4 * quad + k) * 8 + my_n] = (my_n < N) ? acc[k] : 0.f;
                 }
             }
-            __syncwarp();
+        }
+        __syncwarp();
 
-            // per-pair forces
-            const float4 pi = a.pos[i];
-            const int cnt = a.count[i];
-            const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
-            const float rc = a.rcut, rc2 = rc * rc;
-            float fi[3] = {0.f, 0.f, 0.f};
-            for (int base = 0; base < cnt; base += 32) {
-                const int q = base + lane;
-                if (q < cnt) {
-                    int j, sx, sy, sz;
-                    decode_entry(rowp[q], j, sx, sy, sz);
-                    const float4 pj = a.pos[j];
-                    const float3 rv = pair_vector(pi, pj, sx, sy, sz, a.cell);
-                    const float d2 = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z;
-                    if (d2 < rc2) {
-                        const int sj = a.species[j];
-                        const float rr = sqrtf(d2), inv = 1.f / rr;
-                        const float ux = rv.x * inv, uy = rv.y * inv, uz = rv.z * inv;
-                        float Rf[N], dRf[N];
-                        radial<N, true>(rr, rc, Rf, dRf);
-                        float Y[16];
-                        real_ylm(ux, uy, uz, Y);
-                        const float *wp = sW + (sj == 0 ? 0 : N) * kAStride;
-                        float c[16], cp[16];
-#pragma unroll
-                        for (int lm = 0; lm < 16; ++lm) {
-                            float s = 0.f, t = 0.f;
-#pragma unroll
-                            for (int n = 0; n < N; ++n) {
-                                const float wv = wp[n * kAStride + lm];
-                                s += wv * Rf[n];
-                                t += wv * dRf[n];
-                            }
-                            c[lm] = s;
-                            cp[lm] = t;
-                        }
-                        float gx, gy, gz, lsum;
-                        ylm_grad_contract(ux, uy, uz, c, Y, gx, gy, gz, lsum);
-                        float radial_part = 0.f;
-#pragma unroll
-                        for (int lm = 0; lm < 16; ++lm) radial_part += cp[lm] * Y[lm];
-                        const float coef = radial_part - lsum * inv;
-                        const float fx = coef * ux + gx * inv;
-                        const float fy = coef * uy + gy * inv;
-                        const float fz = coef * uz + gz * inv;
-                        fi[0] += fx;
-                        fi[1] += fy;
-                        fi[2] += fz;
-                        unsigned long long *dst = a.Facc + 3 * (size_t)j;
-                        fix_add(dst + 0, -fx, a.status);
-                        fix_add(dst + 1, -fy, a.status);
-                        fix_add(dst + 2, -fz, a.status);
-                        vir[0] -= rv.x * fx; vir[1] -= rv.x * fy; vir[2] -= rv.x * fz;
-                        vir[3] -= rv.y * fx; vir[4] -= rv.y * fy; vir[5] -= rv.y * fz;
-                        vir[6] -= rv.z * fx; vir[7] -= rv.z * fy; vir[8] -= rv.z * fz;
-                    }
-                }
+        // queue the pairs inside r_cut
+        const float4 pi = a.pos[i];
+        const int cnt = a.count[i];
+        const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
+        for (int base = 0; base < cnt; base += 32) {
+            const int q = base + lane;
+            bool ok = false;
+            float3 rv = make_float3(0.f, 0.f, 0.f);
+            int j = 0;
+            if (q < cnt) {
+                int sx, sy, sz;
+                decode_entry(rowp[q], j, sx, sy, sz);
+                const float4 pj = a.pos[j];
+                rv = pair_vector(pi, pj, sx, sy, sz, a.cell);
+                ok = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z < rc2;
             }
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                for (int o = 16; o; o >>= 1) fi[c] += __shfl_xor_sync(0xffffffffu, fi[c], o);
-            if (lane == 0) {
-                unsigned long long *dst = a.Facc + 3 * (size_t)i;
-                fix_add(dst + 0, fi[0], a.status);
-                fix_add(dst + 1, fi[1], a.status);
-                fix_add(dst + 2, fi[2], a.status);
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int sj = a.species[j] & 1;
+                const int at = nq + __popc(m & ((1u << lane) - 1u));
+                sm.q[w][at] = make_float4(rv.x, rv.y, rv.z, __int_as_float(j | (sj << 25) | (slot << 26)));
+                sm.qseq[w][at] = seq;
             }
+            nq += __popc(m);
+            __syncwarp();
+            drain<N>(sm, w, lane, nq, false, rc, a.Facc, a.status, vir);
         }
-    } else {
-        if (lane == 0) {
-            a.energy[i] = 0.f;
-            if (a.variance) a.variance[i] = 0.f;
-            if (a.sigma) a.sigma[i] = 0.f;
-        }
-    }
-    __syncwarp();
+        ++seq;
     }  // atoms
+    drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
+    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc);
+
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
     for (int k = 0; k < 9; ++k)
@@ -234,7 +337,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_force(ForceArgs a)
     __syncthreads();
     if (threadIdx.x < 9) {
         double s = 0.0;
-        for (int q = 0; q < kWarpsDesc; ++q) s += (double)sm.vir[q][threadIdx.x];
+        for (int q = 0; q < kWarpsForce; ++q) s += (double)sm.vir[q][threadIdx.x];
         a.vir_part[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
     }
 }
@@ -398,14 +501,14 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.Facc = reinterpret_cast<unsigned long long *>(ctx->Facc);
     a.vir_part = ctx->partials;
     a.status = ctx->status;
-    const long long work = (n + kWarpsDesc - 1) / kWarpsDesc;
+    const long long work = (n + kWarpsForce - 1) / kWarpsForce;
     int grid;
     if (ctx->dims.N == 8) {
-        grid = std::min(kMaxPartials, persistent_grid(k_force<8>, kWarpsDesc * 32, ctx->num_sms, work));
-        k_force<8><<<grid, kWarpsDesc * 32, 0, st>>>(a);
+        grid = std::min(kMaxPartials, persistent_grid(k_force<8>, kWarpsForce * 32, ctx->num_sms, work));
+        k_force<8><<<grid, kWarpsForce * 32, 0, st>>>(a);
     } else {
-        grid = std::min(kMaxPartials, persistent_grid(k_force<7>, kWarpsDesc * 32, ctx->num_sms, work));
-        k_force<7><<<grid, kWarpsDesc * 32, 0, st>>>(a);
+        grid = std::min(kMaxPartials, persistent_grid(k_force<7>, kWarpsForce * 32, ctx->num_sms, work));
+        k_force<7><<<grid, kWarpsForce * 32, 0, st>>>(a);
     }
     ctx->n_part = grid;
     count_launch(ctx);
