@@ -80,6 +80,33 @@ __device__ __forceinline__ void desc_batch(DescSmem<N> &sm, int w, int lane, int
     __syncwarp();
 }
 
+// Per-atom values loaded one iteration ahead of their use.
+struct DescPre {
+    int g, cnt, row;
+    float4 pi;
+    int e0, e1;     // the first 64 neighbour-list entries (lane, 32 + lane)
+};
+
+__device__ __forceinline__ DescPre desc_preload(const DescArgs &a, int i, int lane)
+{
+    DescPre p;
+    p.g = -2;
+    p.cnt = 0;
+    p.row = 0;
+    p.pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    p.e0 = p.e1 = 0;
+    if (i < a.n) {
+        p.g = a.group[i];
+        p.cnt = a.count[i];
+        p.row = a.row[i];
+        p.pi = a.pos[i];
+        const int32_t *rp = a.entries + (size_t)i * a.max_nbr;
+        p.e0 = rp[lane];
+        p.e1 = a.max_nbr > 32 ? rp[32 + lane] : 0;
+    }
+    return p;
+}
+
 // B2 for one radial-channel pair (a, b): all four l at once from two rows of A.
 __device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
 {
@@ -97,7 +124,7 @@ __device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
 }
 
 template <int N>
-__global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
+__global__ void __launch_bounds__(kWarpsDesc * 32, 3) k_desc(DescArgs a)
 {
     constexpr int C = 2 * N;
     constexpr int NPF = C * (C + 1) / 2;          // channel pairs of the full descriptor
@@ -106,17 +133,23 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
     __shared__ __align__(16) DescSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float rc = a.rcut, rc2 = rc * rc;
-    // persistent warps: a fixed grid walks the atoms
-    for (int i = blockIdx.x * kWarpsDesc + w; i < a.n; i += gridDim.x * kWarpsDesc) {
-        const int g = a.group[i];
+    // persistent warps: a fixed grid walks the atoms; each atom's scalars and
+    // first 64 list entries are loaded one iteration ahead
+    const int stride = gridDim.x * kWarpsDesc;
+    int i = blockIdx.x * kWarpsDesc + w;
+    DescPre cur = desc_preload(a, i, lane);
+    for (; i < a.n; i += stride) {
+        const DescPre nxt = desc_preload(a, i + stride, lane);
+        const int g = cur.g;
         if (g < 0) {
             if (lane == 0) a.norm[i] = 0.f;
+            cur = nxt;
             continue;
         }
         const int cls = group_cls(g);
         const int reg = group_region(g);
-        const float4 pi = a.pos[i];
-        const int cnt = a.count[i];
+        const float4 pi = cur.pi;
+        const int cnt = cur.cnt;
         const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
 
         float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
@@ -128,7 +161,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
             int sj = 0;
             if (q < cnt) {
                 int j, sx, sy, sz;
-                decode_entry(rowp[q], j, sx, sy, sz);
+                decode_entry(base == 0 ? cur.e0 : (base == 32 ? cur.e1 : rowp[q]), j, sx, sy, sz);
                 const float4 pj = a.pos[j];
                 r = pair_vector(pi, pj, sx, sy, sz, a.cell);
                 ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
@@ -185,7 +218,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
         const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
         if (lane == 0) a.norm[i] = nrm;
 
-        const int r = a.row[i];
+        const int r = cur.row;
         const int K = 4 * npairs;
         float *d32 = a.D32[reg] + (size_t)r * a.kp32[reg];
         __nv_bfloat16 *dh = a.bf16 ? a.Dhi[reg] + (size_t)r * a.kp64[reg] : nullptr;
@@ -220,6 +253,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32) k_desc(DescArgs a)
                 dl[o] = __float2bfloat16_rn(0.f);
             }
         __syncwarp();
+        cur = nxt;
     }  // atoms
 }
 

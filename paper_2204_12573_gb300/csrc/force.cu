@@ -172,6 +172,37 @@ __device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, in
     __syncwarp();
 }
 
+// Per-atom values loaded one iteration ahead, so their latency overlaps the
+// previous atom's work.
+struct AtomPre {
+    int g, cnt, row;
+    float nrm;
+    float4 pi;
+    int e0, e1;     // the first 64 neighbour-list entries (lane, 32 + lane)
+};
+
+__device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int lane)
+{
+    AtomPre p;
+    p.g = -2;
+    p.cnt = 0;
+    p.row = 0;
+    p.nrm = 0.f;
+    p.pi = make_float4(0.f, 0.f, 0.f, 0.f);
+    p.e0 = p.e1 = 0;
+    if (i < a.n) {
+        p.g = a.group[i];
+        p.cnt = a.count[i];
+        p.row = a.row[i];
+        p.nrm = a.norm[i];
+        p.pi = a.pos[i];
+        const int32_t *rp = a.entries + (size_t)i * a.max_nbr;
+        p.e0 = rp[lane];
+        p.e1 = a.max_nbr > 32 ? rp[32 + lane] : 0;
+    }
+    return p;
+}
+
 template <int N>
 __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 {
@@ -189,35 +220,49 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     __syncwarp();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
+    const int stride = gridDim.x * kWarpsForce;
+    int i = blockIdx.x * kWarpsForce + w;
+    AtomPre cur = preload(a, i, lane);
 
-    for (int i = blockIdx.x * kWarpsForce + w; i < a.n; i += gridDim.x * kWarpsForce) {
-        const int g = a.group[i];
+    for (; i < a.n; i += stride) {
+        const AtomPre nxt = preload(a, i + stride, lane);
+        const int g = cur.g;
         if (g < 0) {
             if (lane == 0) {
                 a.energy[i] = 0.f;
                 if (a.variance) a.variance[i] = 0.f;
                 if (a.sigma) a.sigma[i] = 0.f;
             }
+            cur = nxt;
             continue;
         }
+        // start the neighbour gathers of the first 64 entries now
+        const int cnt = cur.cnt;
+        float4 pj0 = make_float4(0.f, 0.f, 0.f, 0.f), pj1 = pj0;
+        int sj0 = 0, sj1 = 0;
+        if (lane < cnt) {
+            const int j = (int)((unsigned)cur.e0 >> 7);
+            pj0 = a.pos[j];
+            sj0 = a.species[j];
+        }
+        if (32 + lane < cnt) {
+            const int j = (int)((unsigned)cur.e1 >> 7);
+            pj1 = a.pos[j];
+            sj1 = a.species[j];
+        }
+
         const int cls = group_cls(g), reg = group_region(g);
         const int K = a.K[reg];
-        const int r = a.row[i];
-        const float4 *d4 = reinterpret_cast<const float4 *>(a.D32[reg] + (size_t)r * a.kp32[reg]);
-        const float4 *p4 = reinterpret_cast<const float4 *>(a.P[reg] + (size_t)r * (2 * K));
-        float4 dv[NK4], pb[NK4];
+        const float4 *d4 = reinterpret_cast<const float4 *>(a.D32[reg] + (size_t)cur.row * a.kp32[reg]);
+        const float4 *p4 = reinterpret_cast<const float4 *>(a.P[reg] + (size_t)cur.row * (2 * K));
         float E = 0.f, V = 0.f;
 #pragma unroll
         for (int k = 0; k < NK4; ++k) {
             const int o = lane + 32 * k;          // float4 index
-            dv[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            pb[k] = dv[k];
             if (4 * o < K) {
-                dv[k] = d4[o];
-                pb[k] = p4[o];
-                const float4 ps = p4[K / 4 + o];
-                E += dv[k].x * pb[k].x + dv[k].y * pb[k].y + dv[k].z * pb[k].z + dv[k].w * pb[k].w;
-                V += dv[k].x * ps.x + dv[k].y * ps.y + dv[k].z * ps.z + dv[k].w * ps.w;
+                const float4 dv = d4[o], pb = p4[o], ps = p4[K / 4 + o];
+                E += dv.x * pb.x + dv.y * pb.y + dv.z * pb.z + dv.w * pb.w;
+                V += dv.x * ps.x + dv.y * ps.y + dv.z * ps.z + dv.w * ps.w;
             }
         }
 #pragma unroll
@@ -230,8 +275,11 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             if (a.variance) a.variance[i] = V;
             if (a.sigma) a.sigma[i] = sqrtf(fmaxf(V, 0.f));
         }
-        const float nrm = a.norm[i];
-        if (!(nrm > 0.f)) continue;
+        const float nrm = cur.nrm;
+        if (!(nrm > 0.f)) {
+            cur = nxt;
+            continue;
+        }
 
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
         const int slot = seq & (kSlots - 1);
@@ -239,16 +287,18 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         flush_slot<N>(sm, w, lane, slot, a.Facc);
         if (lane == 0) sm.atom[w][slot] = i;
 
-        // g = (2/||B||)(beta d - E d), compact order of the class
+        // g = (2/||B||)(beta d - E d), compact order of the class (rows re-read from L1)
         const float s2 = 2.f / nrm;
         float *sG = sm.G[w];
 #pragma unroll
         for (int k = 0; k < NK4; ++k) {
             const int o = lane + 32 * k;
-            if (4 * o < K)
+            if (4 * o < K) {
+                const float4 dv = d4[o], pb = p4[o];
                 *reinterpret_cast<float4 *>(sG + 4 * o) =
-                    make_float4(s2 * (pb[k].x - E * dv[k].x), s2 * (pb[k].y - E * dv[k].y),
-                                s2 * (pb[k].z - E * dv[k].z), s2 * (pb[k].w - E * dv[k].w));
+                    make_float4(s2 * (pb.x - E * dv.x), s2 * (pb.y - E * dv.y), s2 * (pb.z - E * dv.z),
+                                s2 * (pb.w - E * dv.w));
+            }
         }
         // A of the blocks in use (zero elsewhere)
         float *sA = sm.A[w];
@@ -296,26 +346,36 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         __syncwarp();
 
         // queue the pairs inside r_cut
-        const float4 pi = a.pos[i];
-        const int cnt = a.count[i];
+        const float4 pi = cur.pi;
         const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
         for (int base = 0; base < cnt; base += 32) {
             const int q = base + lane;
             bool ok = false;
             float3 rv = make_float3(0.f, 0.f, 0.f);
-            int j = 0;
+            int j = 0, sj = 0;
             if (q < cnt) {
                 int sx, sy, sz;
-                decode_entry(rowp[q], j, sx, sy, sz);
-                const float4 pj = a.pos[j];
+                float4 pj;
+                if (base == 0) {
+                    decode_entry(cur.e0, j, sx, sy, sz);
+                    pj = pj0;
+                    sj = sj0;
+                } else if (base == 32) {
+                    decode_entry(cur.e1, j, sx, sy, sz);
+                    pj = pj1;
+                    sj = sj1;
+                } else {
+                    decode_entry(rowp[q], j, sx, sy, sz);
+                    pj = a.pos[j];
+                    sj = a.species[j];
+                }
                 rv = pair_vector(pi, pj, sx, sy, sz, a.cell);
                 ok = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z < rc2;
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
-                const int sj = a.species[j] & 1;
                 const int at = nq + __popc(m & ((1u << lane) - 1u));
-                sm.q[w][at] = make_float4(rv.x, rv.y, rv.z, __int_as_float(j | (sj << 25) | (slot << 26)));
+                sm.q[w][at] = make_float4(rv.x, rv.y, rv.z, __int_as_float(j | ((sj & 1) << 25) | (slot << 26)));
                 sm.qseq[w][at] = seq;
             }
             nq += __popc(m);
@@ -323,6 +383,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             drain<N>(sm, w, lane, nq, false, rc, a.Facc, a.status, vir);
         }
         ++seq;
+        cur = nxt;
     }  // atoms
     drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
     for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc);

@@ -260,101 +260,135 @@ struct RowArgs {
 
 __device__ __forceinline__ int img_comp(int v, int d) { return (int)(int8_t)((v >> (8 * d)) & 0xFF); }
 
-// one warp per atom; lanes take the candidates of a bin 32 at a time
+// One warp per atom.  The candidates of all stencil bins are treated as one
+// sequence (bins in stencil order, atoms inside a bin by index), and lanes
+// take 32 consecutive candidates at a time, so the lanes stay full however
+// few atoms each bin holds.
 __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
 {
     if (a.flags[0] == 0) return;
-    const int lane = threadIdx.x & 31;
+    __shared__ int s_start[8][32], s_excl[8][32], s_shift[8][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < a.n; i += warps) {
-    const float4 pi = a.pos[i];
-    const int bin = a.atom_bin[i];
-    const int bi[3] = {bin / (a.nb[1] * a.nb[2]), (bin / a.nb[2]) % a.nb[1], bin % a.nb[2]};
-    const int imi = a.img[i];
-    int32_t *row = a.entries + (size_t)i * a.max_nbr;
-    int cnt = 0;
-    unsigned smask = 0;
-    for (int dx = -a.R[0]; dx <= a.R[0]; ++dx)
-        for (int dy = -a.R[1]; dy <= a.R[1]; ++dy)
-            for (int dz = -a.R[2]; dz <= a.R[2]; ++dz) {
-                int dd[3] = {dx, dy, dz}, bj[3], sb[3];
+    const int span[3] = {2 * a.R[0] + 1, 2 * a.R[1] + 1, 2 * a.R[2] + 1};
+    const int n_stencil = span[0] * span[1] * span[2];
+    for (int i = blockIdx.x * (blockDim.x >> 5) + wl; i < a.n; i += warps) {
+        const float4 pi = a.pos[i];
+        const int bin = a.atom_bin[i];
+        const int bi[3] = {bin / (a.nb[1] * a.nb[2]), (bin / a.nb[2]) % a.nb[1], bin % a.nb[2]};
+        const int imi = a.img[i];
+        int32_t *row = a.entries + (size_t)i * a.max_nbr;
+        int cnt = 0;
+        unsigned smask = 0;
+        for (int sbase = 0; sbase < n_stencil; sbase += 32) {
+            // this lane's stencil bin: range of candidates and lattice shift
+            const int k = sbase + lane;
+            int c = 0, start = 0, shift = 0;
+            if (k < n_stencil) {
+                const int dd[3] = {k / (span[1] * span[2]) - a.R[0], (k / span[2]) % span[1] - a.R[1],
+                                   k % span[2] - a.R[2]};
+                int bj[3], sb[3];
                 bool skip = false;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    int k = bi[d] + dd[d];
+                    const int kk = bi[d] + dd[d];
                     if (a.pbc[d]) {
-                        int q = (k >= 0) ? k / a.nb[d] : -((-k + a.nb[d] - 1) / a.nb[d]);
+                        const int q = (kk >= 0) ? kk / a.nb[d] : -((-kk + a.nb[d] - 1) / a.nb[d]);
                         sb[d] = q;
-                        bj[d] = k - q * a.nb[d];
+                        bj[d] = kk - q * a.nb[d];
                     } else {
-                        skip |= (k < 0 || k >= a.nb[d]);
+                        skip |= (kk < 0 || kk >= a.nb[d]);
                         sb[d] = 0;
-                        bj[d] = k;
+                        bj[d] = kk;
                     }
                 }
-                if (skip) continue;
-                const int b = (bj[0] * a.nb[1] + bj[1]) * a.nb[2] + bj[2];
-                const int s0 = a.bin_start[b], s1 = a.bin_start[b + 1];
-                for (int base = s0; base < s1; base += 32) {
-                    const int q = base + lane;
-                    bool ok = false;
-                    int entry = 0, sj = 0;
-                    if (q < s1) {
-                        const int j = a.bin_atoms[q];
-                        const int imj = a.img[j];
-                        int S[3];
-#pragma unroll
-                        for (int d = 0; d < 3; ++d) S[d] = sb[d] + img_comp(imi, d) - img_comp(imj, d);
-                        const bool in_range = S[0] >= -2 && S[0] <= 2 && S[1] >= -2 && S[1] <= 2 &&
-                                              S[2] >= -2 && S[2] <= 2;
-                        if (!in_range) atomicOr(a.status, kErrShift);
-                        if (in_range && !(j == i && S[0] == 0 && S[1] == 0 && S[2] == 0)) {
-                            const float4 pj = a.pos[j];
-                            const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], a.cell);
-                            const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
-                            if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
-                                ok = d2 < a.rc2;
-                            } else {
-                                // near the cutoff: decide in FP64 from the exact inputs
-                                double t[3];
-#pragma unroll
-                                for (int c = 0; c < 3; ++c)
-                                    t[c] = S[0] * a.cell.c[c] + S[1] * a.cell.c[3 + c] + S[2] * a.cell.c[6 + c];
-                                const double x = ((double)pj.x - (double)pi.x) + t[0];
-                                const double y = ((double)pj.y - (double)pi.y) + t[1];
-                                const double z = ((double)pj.z - (double)pi.z) + t[2];
-                                ok = x * x + y * y + z * z < a.rc2d;
-                            }
-                            entry = (j << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
-                            sj = a.species[j];
-                        }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    const int slot = cnt + __popc(m & ((1u << lane) - 1u));
-                    if (ok) {
-                        if (slot < a.max_nbr) row[slot] = entry;
-                        smask |= 1u << (sj & 31);
-                    }
-                    cnt += __popc(m);
+                if (!skip) {
+                    const int b = (bj[0] * a.nb[1] + bj[1]) * a.nb[2] + bj[2];
+                    start = a.bin_start[b];
+                    c = a.bin_start[b + 1] - start;
+                    shift = (sb[0] & 0xFF) | ((sb[1] & 0xFF) << 8) | ((sb[2] & 0xFF) << 16);
                 }
             }
+            int incl = c;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) smask |= __shfl_xor_sync(0xffffffffu, smask, o);
-    if (lane == 0) {
-        if (cnt > a.max_nbr) atomicOr(a.status, kErrOverflow);
-        atomicMax(&a.gtab->max_count, cnt);
-        a.count[i] = min(cnt, a.max_nbr);
-        int g = -1;
-        if (cnt > 0) {
-            const int si = a.species[i];
-            if (si < 0 || si >= kSpecies || (smask >> kSpecies) != 0) atomicOr(a.status, kErrSpecies);
-            int cls = 0;
-            if (a.compaction) cls = (smask == 1u) ? 1 : (smask == 2u ? 2 : 0);
-            g = min(max(si, 0), kSpecies - 1) * 3 + cls;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            s_start[wl][lane] = start;
+            s_excl[wl][lane] = incl - c;
+            s_shift[wl][lane] = shift;
+            __syncwarp();
+            for (int base = 0; base < total; base += 32) {
+                const int t = base + lane;
+                bool ok = false;
+                int entry = 0, sj = 0;
+                if (t < total) {
+                    // last stencil slot whose first candidate index is <= t
+                    int lo = 0, hi = 31;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_excl[wl][mid] <= t) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int j = a.bin_atoms[s_start[wl][lo] + (t - s_excl[wl][lo])];
+                    const int sh = s_shift[wl][lo];
+                    const int imj = a.img[j];
+                    int S[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) S[d] = img_comp(sh, d) + img_comp(imi, d) - img_comp(imj, d);
+                    const bool in_range = S[0] >= -2 && S[0] <= 2 && S[1] >= -2 && S[1] <= 2 && S[2] >= -2 &&
+                                          S[2] <= 2;
+                    if (!in_range) atomicOr(a.status, kErrShift);
+                    if (in_range && !(j == i && S[0] == 0 && S[1] == 0 && S[2] == 0)) {
+                        const float4 pj = a.pos[j];
+                        const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], a.cell);
+                        const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                        if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
+                            ok = d2 < a.rc2;
+                        } else {
+                            // near the cutoff: decide in FP64 from the exact inputs
+                            double tv[3];
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc)
+                                tv[cc] = S[0] * a.cell.c[cc] + S[1] * a.cell.c[3 + cc] + S[2] * a.cell.c[6 + cc];
+                            const double x = ((double)pj.x - (double)pi.x) + tv[0];
+                            const double y = ((double)pj.y - (double)pi.y) + tv[1];
+                            const double z = ((double)pj.z - (double)pi.z) + tv[2];
+                            ok = x * x + y * y + z * z < a.rc2d;
+                        }
+                        entry = (j << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
+                        sj = a.species[j];
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+                if (ok) {
+                    if (slot < a.max_nbr) row[slot] = entry;
+                    smask |= 1u << (sj & 31);
+                }
+                cnt += __popc(m);
+            }
+            __syncwarp();
         }
-        a.group[i] = g;
-    }
-    __syncwarp();
+#pragma unroll
+        for (int o = 16; o; o >>= 1) smask |= __shfl_xor_sync(0xffffffffu, smask, o);
+        if (lane == 0) {
+            if (cnt > a.max_nbr) atomicOr(a.status, kErrOverflow);
+            atomicMax(&a.gtab->max_count, cnt);
+            a.count[i] = min(cnt, a.max_nbr);
+            int g = -1;
+            if (cnt > 0) {
+                const int si = a.species[i];
+                if (si < 0 || si >= kSpecies || (smask >> kSpecies) != 0) atomicOr(a.status, kErrSpecies);
+                int cls = 0;
+                if (a.compaction) cls = (smask == 1u) ? 1 : (smask == 2u ? 2 : 0);
+                g = min(max(si, 0), kSpecies - 1) * 3 + cls;
+            }
+            a.group[i] = g;
+        }
+        __syncwarp();
     }  // atoms
 }
 
