@@ -67,6 +67,7 @@ __device__ __forceinline__ void desc_batch(DescSmem<N> &sm, int w, int lane, int
     __syncwarp();
     const int my_n = lane >> 2, quad = lane & 3;
     if (my_n < N) {
+#pragma unroll 4
         for (int p = 0; p < m; ++p) {
             const float rf = sm.Rf[w][p][my_n];
             const float4 y = *reinterpret_cast<const float4 *>(&sm.Y[w][p][4 * quad]);

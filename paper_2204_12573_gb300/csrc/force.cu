@@ -17,9 +17,10 @@
 // are queued they are evaluated with one pair per lane, whatever atoms they
 // belong to, so the expensive per-pair path always runs with full lanes.
 // Forces are accumulated as 64-bit fixed point (2^-32 eV/A): F_j through
-// global atomics, F_i through per-slot shared-memory atomics flushed once per
-// atom.  Integer sums do not depend on order, so forces are bitwise
-// reproducible; the virial is accumulated per lane in a fixed order.
+// global atomics (integer sums do not depend on arrival order), F_i by
+// fixed-order warp reductions into a per-slot FP32 sum that is added once
+// per atom.  Forces are therefore bitwise reproducible; the virial is
+// accumulated per lane in a fixed order.
 #include "basis.cuh"
 #include "internal.cuh"
 
@@ -55,7 +56,7 @@ struct ForceSmem {
     float A[kWarpsForce][2 * N * kAStride];
     float W[kWarpsForce][kSlots * kWSlot];
     float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
-    unsigned long long F[kWarpsForce][kSlots][3];
+    float F[kWarpsForce][kSlots][3];             // F_i of each slot's atom, summed in a fixed order
     int atom[kWarpsForce][kSlots];
     int qseq[kWarpsForce][64];                  // atom sequence number of each queued pair
     float vir[kWarpsForce][9];
@@ -78,6 +79,8 @@ template <int N>
 __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, int m, float rc,
                                             unsigned long long *Facc, int *status, float vir[9])
 {
+    int my_slot = -1;
+    float f3[3] = {0.f, 0.f, 0.f};
     if (lane < m) {
         const float4 rec = sm.q[w][lane];
         const int packed = __float_as_int(rec.w);
@@ -122,12 +125,31 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
         atomicAdd(dj + 0, (unsigned long long)(-ix));
         atomicAdd(dj + 1, (unsigned long long)(-iy));
         atomicAdd(dj + 2, (unsigned long long)(-iz));
-        atomicAdd(&sm.F[w][slot][0], (unsigned long long)ix);
-        atomicAdd(&sm.F[w][slot][1], (unsigned long long)iy);
-        atomicAdd(&sm.F[w][slot][2], (unsigned long long)iz);
         vir[0] -= rec.x * fx; vir[1] -= rec.x * fy; vir[2] -= rec.x * fz;
         vir[3] -= rec.y * fx; vir[4] -= rec.y * fy; vir[5] -= rec.y * fz;
         vir[6] -= rec.z * fx; vir[7] -= rec.z * fy; vir[8] -= rec.z * fz;
+        my_slot = slot;
+        f3[0] = fx;
+        f3[1] = fy;
+        f3[2] = fz;
+    }
+    // F_i: the batch's pairs belong to at most kSlots atoms; sum each atom's
+    // pairs with a fixed-order warp reduction (deterministic) into its slot
+#pragma unroll
+    for (int s = 0; s < kSlots; ++s) {
+        if (!__any_sync(0xffffffffu, my_slot == s)) continue;
+        float v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v[c] = my_slot == s ? f3[c] : 0.f;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+        }
+        if (lane == 0) {
+            sm.F[w][s][0] += v[0];
+            sm.F[w][s][1] += v[1];
+            sm.F[w][s][2] += v[2];
+        }
     }
     __syncwarp();
 }
@@ -160,12 +182,12 @@ __device__ __forceinline__ void drain(ForceSmem<N> &sm, int w, int lane, int &nq
 // Move a slot's accumulated F_i to the global accumulator and clear it.
 template <int N>
 __device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, int slot,
-                                           unsigned long long *Facc)
+                                           unsigned long long *Facc, int *status)
 {
     const int i = sm.atom[w][slot];
     if (lane < 3 && i >= 0) {
-        atomicAdd(Facc + 3 * (size_t)i + lane, sm.F[w][slot][lane]);
-        sm.F[w][slot][lane] = 0ull;
+        atomicAdd(Facc + 3 * (size_t)i + lane, (unsigned long long)to_fix(sm.F[w][slot][lane], status));
+        sm.F[w][slot][lane] = 0.f;
     }
     __syncwarp();
     if (lane == 0) sm.atom[w][slot] = -1;
@@ -216,7 +238,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
     if (lane < kSlots) sm.atom[w][lane] = -1;
-    if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0ull;
+    if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0.f;
     __syncwarp();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
@@ -284,7 +306,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
         const int slot = seq & (kSlots - 1);
         if (nq > 0 && sm.qseq[w][0] <= seq - kSlots) drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
-        flush_slot<N>(sm, w, lane, slot, a.Facc);
+        flush_slot<N>(sm, w, lane, slot, a.Facc, a.status);
         if (lane == 0) sm.atom[w][slot] = i;
 
         // g = (2/||B||)(beta d - E d), compact order of the class (rows re-read from L1)
@@ -386,7 +408,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         cur = nxt;
     }  // atoms
     drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
-    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc);
+    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc, a.status);
 
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
