@@ -130,6 +130,8 @@ void free_workspace(flr_ctx *ctx)
         ctx->D32[r] = nullptr;
         ctx->Dhi[r] = ctx->Dlo[r] = nullptr;
         ctx->P[r] = nullptr;
+        cudaFree(ctx->G[r]);
+        ctx->G[r] = nullptr;
     }
     cudaFree(ctx->Facc);
     cudaFree(ctx->partials);
@@ -158,6 +160,7 @@ int ensure_workspace(flr_ctx *ctx, int n)
         if (s == FLR_OK) s = dev_alloc(&ctx->Dhi[r], N * D.kp64[r], "workspace Dhi");
         if (s == FLR_OK) s = dev_alloc(&ctx->Dlo[r], N * D.kp64[r], "workspace Dlo");
         if (s == FLR_OK) s = dev_alloc(&ctx->P[r], N * 2 * D.K[r], "workspace P");
+        if (s == FLR_OK) s = dev_alloc(&ctx->G[r], N * D.K[r], "workspace G");
     }
     if (s == FLR_OK) s = dev_alloc(&ctx->Facc, N * 3, "workspace forces");
     if (s == FLR_OK) s = dev_alloc(&ctx->partials, (size_t)kMaxPartials * 13 + 16, "workspace partials");
@@ -240,7 +243,7 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
     prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
     if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_QFORM, st);
-    s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, st) : launch_qform_tc(ctx, nl, st);
+    s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, out, st) : launch_qform_tc(ctx, nl, out, st);
     prof_end(ctx, FLR_KERNEL_QFORM, st);
     if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_FORCE, st);

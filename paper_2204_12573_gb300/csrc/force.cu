@@ -40,9 +40,8 @@ struct ForceArgs {
     int max_nbr, n;
     CellArg cell;
     float rcut;
-    const float *D32[2];
-    int kp32[2], K[2];
-    const float *P[2];
+    int K[2];
+    const float *G[2];         // g = dE/dB rows from the quadratic-form epilogue
     const float *A, *norm;
     float *energy, *variance, *sigma;
     unsigned long long *Facc;
@@ -275,32 +274,18 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 
         const int cls = group_cls(g), reg = group_region(g);
         const int K = a.K[reg];
-        const float4 *d4 = reinterpret_cast<const float4 *>(a.D32[reg] + (size_t)cur.row * a.kp32[reg]);
-        const float4 *p4 = reinterpret_cast<const float4 *>(a.P[reg] + (size_t)cur.row * (2 * K));
-        float E = 0.f, V = 0.f;
-#pragma unroll
-        for (int k = 0; k < NK4; ++k) {
-            const int o = lane + 32 * k;          // float4 index
-            if (4 * o < K) {
-                const float4 dv = d4[o], pb = p4[o], ps = p4[K / 4 + o];
-                E += dv.x * pb.x + dv.y * pb.y + dv.z * pb.z + dv.w * pb.w;
-                V += dv.x * ps.x + dv.y * ps.y + dv.z * ps.z + dv.w * ps.w;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            E += __shfl_xor_sync(0xffffffffu, E, o);
-            V += __shfl_xor_sync(0xffffffffu, V, o);
-        }
-        if (lane == 0) {
-            a.energy[i] = E;
-            if (a.variance) a.variance[i] = V;
-            if (a.sigma) a.sigma[i] = sqrtf(fmaxf(V, 0.f));
-        }
-        const float nrm = cur.nrm;
-        if (!(nrm > 0.f)) {
+        // E, V and sigma were written by the quadratic-form epilogue
+        if (!(cur.nrm > 0.f)) {
             cur = nxt;
             continue;
+        }
+        // g = dE/dB of this atom, in the compact order of its class
+        const float4 *g4 = reinterpret_cast<const float4 *>(a.G[reg] + (size_t)cur.row * K);
+        float4 gv[NK4];
+#pragma unroll
+        for (int k = 0; k < NK4; ++k) {
+            const int o = lane + 32 * k;
+            gv[k] = 4 * o < K ? g4[o] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
@@ -309,18 +294,11 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         flush_slot<N>(sm, w, lane, slot, a.Facc, a.status);
         if (lane == 0) sm.atom[w][slot] = i;
 
-        // g = (2/||B||)(beta d - E d), compact order of the class (rows re-read from L1)
-        const float s2 = 2.f / nrm;
         float *sG = sm.G[w];
 #pragma unroll
         for (int k = 0; k < NK4; ++k) {
             const int o = lane + 32 * k;
-            if (4 * o < K) {
-                const float4 dv = d4[o], pb = p4[o];
-                *reinterpret_cast<float4 *>(sG + 4 * o) =
-                    make_float4(s2 * (pb.x - E * dv.x), s2 * (pb.y - E * dv.y), s2 * (pb.z - E * dv.z),
-                                s2 * (pb.w - E * dv.w));
-            }
+            if (4 * o < K) *reinterpret_cast<float4 *>(sG + 4 * o) = gv[k];
         }
         // A of the blocks in use (zero elsewhere)
         float *sA = sm.A[w];
@@ -571,10 +549,8 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     for (int c = 0; c < 9; ++c) a.cell.c[c] = nl->plan.cell[c];
     a.rcut = (float)ctx->p.r_cut;
     for (int r = 0; r < 2; ++r) {
-        a.D32[r] = ctx->D32[r];
-        a.kp32[r] = ctx->dims.kp32[r];
         a.K[r] = ctx->dims.K[r];
-        a.P[r] = ctx->P[r];
+        a.G[r] = ctx->G[r];
     }
     a.A = ctx->A;
     a.norm = ctx->norm;

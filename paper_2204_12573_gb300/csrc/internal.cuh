@@ -51,7 +51,7 @@ struct GroupTab {
     int count[kGroups];
     int off[kGroups];       // first row inside its region
     int tiles_simt[kGroups + 1];  // prefix of SIMT tiles (M-tiles x N-tiles)
-    int tiles_tc[kGroups + 1];    // prefix of tensor-core tiles (M-tiles x N-chunks)
+    int tiles_tc[kGroups + 1];    // prefix of tensor-core M-tiles (each covers all its column chunks)
     int n_isolated;         // atoms with an empty list
     int max_count;          // longest neighbour row seen (before clipping)
 };
@@ -125,7 +125,8 @@ struct flr_ctx {
     float *D32[2];             // [n][kp32[r]]
     __nv_bfloat16 *Dhi[2];     // [n][kp64[r]]
     __nv_bfloat16 *Dlo[2];
-    float *P[2];               // [n][2K[r]]
+    float *P[2];               // [n][2K[r]] quadratic-form products (FP32 SIMT path only)
+    float *G[2];               // [n][K[r]]  g = dE/dB rows, consumed by the force kernel
     long long *Facc;           // [n][3] fixed point
     double *partials;          // [n_blocks][16]
     int n_part;
@@ -170,8 +171,8 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
                 cudaStream_t st);
 int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat, float *norm,
                        cudaStream_t st);
-int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st);
-int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st);
+int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
+int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, cudaStream_t st);
 struct KickArgs {

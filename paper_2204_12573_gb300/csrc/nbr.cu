@@ -712,7 +712,7 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     for (int g = 0; g < kGroups; ++g) {
         const int reg = group_region(g);
         sg.ntile_simt[g] = (2 * D.K[reg] + 143) / 144;
-        sg.nchunk_tc[g] = D.nrows_pad[reg] / 288;
+        sg.nchunk_tc[g] = 1;   // the tensor-core kernel walks the column chunks of an M-tile itself
     }
     sg.flags = nl->flags;
     k_group_scan<<<1, kScanBlock, 0, st>>>(sg);

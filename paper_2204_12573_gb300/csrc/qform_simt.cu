@@ -133,9 +133,60 @@ __global__ void __launch_bounds__(kThreads) k_qform_simt(SimtArgs a)
     }
 }
 
+// Epilogue of the SIMT path, one warp per atom: E = d . P_beta, V = d . P_Sigma,
+// sigma = sqrt(V), g = (2/||B||)(P_beta - E d)  (the tensor-core kernel does
+// this in its own epilogue).
+struct EpiArgs {
+    const int32_t *group, *row;
+    const float *norm;
+    const float *D32[2];
+    int kp32[2], K[2];
+    const float *P[2];
+    float *G[2];
+    float *energy, *variance, *sigma;
+    int n;
+};
+
+__global__ void __launch_bounds__(256) k_qform_epilogue(EpiArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * 8;
+    for (int i = blockIdx.x * 8 + (threadIdx.x >> 5); i < a.n; i += warps) {
+        const int g = a.group[i];
+        if (g < 0) continue;
+        const int reg = group_region(g), K = a.K[reg], r = a.row[i];
+        const float4 *d4 = reinterpret_cast<const float4 *>(a.D32[reg] + (size_t)r * a.kp32[reg]);
+        const float4 *p4 = reinterpret_cast<const float4 *>(a.P[reg] + (size_t)r * (2 * K));
+        float E = 0.f, V = 0.f;
+        for (int o = lane; 4 * o < K; o += 32) {
+            const float4 d = d4[o], pb = p4[o], ps = p4[K / 4 + o];
+            E += d.x * pb.x + d.y * pb.y + d.z * pb.z + d.w * pb.w;
+            V += d.x * ps.x + d.y * ps.y + d.z * ps.z + d.w * ps.w;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            E += __shfl_xor_sync(0xffffffffu, E, o);
+            V += __shfl_xor_sync(0xffffffffu, V, o);
+        }
+        const float nrm = a.norm[i];
+        const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
+        float4 *g4 = reinterpret_cast<float4 *>(a.G[reg] + (size_t)r * K);
+        for (int o = lane; 4 * o < K; o += 32) {
+            const float4 d = d4[o], pb = p4[o];
+            g4[o] = make_float4(s2 * (pb.x - E * d.x), s2 * (pb.y - E * d.y), s2 * (pb.z - E * d.z),
+                                s2 * (pb.w - E * d.w));
+        }
+        if (lane == 0) {
+            a.energy[i] = E;
+            if (a.variance) a.variance[i] = V;
+            if (a.sigma) a.sigma[i] = sqrtf(fmaxf(V, 0.f));
+        }
+    }
+}
+
 }  // namespace
 
-int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st)
+int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st)
 {
     SimtArgs a;
     for (int r = 0; r < 2; ++r) {
@@ -147,7 +198,23 @@ int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st)
     for (int g = 0; g < kGroups; ++g) a.W32[g] = ctx->W32[g];
     a.gtab = nl->gtab;
     k_qform_simt<<<ctx->num_sms * 2, kThreads, 0, st>>>(a);
-    count_launch(ctx);
+    EpiArgs e;
+    e.group = nl->group;
+    e.row = nl->row;
+    e.norm = ctx->norm;
+    for (int r = 0; r < 2; ++r) {
+        e.D32[r] = ctx->D32[r];
+        e.kp32[r] = ctx->dims.kp32[r];
+        e.K[r] = ctx->dims.K[r];
+        e.P[r] = ctx->P[r];
+        e.G[r] = ctx->G[r];
+    }
+    e.energy = out->energy;
+    e.variance = out->variance;
+    e.sigma = out->sigma;
+    e.n = nl->n;
+    k_qform_epilogue<<<persistent_grid(k_qform_epilogue, 256, ctx->num_sms, (nl->n + 7) / 8), 256, 0, st>>>(e);
+    count_launch(ctx, 2);
     return cuda_fail(cudaGetLastError(), "FP32 quadratic-form GEMM");
 }
 

@@ -1,16 +1,23 @@
-// Quadratic-form products on the 5th-generation tensor cores (tcgen05).
+// Quadratic-form products on the 5th-generation tensor cores (tcgen05),
+// with the energy / variance / gradient epilogue fused.
 //
-// Same contraction as the SIMT path, P_g = D_g [beta_g | Sigma_g] (Eq. 1,
-// Eq. 2), for tiles of 128 atoms x 288 output columns:
+// For a tile of 128 atoms of one compaction group the kernel forms
+// P = D_g [beta_g | Sigma_g] (Eq. 1, Eq. 2) 288 columns at a time:
 //   * TF32: FP32 operands read as TF32 (kind::tf32), FP32 accumulation;
 //   * 3xBF16: both operands split into BF16 hi + lo parts; the K loop runs
 //     three times (hi.hi, hi.lo, lo.hi), the lo.lo term is dropped, so the
 //     product keeps about 16 significant bits (kind::f16, FP32 accumulate).
 // Operand tiles arrive by TMA (128-byte swizzle) into a 4-stage shared
 // memory ring guarded by mbarriers; one thread issues the MMAs, which
-// accumulate in tensor memory (288 of 512 columns); four epilogue warps read
-// the accumulator back with tcgen05.ld and store P rows.  CTAs are
-// persistent, one per SM, and walk the device-side tile table.
+// accumulate in tensor memory (288 of 512 columns).  Four epilogue warps
+// read the accumulator back with tcgen05.ld, one atom (row) per thread:
+//   E = d . (beta d),  V = d . (Sigma d),  sigma = sqrt(V),
+//   g = dE/dB = (2/||B||)(beta d - E d)
+// and store E, V, sigma per atom and g as the row the force kernel needs,
+// so P itself never goes to memory.  A one-species tile (d = 144) is a
+// single 288-column chunk; a two-species tile (d = 544) takes four chunks
+// of the same CTA, the partial E and V living in the epilogue registers
+// and the beta d columns parked in the g row until E is final.
 //
 // Every wait on an mbarrier has a deadline (about 2 s of %globaltimer); on
 // expiry the kernel records FLR_ETIMEOUT in the status word, stops issuing
@@ -25,7 +32,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int NH = 144;            // N of one MMA
-constexpr int NC = 2 * NH;         // columns per tile (one accumulator)
+constexpr int NC = 2 * NH;         // columns per chunk (one accumulator)
 constexpr int kStages = 4;
 constexpr int kTileA = BM * 128;   // bytes (128-byte rows)
 constexpr int kTileB = NC * 128;
@@ -36,9 +43,15 @@ constexpr unsigned long long kDeadlineNs = 2000000000ull;
 
 struct TcArgs {
     int K[2];
-    float *P[2];
+    int kp32[2];
     int nkb[2];          // K blocks of 128 bytes per part
     int nch[kGroups];    // 288-column chunks per group
+    const float *D32[2]; // FP32 descriptor rows (epilogue dot products)
+    float *G[2];         // out: g rows [row][K]
+    const int32_t *atom_of_row;
+    int n_cap;
+    const float *norm;
+    float *energy, *variance, *sigma;
     const GroupTab *gtab;
     int *status;
 };
@@ -141,21 +154,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 }
 
 struct TileInfo {
-    int g, reg, row0, rend, chunk;
+    int g, reg, row0, rend, nch;
 };
 __device__ __forceinline__ TileInfo decode_tile(const GroupTab &T, const int *nchunks, int t)
 {
     TileInfo ti;
     int g = 0;
     while (g < kGroups - 1 && t >= T.tiles_tc[g + 1]) ++g;
-    const int local = t - T.tiles_tc[g];
-    const int nch = nchunks[g];
     ti.g = g;
     ti.reg = group_region(g);
-    ti.row0 = T.off[g] + (local / nch) * BM;
-    ti.chunk = local % nch;
+    ti.row0 = T.off[g] + (t - T.tiles_tc[g]) * BM;
     ti.rend = T.off[g] + T.count[g];
+    ti.nch = nchunks[g];
     return ti;
+}
+
+// d[c .. c+15] of a descriptor row (four float4 loads; c is a multiple of 4)
+__device__ __forceinline__ void load16(const float *p, float v[16])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 q = *reinterpret_cast<const float4 *>(p + 4 * k);
+        v[4 * k] = q.x;
+        v[4 * k + 1] = q.y;
+        v[4 * k + 2] = q.z;
+        v[4 * k + 3] = q.w;
+    }
 }
 
 template <bool BF16>
@@ -210,22 +234,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 const TileInfo ti = decode_tile(T, a.nch, t);
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
-                for (int kb = 0; kb < nkt; ++kb) {
-                    const int part = BF16 ? kb / nkb : 0;
-                    const int kk = BF16 ? kb % nkb : kb;
-                    if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
-                    const uint32_t fb = full0 + 8 * stage;
-                    mbar_expect_tx(fb, kStageBytes);
-                    const int x = kk * (BF16 ? 64 : 32);
-                    const CUtensorMap *am = &maps.a[ti.reg][(BF16 && part == 2) ? 1 : 0];
-                    const CUtensorMap *bm = &maps.b[ti.g][(BF16 && part == 1) ? 1 : 0];
-                    const uint32_t da = smem_u32(sA + stage * kTileA);
-                    const uint32_t db = smem_u32(sB + stage * kTileB);
-                    tma_load_2d(da, am, x, ti.row0, fb);
-                    tma_load_2d(db, bm, x, ti.chunk * NC, fb);
-                    tma_load_2d(db + NH * 128, bm, x, ti.chunk * NC + NH, fb);
-                    last_phase[stage] = (int)phase;
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                for (int ch = 0; ch < ti.nch && ok; ++ch) {
+                    for (int kb = 0; kb < nkt; ++kb) {
+                        const int part = BF16 ? kb / nkb : 0;
+                        const int kk = BF16 ? kb % nkb : kb;
+                        if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
+                        const uint32_t fb = full0 + 8 * stage;
+                        mbar_expect_tx(fb, kStageBytes);
+                        const int x = kk * (BF16 ? 64 : 32);
+                        const CUtensorMap *am = &maps.a[ti.reg][(BF16 && part == 2) ? 1 : 0];
+                        const CUtensorMap *bm = &maps.b[ti.g][(BF16 && part == 1) ? 1 : 0];
+                        const uint32_t da = smem_u32(sA + stage * kTileA);
+                        const uint32_t db = smem_u32(sB + stage * kTileB);
+                        tma_load_2d(da, am, x, ti.row0, fb);
+                        tma_load_2d(db, bm, x, ch * NC, fb);
+                        tma_load_2d(db + NH * 128, bm, x, ch * NC + NH, fb);
+                        last_phase[stage] = (int)phase;
+                        if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    }
                 }
             }
             if (!ok) {
@@ -249,33 +275,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                                    ((uint32_t)(BM >> 4) << 24);
             int stage = 0;
             uint32_t phase = 0;
-            int it = 0;
+            int it = 0;   // accumulator uses (chunks)
             bool ok = true;
             bool issued = false;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const TileInfo ti = decode_tile(T, a.nch, t);
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
-                if (!mbar_wait(tempty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
-                fence_after();
-                for (int kb = 0; kb < nkt; ++kb) {
-                    if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
+                for (int ch = 0; ch < ti.nch && ok; ++ch, ++it) {
+                    if (!mbar_wait(tempty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
                     fence_after();
-                    const uint32_t da = smem_u32(sA + stage * kTileA);
-                    const uint32_t db = smem_u32(sB + stage * kTileB);
-                    const uint64_t ad = sw128_desc(da);
-                    const uint64_t bd0 = sw128_desc(db), bd1 = sw128_desc(db + NH * 128);
+                    for (int kb = 0; kb < nkt; ++kb) {
+                        if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t da = smem_u32(sA + stage * kTileA);
+                        const uint32_t db = smem_u32(sB + stage * kTileB);
+                        const uint64_t ad = sw128_desc(da);
+                        const uint64_t bd0 = sw128_desc(db), bd1 = sw128_desc(db + NH * 128);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint32_t accum = (kb | ks) != 0;
-                        mma<BF16>(tmem, ad + 2 * ks, bd0 + 2 * ks, idesc, accum);
-                        mma<BF16>(tmem + NH, ad + 2 * ks, bd1 + 2 * ks, idesc, accum);
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint32_t accum = (kb | ks) != 0;
+                            mma<BF16>(tmem, ad + 2 * ks, bd0 + 2 * ks, idesc, accum);
+                            mma<BF16>(tmem + NH, ad + 2 * ks, bd1 + 2 * ks, idesc, accum);
+                        }
+                        issued = true;
+                        mma_commit(empty0 + 8 * stage);
+                        if (++stage == kStages) { stage = 0; phase ^= 1; }
                     }
-                    issued = true;
-                    mma_commit(empty0 + 8 * stage);
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    if (ok) mma_commit(tfull);
                 }
-                if (ok) mma_commit(tfull);
             }
             if (!ok) {
                 atomicOr(a.status, kErrTimeout);
@@ -290,47 +318,115 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             }
         }
     } else {
-        // ---------------- epilogue: TMEM -> registers -> P ----------------
+        // ---------------- epilogue: TMEM -> E, V, sigma, g ----------------
         const int qw = warp & 3;                // TMEM lane quarter of this warp
+        const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
         int it = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+        bool alive = true;
+        for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
             const TileInfo ti = decode_tile(T, a.nch, t);
-            // lane 0 waits and the warp follows its verdict, so the warp stays converged
-            int okw = 1;
-            if (lane == 0) okw = mbar_wait(tfull, (uint32_t)(it & 1), abort_flag) ? 1 : 0;
-            okw = __shfl_sync(0xffffffffu, okw, 0);
-            if (!okw) {
-                if (lane == 0) {
-                    atomicOr(a.status, kErrTimeout);
-                    *abort_flag = 1;
-                }
-                break;
-            }
-            fence_after();
-            const int N2 = 2 * a.K[ti.reg];
+            const int K = a.K[ti.reg];
             const int row = ti.row0 + qw * 32 + lane;
-            float *prow = a.P[ti.reg] + (size_t)row * N2;
-            const int c0 = ti.chunk * NC;
+            const bool valid = row < ti.rend;
+            const int atom = valid ? a.atom_of_row[(size_t)ti.reg * a.n_cap + row] : 0;
+            const float nrm = valid ? a.norm[atom] : 0.f;
+            const float *d = a.D32[ti.reg] + (size_t)(valid ? row : 0) * a.kp32[ti.reg];
+            float *grow = a.G[ti.reg] + (size_t)(valid ? row : 0) * K;
+            const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
+            float E = 0.f, V = 0.f;
+            for (int ch = 0; ch < ti.nch; ++ch, ++it) {
+                // lane 0 waits and the warp follows its verdict, so the warp stays converged
+                int okw = 1;
+                if (lane == 0) okw = mbar_wait(tfull, (uint32_t)(it & 1), abort_flag) ? 1 : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) {
+                    if (lane == 0) {
+                        atomicOr(a.status, kErrTimeout);
+                        *abort_flag = 1;
+                    }
+                    alive = false;
+                    break;
+                }
+                fence_after();
+                const int c0 = ch * NC;
 #pragma unroll 1
-            for (int c = 0; c < NC; c += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)c, v);
-                if (row < ti.rend) {
-                    const int col = c0 + c;
-                    if (col + 16 <= N2) {
+                for (int c = 0; c < NC; c += 16) {
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)c, v);
+                    const int cg = c0 + c;
+                    if (valid && cg < 2 * K) {
+                        if (cg + 16 <= K) {                       // beta d columns
+                            float dv[16];
+                            load16(d + cg, dv);
 #pragma unroll
-                        for (int k = 0; k < 16; k += 4)
-                            *reinterpret_cast<float4 *>(prow + col + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-                    } else {
+                            for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
+                            if (ti.nch > 1) {
 #pragma unroll
-                        for (int k = 0; k < 16; ++k)
-                            if (col + k < N2) prow[col + k] = v[k];
+                                for (int k = 0; k < 16; k += 4)
+                                    *reinterpret_cast<float4 *>(grow + cg + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                            }
+                        } else if (cg >= K && cg + 16 <= 2 * K) { // Sigma d columns
+                            float dv[16];
+                            load16(d + cg - K, dv);
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) V += dv[k] * v[k];
+                        } else {                                  // a group straddling K or 2K
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                const int cc = cg + k;
+                                if (cc < K) {
+                                    E += d[cc] * v[k];
+                                    if (ti.nch > 1) grow[cc] = v[k];
+                                } else if (cc < 2 * K) {
+                                    V += d[cc - K] * v[k];
+                                }
+                            }
+                        }
                     }
                 }
+                if (ti.nch == 1) {
+                    // one chunk: E is final, read beta d again and emit g directly
+                    // (every lane issues the same tcgen05.ld sequence; only valid rows store)
+#pragma unroll 1
+                    for (int c = 0; c < K; c += 16) {
+                        float v[16];
+                        tmem_ld16(tbase + (uint32_t)c, v);
+                        if (!valid) continue;
+                        if (c + 16 <= K) {
+                            float dv[16];
+                            load16(d + c, dv);
+#pragma unroll
+                            for (int k = 0; k < 16; k += 4)
+                                *reinterpret_cast<float4 *>(grow + c + k) =
+                                    make_float4(s2 * (v[k] - E * dv[k]), s2 * (v[k + 1] - E * dv[k + 1]),
+                                                s2 * (v[k + 2] - E * dv[k + 2]), s2 * (v[k + 3] - E * dv[k + 3]));
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k)
+                                if (c + k < K) grow[c + k] = s2 * (v[k] - E * d[c + k]);
+                        }
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty);
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty);
+            if (!alive) break;
+            if (valid) {
+                if (ti.nch > 1) {
+                    // several chunks: fix the parked beta d columns up into g
+                    for (int k = 0; k < K; k += 4) {
+                        const float4 p = *reinterpret_cast<const float4 *>(grow + k);
+                        const float4 q = *reinterpret_cast<const float4 *>(d + k);
+                        *reinterpret_cast<float4 *>(grow + k) =
+                            make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
+                                        s2 * (p.w - E * q.w));
+                    }
+                }
+                a.energy[atom] = E;
+                if (a.variance) a.variance[atom] = V;
+                if (a.sigma) a.sigma[atom] = sqrtf(fmaxf(V, 0.f));
+            }
         }
     }
     fence_before();
@@ -418,7 +514,7 @@ int ensure_maps(flr_ctx *ctx)
 
 }  // namespace
 
-int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st)
+int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st)
 {
     int s = ensure_maps(ctx);
     if (s != FLR_OK) return s;
@@ -426,10 +522,18 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, cudaStream_t st)
     TcArgs a;
     for (int r = 0; r < 2; ++r) {
         a.K[r] = ctx->dims.K[r];
-        a.P[r] = ctx->P[r];
+        a.kp32[r] = ctx->dims.kp32[r];
         a.nkb[r] = bf16 ? ctx->dims.kp64[r] / 64 : ctx->dims.kp32[r] / 32;
+        a.D32[r] = ctx->D32[r];
+        a.G[r] = ctx->G[r];
     }
     for (int g = 0; g < kGroups; ++g) a.nch[g] = ctx->dims.nrows_pad[group_region(g)] / NC;
+    a.atom_of_row = nl->atom_of_row;
+    a.n_cap = nl->n_cap;
+    a.norm = ctx->norm;
+    a.energy = out->energy;
+    a.variance = out->variance;
+    a.sigma = out->sigma;
     a.gtab = nl->gtab;
     a.status = ctx->status;
     const size_t smem = 1024 + (size_t)kStages * kStageBytes + 256;
