@@ -309,37 +309,49 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             *reinterpret_cast<float4 *>(sA + ch * kAStride + 4 * (k & 3)) = used ? Ag[k] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();
-        // w = G~ A over the class's channels -> slot layout [species][lm][n]
+        // w = G~ A over the class's channels -> slot layout [species][lm][n].
+        // Lane (lm = lane & 15, half = lane >> 4) owns harmonic lm of half of
+        // the class's channels; each A[b][lm] is loaded once and used for all
+        // of them, and G~[a][b][l] is walked with incremental triangular indices.
         {
             const int Cg = cls == 0 ? C : N;
             const int choff = cls == 0 ? 0 : (cls - 1) * N;
             float *ws = sm.W[w] + slot * kWSlot;
-            const int my_n = lane >> 2, quad = lane & 3;
-            // l of the four harmonics owned by this lane: quad 0 -> 0,1,1,1; 1 -> 2,2,2,2; 2 -> 2,3,3,3; 3 -> 3
-            for (int blk = 0; blk < 2; ++blk) {
-                float acc[4] = {0.f, 0.f, 0.f, 0.f};
-                const bool active = my_n < N && (cls == 0 || blk == cls - 1);
-                if (active) {
-                    const int aloc = (cls == 0 ? blk * N : 0) + my_n;
-                    for (int bloc = 0; bloc < Cg; ++bloc) {
-                        const int lo = min(aloc, bloc), hi = max(aloc, bloc);
-                        const float4 gl = *reinterpret_cast<const float4 *>(sG + 4 * tri(lo, hi, Cg));
-                        const float4 av = *reinterpret_cast<const float4 *>(sA + (choff + bloc) * kAStride + 4 * quad);
-                        const float dbl = aloc == bloc ? 2.f : 1.f;
-                        float g0, g1, g2, g3;
-                        if (quad == 0) { g0 = gl.x; g1 = gl.y; g2 = gl.y; g3 = gl.y; }
-                        else if (quad == 1) { g0 = gl.z; g1 = gl.z; g2 = gl.z; g3 = gl.z; }
-                        else if (quad == 2) { g0 = gl.z; g1 = gl.w; g2 = gl.w; g3 = gl.w; }
-                        else { g0 = gl.w; g1 = gl.w; g2 = gl.w; g3 = gl.w; }
-                        acc[0] += dbl * g0 * av.x;
-                        acc[1] += dbl * g1 * av.y;
-                        acc[2] += dbl * g2 * av.z;
-                        acc[3] += dbl * g3 * av.w;
+            const int lm = lane & 15, half = lane >> 4;
+            const int l = l_of(lm);
+            constexpr int MAXA = N;                       // channels per lane (mixed class: N, one species: <= N/2 + 1)
+            const int per = (Cg + 1) / 2;
+            const int a0 = half * per;
+            const int na = min(per, Cg - a0);
+            float acc[MAXA];
+#pragma unroll
+            for (int k = 0; k < MAXA; ++k) acc[k] = 0.f;
+            // idx[k]: triangular index of (min(a, b), max(a, b)) for a = a0 + k, starting at b = 0
+            int idx[MAXA];
+#pragma unroll
+            for (int k = 0; k < MAXA; ++k) idx[k] = a0 + k;   // tri(0, a) = a
+            for (int b = 0; b < Cg; ++b) {
+                const float av = sA[(choff + b) * kAStride + lm];
+#pragma unroll
+                for (int k = 0; k < MAXA; ++k) {
+                    if (k < na) {
+                        const int a_ = a0 + k;
+                        const float gv = sG[4 * idx[k] + l];
+                        acc[k] += (a_ == b ? 2.f * gv : gv) * av;
+                        // advance to b + 1: below the diagonal the row of b grows by (Cg - b - 1),
+                        // on and after it the column index just steps
+                        idx[k] += (b < a_) ? (Cg - b - 1) : 1;
                     }
                 }
-                if (my_n < 8) {
+            }
+            // zero both species blocks of the slot, then place this class's w
+            for (int k = lane; k < 256; k += 32) ws[k] = 0.f;
+            __syncwarp();
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) ws[blk * 128 + (4 * quad + k) * 8 + my_n] = (my_n < N) ? acc[k] : 0.f;
+            for (int k = 0; k < MAXA; ++k) {
+                if (k < na) {
+                    const int ch = choff + a0 + k;            // channel = species * N + n
+                    ws[(ch / N) * 128 + lm * 8 + (ch % N)] = acc[k];
                 }
             }
         }

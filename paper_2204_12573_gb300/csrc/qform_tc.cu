@@ -348,80 +348,77 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     break;
                 }
                 fence_after();
-                const int c0 = ch * NC;
+                if (ti.nch == 1 && (K % 16) == 0 && 2 * K <= NC) {
+                    // one chunk holding [beta d | Sigma d]: read both halves together,
+                    // one load of d serves E and V; beta d is parked in the g row
 #pragma unroll 1
-                for (int c = 0; c < NC; c += 16) {
-                    float v[16];
-                    tmem_ld16(tbase + (uint32_t)c, v);
-                    const int cg = c0 + c;
-                    if (valid && cg < 2 * K) {
-                        if (cg + 16 <= K) {                       // beta d columns
+                    for (int c = 0; c < K; c += 16) {
+                        float vb[16], vs[16];
+                        tmem_ld16(tbase + (uint32_t)c, vb);
+                        tmem_ld16(tbase + (uint32_t)(K + c), vs);
+                        if (valid) {
                             float dv[16];
-                            load16(d + cg, dv);
+                            load16(d + c, dv);
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
-                            if (ti.nch > 1) {
+                            for (int k = 0; k < 16; ++k) {
+                                E += dv[k] * vb[k];
+                                V += dv[k] * vs[k];
+                            }
+#pragma unroll
+                            for (int k = 0; k < 16; k += 4)
+                                *reinterpret_cast<float4 *>(grow + c + k) = make_float4(vb[k], vb[k + 1], vb[k + 2], vb[k + 3]);
+                        }
+                    }
+                } else {
+                    const int c0 = ch * NC;
+#pragma unroll 1
+                    for (int c = 0; c < NC; c += 16) {
+                        float v[16];
+                        tmem_ld16(tbase + (uint32_t)c, v);
+                        const int cg = c0 + c;
+                        if (valid && cg < 2 * K) {
+                            if (cg + 16 <= K) {                       // beta d columns
+                                float dv[16];
+                                load16(d + cg, dv);
+#pragma unroll
+                                for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
 #pragma unroll
                                 for (int k = 0; k < 16; k += 4)
                                     *reinterpret_cast<float4 *>(grow + cg + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-                            }
-                        } else if (cg >= K && cg + 16 <= 2 * K) { // Sigma d columns
-                            float dv[16];
-                            load16(d + cg - K, dv);
+                            } else if (cg >= K && cg + 16 <= 2 * K) { // Sigma d columns
+                                float dv[16];
+                                load16(d + cg - K, dv);
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) V += dv[k] * v[k];
-                        } else {                                  // a group straddling K or 2K
+                                for (int k = 0; k < 16; ++k) V += dv[k] * v[k];
+                            } else {                                  // a group straddling K or 2K
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                const int cc = cg + k;
-                                if (cc < K) {
-                                    E += d[cc] * v[k];
-                                    if (ti.nch > 1) grow[cc] = v[k];
-                                } else if (cc < 2 * K) {
-                                    V += d[cc - K] * v[k];
+                                for (int k = 0; k < 16; ++k) {
+                                    const int cc = cg + k;
+                                    if (cc < K) {
+                                        E += d[cc] * v[k];
+                                        grow[cc] = v[k];
+                                    } else if (cc < 2 * K) {
+                                        V += d[cc - K] * v[k];
+                                    }
                                 }
                             }
                         }
                     }
                 }
-                if (ti.nch == 1) {
-                    // one chunk: E is final, read beta d again and emit g directly
-                    // (every lane issues the same tcgen05.ld sequence; only valid rows store)
-#pragma unroll 1
-                    for (int c = 0; c < K; c += 16) {
-                        float v[16];
-                        tmem_ld16(tbase + (uint32_t)c, v);
-                        if (!valid) continue;
-                        if (c + 16 <= K) {
-                            float dv[16];
-                            load16(d + c, dv);
-#pragma unroll
-                            for (int k = 0; k < 16; k += 4)
-                                *reinterpret_cast<float4 *>(grow + c + k) =
-                                    make_float4(s2 * (v[k] - E * dv[k]), s2 * (v[k + 1] - E * dv[k + 1]),
-                                                s2 * (v[k + 2] - E * dv[k + 2]), s2 * (v[k + 3] - E * dv[k + 3]));
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 16; ++k)
-                                if (c + k < K) grow[c + k] = s2 * (v[k] - E * d[c + k]);
-                        }
-                    }
-                }
+                // the accumulator is free again: the next MMAs overlap the fix-up below
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty);
             }
             if (!alive) break;
             if (valid) {
-                if (ti.nch > 1) {
-                    // several chunks: fix the parked beta d columns up into g
-                    for (int k = 0; k < K; k += 4) {
-                        const float4 p = *reinterpret_cast<const float4 *>(grow + k);
-                        const float4 q = *reinterpret_cast<const float4 *>(d + k);
-                        *reinterpret_cast<float4 *>(grow + k) =
-                            make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
-                                        s2 * (p.w - E * q.w));
-                    }
+                // g = (2/||B||)(beta d - E d) from the parked beta d columns
+                for (int k = 0; k < K; k += 4) {
+                    const float4 p = *reinterpret_cast<const float4 *>(grow + k);
+                    const float4 q = *reinterpret_cast<const float4 *>(d + k);
+                    *reinterpret_cast<float4 *>(grow + k) =
+                        make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
+                                    s2 * (p.w - E * q.w));
                 }
                 a.energy[atom] = E;
                 if (a.variance) a.variance[atom] = V;
