@@ -193,6 +193,44 @@ __device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, in
     __syncwarp();
 }
 
+// w_{a,lm} = sum_b G~_{ab,l} A_{b,lm} for the channels a0 .. a0+na-1 (na <= NA)
+// of a class with Cg channels, harmonic lm of this lane.  G~ is read with
+// triangular indices kept incrementally per channel.
+template <int NA, int N>
+__device__ __forceinline__ void w_channels(const float *sG, const float *sA, float *ws, int Cg, int choff, int a0,
+                                           int na, int lm)
+{
+    const int l = l_of(lm);
+    float acc[NA];
+    int idx[NA];   // tri(min(a, b), max(a, b)) for a = a0 + k at the current b
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        acc[k] = 0.f;
+        idx[k] = a0 + k;   // tri(0, a) = a
+    }
+    for (int b = 0; b < Cg; ++b) {
+        const float av = sA[(choff + b) * kAStride + lm];
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            if (k < na) {
+                const int a_ = a0 + k;
+                const float gv = sG[4 * idx[k] + l];
+                acc[k] += (a_ == b ? 2.f * gv : gv) * av;
+                // step to b + 1: above the diagonal the row of b grows by (Cg - b - 1),
+                // from the diagonal on the column index just steps
+                idx[k] += (b < a_) ? (Cg - b - 1) : 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        if (k < na) {
+            const int ch = choff + a0 + k;            // channel = species * N + n
+            ws[(ch / N) * 128 + lm * 8 + (ch % N)] = acc[k];
+        }
+    }
+}
+
 // Per-atom values loaded one iteration ahead, so their latency overlaps the
 // previous atom's work.
 struct AtomPre {
@@ -318,42 +356,16 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             const int choff = cls == 0 ? 0 : (cls - 1) * N;
             float *ws = sm.W[w] + slot * kWSlot;
             const int lm = lane & 15, half = lane >> 4;
-            const int l = l_of(lm);
-            constexpr int MAXA = N;                       // channels per lane (mixed class: N, one species: <= N/2 + 1)
             const int per = (Cg + 1) / 2;
             const int a0 = half * per;
             const int na = min(per, Cg - a0);
-            float acc[MAXA];
-#pragma unroll
-            for (int k = 0; k < MAXA; ++k) acc[k] = 0.f;
-            // idx[k]: triangular index of (min(a, b), max(a, b)) for a = a0 + k, starting at b = 0
-            int idx[MAXA];
-#pragma unroll
-            for (int k = 0; k < MAXA; ++k) idx[k] = a0 + k;   // tri(0, a) = a
-            for (int b = 0; b < Cg; ++b) {
-                const float av = sA[(choff + b) * kAStride + lm];
-#pragma unroll
-                for (int k = 0; k < MAXA; ++k) {
-                    if (k < na) {
-                        const int a_ = a0 + k;
-                        const float gv = sG[4 * idx[k] + l];
-                        acc[k] += (a_ == b ? 2.f * gv : gv) * av;
-                        // advance to b + 1: below the diagonal the row of b grows by (Cg - b - 1),
-                        // on and after it the column index just steps
-                        idx[k] += (b < a_) ? (Cg - b - 1) : 1;
-                    }
-                }
-            }
             // zero both species blocks of the slot, then place this class's w
             for (int k = lane; k < 256; k += 32) ws[k] = 0.f;
             __syncwarp();
-#pragma unroll
-            for (int k = 0; k < MAXA; ++k) {
-                if (k < na) {
-                    const int ch = choff + a0 + k;            // channel = species * N + n
-                    ws[(ch / N) * 128 + lm * 8 + (ch % N)] = acc[k];
-                }
-            }
+            if (cls == 0)
+                w_channels<N, N>(sG, sA, ws, Cg, choff, a0, na, lm);
+            else
+                w_channels<(N + 1) / 2, N>(sG, sA, ws, Cg, choff, a0, na, lm);
         }
         __syncwarp();
 

@@ -169,12 +169,13 @@ __device__ __forceinline__ TileInfo decode_tile(const GroupTab &T, const int *nc
     return ti;
 }
 
-// d[c .. c+15] of a descriptor row (four float4 loads; c is a multiple of 4)
+// d[c .. c+15] of a descriptor row (four float4 loads through the read-only
+// path, so they may be issued ahead of the g-row stores; c is a multiple of 4)
 __device__ __forceinline__ void load16(const float *p, float v[16])
 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float4 q = *reinterpret_cast<const float4 *>(p + 4 * k);
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p + 4 * k));
         v[4 * k] = q.x;
         v[4 * k + 1] = q.y;
         v[4 * k + 2] = q.z;
@@ -395,10 +396,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                                 for (int k = 0; k < 16; ++k) {
                                     const int cc = cg + k;
                                     if (cc < K) {
-                                        E += d[cc] * v[k];
+                                        E += __ldg(d + cc) * v[k];
                                         grow[cc] = v[k];
                                     } else if (cc < 2 * K) {
-                                        V += d[cc - K] * v[k];
+                                        V += __ldg(d + cc - K) * v[k];
                                     }
                                 }
                             }
@@ -413,12 +414,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             if (!alive) break;
             if (valid) {
                 // g = (2/||B||)(beta d - E d) from the parked beta d columns
-                for (int k = 0; k < K; k += 4) {
-                    const float4 p = *reinterpret_cast<const float4 *>(grow + k);
-                    const float4 q = *reinterpret_cast<const float4 *>(d + k);
-                    *reinterpret_cast<float4 *>(grow + k) =
-                        make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
-                                    s2 * (p.w - E * q.w));
+                float4 *g4 = reinterpret_cast<float4 *>(grow);
+                const float4 *d4 = reinterpret_cast<const float4 *>(d);
+#pragma unroll 4
+                for (int k = 0; k < K / 4; ++k) {
+                    const float4 p = g4[k];
+                    const float4 q = __ldg(d4 + k);
+                    g4[k] = make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
+                                        s2 * (p.w - E * q.w));
                 }
                 a.energy[atom] = E;
                 if (a.variance) a.variance[atom] = V;
