@@ -201,6 +201,32 @@ int flr_sync(flr_ctx *ctx, flr_stream_t stream);
 /* Number of kernels the library launched on this context so far. */
 int64_t flr_launch_count(const flr_ctx *ctx);
 
+/* Cell-list neighbour search that allocates no memory.  (No counterpart in
+ * the paper: this is a deployment variant of flr_build_neighbors.)
+ *
+ * For callers that cannot call cudaMalloc: a process whose device memory is
+ * fixed at start-up (a serving process that reserves its whole budget once,
+ * or a host framework that owns every device allocation through its own
+ * pool), or a caller that holds no flr_ctx.  Inputs and outputs are the
+ * caller's: sys (as for flr_build_neighbors), r_list = list cutoff
+ * (r_cut + skin, A), max_nbr (multiple of 32 in [32, 512]), entries: device
+ * int32[n][max_nbr] and count: device int32[n], in the format of
+ * flr_nbrlist_view.  Rows hold the same pairs in the same order as
+ * flr_build_neighbors with r_cut + skin = r_list.
+ *
+ * Every other buffer lives in one fixed device array inside the library
+ * (about 2.6 MB, held by every GPU that loads the library until the process
+ * exits), so the sizes are bounded: at most 65,536 atoms and 65,536 cell-list
+ * bins; larger inputs return FLR_EINVAL with a message naming the limit.
+ * The first call on a device looks up the array's device address with that
+ * device current (make that first call before any stream capture).  All
+ * calls share the array, so calls whose GPU work overlaps (several host
+ * threads, or several streams) race; serialize them.  The call synchronizes
+ * the stream twice (bounding box, then status) and returns
+ * FLR_ENBR_OVERFLOW when a row exceeds max_nbr. */
+int flr_build_neighbors_noalloc(const flr_system *sys, double r_list, int32_t max_nbr, int32_t *entries,
+                                int32_t *count, flr_stream_t stream);
+
 /* Kernel classes of flr_profile_read. */
 #define FLR_KERNEL_DESCRIPTOR 0   /* A, B2, normalization (one launch per evaluation) */
 #define FLR_KERNEL_QFORM 1        /* quadratic-form GEMM (SIMT or tcgen05) */

@@ -37,7 +37,7 @@ EXPORTED = [
     "flr_set_precision", "flr_set_model", "flr_nbrlist_create", "flr_nbrlist_destroy",
     "flr_nbrlist_view", "flr_build_neighbors", "flr_compute_descriptors",
     "flr_energy_forces_uncertainty", "flr_md_step", "flr_sync", "flr_launch_count",
-    "flr_profile_enable", "flr_profile_read",
+    "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
@@ -102,6 +102,8 @@ def lib():
             "flr_sync": (ctypes.c_int, [P, P]),
             "flr_launch_count": (ctypes.c_int64, [P]),
             "flr_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
+            "flr_build_neighbors_noalloc": (ctypes.c_int, [ctypes.POINTER(System), ctypes.c_double, ctypes.c_int32,
+                                                           P, P, P]),
             "flr_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_int64)]),
         }

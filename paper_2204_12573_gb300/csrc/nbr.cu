@@ -724,3 +724,247 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
 }
 
 }  // namespace flr
+
+// ---------------------------------------------------------------------------
+// Neighbour build that allocates nothing (flr_build_neighbors_noalloc).
+//
+// Some callers cannot call cudaMalloc: applications whose device memory is
+// fixed at start-up (a serving process that reserves its whole budget once,
+// or a host framework that owns every device allocation through its own
+// pool) and callers that hold no library context.  This entry point runs the
+// same cell-list kernels as flr_build_neighbors, but every buffer besides the
+// caller's inputs and outputs (bin counts and starts, the per-atom bin and
+// image tables, the bin-sorted atom order, scan block sums, the status word)
+// lives in one file-scope device array of fixed size, kNoAllocBytes (about
+// 2.6 MB), that each GPU loading this library keeps until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace flr {
+namespace {
+
+constexpr int kNoAllocMaxAtoms = 1 << 16;
+constexpr int kNoAllocMaxBins = 1 << 16;
+constexpr size_t kNoAllocBytes =
+    (size_t)kNoAllocMaxAtoms * (5 * sizeof(int32_t) + sizeof(float4)) +   // bin, img, sorted atoms, group, spare; pos_ref
+    (size_t)2 * (kNoAllocMaxBins + 2) * sizeof(int32_t) +                  // bin starts, bin fill
+    (size_t)(kNoAllocMaxBins / kScanBlock + 2) * sizeof(int32_t) +         // scan block sums
+    4096;                                                                   // flags, status, bbox, group table
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256];   // device address of g_noalloc_scratch, per device ordinal
+
+}  // namespace
+}  // namespace flr
+
+// The scratch itself.  Host code must not use this name as a pointer (on the
+// host it is only a stand-in symbol); the device address comes from
+// cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[flr::kNoAllocBytes];
+
+extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list, int32_t max_nbr, int32_t *entries,
+                                           int32_t *count, flr_stream_t stream)
+{
+    using namespace flr;
+    if (!sys || sys->n_atoms < 0 || !(r_list > 0.0) || max_nbr < 32 || max_nbr > 512 || max_nbr % 32) {
+        set_error("flr_build_neighbors_noalloc: invalid argument (r_list > 0, max_nbr a multiple of 32 in [32, 512])");
+        return FLR_EINVAL;
+    }
+    const int n = sys->n_atoms;
+    if (n > kNoAllocMaxAtoms) {
+        set_error("flr_build_neighbors_noalloc: " + std::to_string(n) + " atoms exceed the fixed scratch limit of " +
+                  std::to_string(kNoAllocMaxAtoms) + "; use flr_build_neighbors");
+        return FLR_EINVAL;
+    }
+    if (n > 0 && (!sys->pos || !sys->species || !entries || !count)) {
+        set_error("flr_build_neighbors_noalloc: null pointer");
+        return FLR_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(sys->pos) % 16) {
+        set_error("flr_build_neighbors_noalloc: pos must be 16-byte aligned float[n][4]");
+        return FLR_EINVAL;
+    }
+    if (n == 0) return FLR_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    int s = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != FLR_OK) return s;
+    if (dev < 0 || dev >= 256) {
+        set_error("flr_build_neighbors_noalloc: device ordinal out of range");
+        return FLR_EINVAL;
+    }
+    // once per device, with that device current: the device address of the scratch array
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+            g_noalloc_ptr[dev] = p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    int num_sms = 1;
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+    // carve the scratch
+    unsigned char *q = static_cast<unsigned char *>(base);
+    auto take = [&q](size_t bytes) {
+        unsigned char *p = q;
+        q += (bytes + 255) & ~size_t(255);
+        return p;
+    };
+    int32_t *atom_bin = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * kNoAllocMaxAtoms));
+    int32_t *img = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * kNoAllocMaxAtoms));
+    int32_t *bin_atoms = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * kNoAllocMaxAtoms));
+    int32_t *group = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * kNoAllocMaxAtoms));
+    float4 *pos_ref = reinterpret_cast<float4 *>(take(sizeof(float4) * kNoAllocMaxAtoms));
+    int32_t *bin_start = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (kNoAllocMaxBins + 2)));
+    int32_t *bin_fill = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (kNoAllocMaxBins + 2)));
+    int32_t *bsums = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (kNoAllocMaxBins / kScanBlock + 2)));
+    int32_t *flags = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * 4));
+    int *status = reinterpret_cast<int *>(take(sizeof(int) * 4));
+    float *bbox = reinterpret_cast<float *>(take(sizeof(float) * 8));
+    GroupTab *gtab = reinterpret_cast<GroupTab *>(take(sizeof(GroupTab)));
+    if (q > static_cast<unsigned char *>(base) + kNoAllocBytes) {
+        set_error("flr_build_neighbors_noalloc: scratch layout exceeds the array");
+        return FLR_EINVAL;
+    }
+
+    // bin grid from the fractional bounding box (host reads six floats)
+    Plan P;
+    for (int k = 0; k < 9; ++k) P.cell[k] = sys->cell[k];
+    inverse3(sys->cell, P.inv);
+    if (!std::isfinite(P.inv[0]) || !std::isfinite(P.inv[4]) || !std::isfinite(P.inv[8])) {
+        set_error("flr_build_neighbors_noalloc: singular cell");
+        return FLR_EINVAL;
+    }
+    InvArg inv;
+    for (int c = 0; c < 9; ++c) inv.m[c] = P.inv[c];
+    const float4 *pos = reinterpret_cast<const float4 *>(sys->pos);
+    k_bbox_init<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox));
+    k_bbox<<<std::max(1, std::min((n + 255) / 256, num_sms * 8)), 256, 0, st>>>(pos, n, inv,
+                                                                              reinterpret_cast<int *>(bbox));
+    k_bbox_finish<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox));
+    float bb[6];
+    s = cuda_fail(cudaMemcpyAsync(bb, bbox, sizeof(bb), cudaMemcpyDeviceToHost, st), "bbox");
+    if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "bbox");
+    if (s != FLR_OK) return s;
+    const double margin = 2.0 * r_list;
+    long long nbins = 1;
+    for (int d = 0; d < 3; ++d) {
+        const double wd = width(sys->cell, d);
+        double flo = 0.0, fspan = 1.0;
+        P.pbc[d] = sys->pbc[d] ? 1 : 0;
+        if (!sys->pbc[d]) {
+            double lo = bb[d], hi = bb[3 + d];
+            if (!(hi >= lo)) { lo = 0.0; hi = 0.0; }
+            flo = lo - margin / wd;
+            fspan = (hi - lo) + 2.0 * margin / wd;
+        }
+        const double extent = fspan * wd;
+        int nb = (int)std::floor(extent / (r_list * 1.0001));
+        nb = std::max(1, std::min(nb, 4096));
+        int R = (int)std::ceil(r_list / (extent / nb) * (1.0 + 1e-6));
+        if (!sys->pbc[d]) R = std::min(R, nb);
+        if (sys->pbc[d] && R > 2 * nb + 1) {
+            set_error("flr_build_neighbors_noalloc: periodic cell too narrow for r_list");
+            return FLR_EINVAL;
+        }
+        P.nb[d] = nb;
+        P.R[d] = R;
+        P.flo[d] = (float)flo;
+        P.fspan[d] = (float)fspan;
+        nbins *= nb;
+    }
+    if (nbins > kNoAllocMaxBins) {
+        set_error("flr_build_neighbors_noalloc: the bin grid needs " + std::to_string(nbins) +
+                  " bins, above the fixed scratch limit of " + std::to_string(kNoAllocMaxBins));
+        return FLR_EINVAL;
+    }
+    // the array keeps the previous call's contents: reset what must start at zero
+    s = cuda_fail(cudaMemsetAsync(status, 0, sizeof(int) * 4, st), "reset scratch");
+    if (s == FLR_OK) s = cuda_fail(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, st), "reset scratch");
+    if (s == FLR_OK) s = cuda_fail(cudaMemsetAsync(flags, 1, 1, st), "reset scratch");   // rebuild flag on
+    if (s != FLR_OK) return s;
+
+    CellArg cell;
+    for (int c = 0; c < 9; ++c) cell.c[c] = P.cell[c];
+    k_zero_bins<<<std::max(1, (int)std::min<long long>((nbins + 255) / 256, 65535)), 256, 0, st>>>(bin_fill, nbins,
+                                                                                                   flags);
+    BinArgs b;
+    b.pos = pos;
+    b.pos_mut = nullptr;
+    b.n = n;
+    b.inv = inv;
+    b.cell = cell;
+    for (int d = 0; d < 3; ++d) {
+        b.nb[d] = P.nb[d];
+        b.pbc[d] = P.pbc[d];
+        b.flo[d] = P.flo[d];
+        b.fspan[d] = P.fspan[d];
+    }
+    b.atom_bin = atom_bin;
+    b.img = img;
+    b.bin_count = bin_fill;
+    b.pos_ref = pos_ref;
+    b.gtab = gtab;
+    b.flags = flags;
+    b.status = status;
+    k_bin<<<std::min((n + 255) / 256, num_sms * 8), 256, 0, st>>>(b);
+    const int nbb = (int)((nbins + kScanBlock - 1) / kScanBlock);
+    k_scan_blocks<<<nbb, kScanBlock, 0, st>>>(bin_fill, bin_start, bsums, nbins, flags);
+    k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, bin_start + nbins, flags, status);
+    k_scan_add<<<nbb, kScanBlock, 0, st>>>(bin_start, bin_fill, bsums, nbins, flags);
+    k_scatter<<<std::min((n + 255) / 256, num_sms * 8), 256, 0, st>>>(atom_bin, bin_fill, bin_atoms, n, flags);
+    k_sort_bins<<<(int)std::min<long long>((nbins + 255) / 256, num_sms * 8), 256, 0, st>>>(bin_start, bin_atoms,
+                                                                                             nbins, flags);
+    RowArgs r;
+    r.pos = pos;
+    r.species = sys->species;
+    r.atom_bin = atom_bin;
+    r.img = img;
+    r.bin_start = bin_start;
+    r.bin_atoms = bin_atoms;
+    r.n = n;
+    r.max_nbr = max_nbr;
+    r.compaction = 1;
+    for (int d = 0; d < 3; ++d) {
+        r.nb[d] = P.nb[d];
+        r.R[d] = P.R[d];
+        r.pbc[d] = P.pbc[d];
+    }
+    r.cell = cell;
+    r.rc2 = (float)(r_list * r_list);
+    r.rc2d = r_list * r_list;
+    r.entries = entries;
+    r.count = count;
+    r.group = group;
+    r.gtab = gtab;
+    r.flags = flags;
+    r.status = status;
+    k_build_rows<<<std::max(1, std::min((n + 7) / 8, num_sms * 8)), 256, 0, st>>>(r);
+    s = cuda_fail(cudaGetLastError(), "neighbour build (no allocation)");
+    if (s != FLR_OK) return s;
+    int stv = 0, maxc = 0;
+    s = cuda_fail(cudaMemcpyAsync(&stv, status, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    if (s == FLR_OK)
+        s = cuda_fail(cudaMemcpyAsync(&maxc, &gtab->max_count, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
+    if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "neighbour build (no allocation)");
+    if (s != FLR_OK) return s;
+    if (stv & kErrOverflow) {
+        set_error("neighbour list overflow: an atom has " + std::to_string(maxc) + " neighbours, max_nbr is " +
+                  std::to_string(max_nbr));
+        return FLR_ENBR_OVERFLOW;
+    }
+    if (stv & kErrShift) {
+        set_error("image shift out of range (positions far outside the cell, or cell too narrow)");
+        return FLR_EDEVICE;
+    }
+    if (stv & kErrSpecies) {
+        set_error("species index out of range");
+        return FLR_EINVAL;
+    }
+    return FLR_OK;
+}

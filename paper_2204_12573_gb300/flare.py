@@ -170,6 +170,16 @@ def build_neighbors(ff: FlareGB, system: System, nl: NbrList, stream=None):
     N.check(ff.lib.flr_build_neighbors(ff.handle, ctypes.byref(s), nl.handle, _stream(stream)))
 
 
+def build_neighbors_noalloc(system: System, r_list: float, max_nbr: int, entries, count, stream=None):
+    """Neighbour list into caller-provided int32 tensors (entries [n, max_nbr],
+    count [n]) without any device allocation by the library; synchronizes.
+    Meant for callers that cannot allocate device memory (see include/flare_gb.h
+    for the size limits and the shared-scratch caveat)."""
+    s = system.c_struct()
+    N.check(N.lib().flr_build_neighbors_noalloc(ctypes.byref(s), float(r_list), int(max_nbr), _ptr(entries),
+                                                _ptr(count), _stream(stream)))
+
+
 def compute_descriptors(ff: FlareGB, system: System, nl: NbrList, stream=None):
     """Normalized B2 descriptors [n, d_full] (float32) and norms ||B|| [n]."""
     n = system.n_atoms
