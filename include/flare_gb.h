@@ -95,6 +95,22 @@ typedef struct {
     int32_t pbc[3];
 } flr_system;
 
+/* A batch of structures evaluated together (different sizes and cells):
+ * atoms of structure s are rows offsets[s] .. offsets[s+1]-1 of pos and
+ * species.  pos: device float[n_atoms][4], 16-byte aligned; species: device
+ * int32[n_atoms]; offsets: host int32[n_structs + 1] with offsets[0] = 0 and
+ * offsets[n_structs] = n_atoms; cells: host double[n_structs][9] (rows are
+ * lattice vectors); pbc: host int32[n_structs][3]. */
+typedef struct {
+    int32_t n_structs;
+    int32_t n_atoms;
+    const float *pos;
+    const int32_t *species;
+    const int32_t *offsets;
+    const double *cells;
+    const int32_t *pbc;
+} flr_batch;
+
 /* Per-atom results (device pointers; any may be NULL except forces). */
 typedef struct {
     float *energy;       /* [n] E_i = d^T beta_{s_i} d (Eq. 1, mapped) */
@@ -173,6 +189,34 @@ int flr_nbrlist_view(const flr_nbrlist *nl, int32_t **entries, int32_t **count, 
  * from the atoms' bounding box).  FLR_ENBR_OVERFLOW if a row exceeds
  * max_nbr (the message gives the count needed). */
 int flr_build_neighbors(flr_ctx *ctx, const flr_system *sys, flr_nbrlist *nl, flr_stream_t stream);
+
+/* Neighbour lists of every structure of a batch at once (same rules as
+ * flr_build_neighbors, each structure with its own cell; rows refer to
+ * batch-wide atom indices).  The list must have capacity for n_atoms.
+ * SYNCHRONIZES the stream once (the bin grids are planned from the
+ * structures' bounding boxes). */
+int flr_build_neighbors_batch(flr_ctx *ctx, const flr_batch *batch, flr_nbrlist *nl, flr_stream_t stream);
+
+/* Energy, forces and uncertainty of every atom of a batch in one launch
+ * sequence (Eq. 1, Eq. 2; used for serving and for batched
+ * differentiation).  Per-atom outputs cover all atoms of the batch; when
+ * out->totals is not NULL it is a device double[n_structs][FLR_NTOTALS] and
+ * receives each structure's totals (FP64 energy and virial, max sigma,
+ * isolated atoms), each reduced in a fixed order.  Asynchronous. */
+int flr_energy_forces_uncertainty_batch(flr_ctx *ctx, const flr_batch *batch, const flr_nbrlist *nl,
+                                        flr_outputs *out, flr_stream_t stream);
+
+/* Backward pass of the energy (differentiation of Eq. 1) for a batch whose
+ * list was built by flr_build_neighbors(_batch): for the loss
+ * L = sum_i u_i E_i with u = grad_energy (device float[n_atoms]),
+ *   grad_pos  = dL/dr  (device float[n_atoms][3]) = -(forces of the weighted energy),
+ *   grad_beta = dL/dbeta_s = sum over atoms i of species s of u_i d_i d_i^T
+ *               (device float[n_species][d_full][d_full], overwritten; may be NULL).
+ * The descriptors, basis values and quadratic forms are recomputed (the
+ * basis is re-evaluated per pair inside the force kernel), so nothing is
+ * stored between the forward and the backward call.  Asynchronous. */
+int flr_energy_backward(flr_ctx *ctx, const flr_batch *batch, const flr_nbrlist *nl, const float *grad_energy,
+                        float *grad_pos, float *grad_beta, flr_stream_t stream);
 
 /* Normalized ACE-B2 descriptors d = B / ||B|| in the full layout
  * (Sec. V-B): d_hat device float[n][d_full] (components outside an atom's

@@ -38,6 +38,7 @@ EXPORTED = [
     "flr_nbrlist_view", "flr_build_neighbors", "flr_compute_descriptors",
     "flr_energy_forces_uncertainty", "flr_md_step", "flr_sync", "flr_launch_count",
     "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
+    "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
@@ -52,6 +53,12 @@ class Params(ctypes.Structure):
 class System(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int32), ("pos", ctypes.c_void_p), ("species", ctypes.c_void_p),
                 ("cell", ctypes.c_double * 9), ("pbc", ctypes.c_int32 * 3)]
+
+
+class Batch(ctypes.Structure):
+    _fields_ = [("n_structs", ctypes.c_int32), ("n_atoms", ctypes.c_int32), ("pos", ctypes.c_void_p),
+                ("species", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("cells", ctypes.c_void_p),
+                ("pbc", ctypes.c_void_p)]
 
 
 class Outputs(ctypes.Structure):
@@ -104,6 +111,10 @@ def lib():
             "flr_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),
             "flr_build_neighbors_noalloc": (ctypes.c_int, [ctypes.POINTER(System), ctypes.c_double, ctypes.c_int32,
                                                            P, P, P]),
+            "flr_build_neighbors_batch": (ctypes.c_int, [P, ctypes.POINTER(Batch), P, P]),
+            "flr_energy_forces_uncertainty_batch": (ctypes.c_int, [P, ctypes.POINTER(Batch), P,
+                                                                   ctypes.POINTER(Outputs), P]),
+            "flr_energy_backward": (ctypes.c_int, [P, ctypes.POINTER(Batch), P, P, P, P, P]),
             "flr_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_int64)]),
         }

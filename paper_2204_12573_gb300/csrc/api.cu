@@ -83,7 +83,6 @@ static void prof_drain(ProfState *p)
     p->n_recs = 0;
 }
 
-int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc, const float *bb, double margin);
 int launch_set_rebuild(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
 int launch_clear_rebuild_counter(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
 int launch_copy_rebuilds(flr_ctx *ctx, flr_nbrlist *nl, double *totals, cudaStream_t st);
@@ -135,6 +134,10 @@ void free_workspace(flr_ctx *ctx)
     }
     cudaFree(ctx->Facc);
     cudaFree(ctx->partials);
+    cudaFree(ctx->vir_atom);
+    ctx->vir_atom = nullptr;
+    cudaFree(ctx->scratch_out);
+    ctx->scratch_out = nullptr;
     ctx->A = ctx->norm = nullptr;
     ctx->Facc = nullptr;
     ctx->partials = nullptr;
@@ -163,6 +166,8 @@ int ensure_workspace(flr_ctx *ctx, int n)
         if (s == FLR_OK) s = dev_alloc(&ctx->G[r], N * D.K[r], "workspace G");
     }
     if (s == FLR_OK) s = dev_alloc(&ctx->Facc, N * 3, "workspace forces");
+    if (s == FLR_OK) s = dev_alloc(&ctx->vir_atom, N * 9, "workspace virial");
+    if (s == FLR_OK) s = dev_alloc(&ctx->scratch_out, N * 3, "workspace outputs");
     if (s == FLR_OK) s = dev_alloc(&ctx->partials, (size_t)kMaxPartials * 13 + 16, "workspace partials");
     if (s != FLR_OK) {
         free_workspace(ctx);
@@ -233,7 +238,7 @@ int status_to_code(int st)
 }
 
 int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
-             flr_outputs *out, const KickArgs &kick, cudaStream_t st)
+             flr_outputs *out, const KickArgs &kick, cudaStream_t st, double *seg_totals = nullptr)
 {
     if (n == 0) return FLR_OK;
     cudaError_t e = cudaMemsetAsync(ctx->Facc, 0, sizeof(long long) * 3 * (size_t)n, st);
@@ -247,13 +252,64 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
     prof_end(ctx, FLR_KERNEL_QFORM, st);
     if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_FORCE, st);
-    s = launch_force(ctx, nl, pos, species, n, out, st);
+    s = launch_force(ctx, nl, pos, species, n, out, seg_totals ? ctx->vir_atom : nullptr, nullptr, st);
     prof_end(ctx, FLR_KERNEL_FORCE, st);
     if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_FINALIZE, st);
-    s = launch_finalize(ctx, nl, n, out, kick, st);
+    if (seg_totals) {
+        // a batch: each structure gets its own totals
+        flr_outputs o = *out;
+        o.totals = nullptr;
+        s = launch_finalize(ctx, nl, n, &o, kick, 1.f, st);
+        if (s == FLR_OK) s = launch_seg_totals(ctx, nl, out, ctx->vir_atom, seg_totals, st);
+    } else {
+        s = launch_finalize(ctx, nl, n, out, kick, 1.f, st);
+    }
     prof_end(ctx, FLR_KERNEL_FINALIZE, st);
     return s;
+}
+
+// Neighbour lists of a batch of structures (one structure for the
+// single-system calls); synchronizes.
+int build_batch(flr_ctx *c, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
+                const int32_t *pbc, const float4 *pos, const int32_t *species, int n, cudaStream_t st)
+{
+    nl->n = n;
+    int s = plan_batch(c, nl, n_structs, offsets, cells, pbc, pos, n, st);
+    if (s != FLR_OK || n == 0) return s;
+    s = launch_set_rebuild(c, nl, st);
+    if (s == FLR_OK) s = launch_rebuild(c, nl, pos, species, n, st, false, nullptr);
+    if (s != FLR_OK) return s;
+    s = cuda_fail(cudaStreamSynchronize(st), "neighbour build");
+    if (s != FLR_OK) return s;
+    int dst[4];
+    GroupTab gt;
+    s = cuda_fail(cudaMemcpy(dst, c->status, sizeof(dst), cudaMemcpyDeviceToHost), "status");
+    if (s == FLR_OK) s = cuda_fail(cudaMemcpy(&gt, nl->gtab, sizeof(gt), cudaMemcpyDeviceToHost), "status");
+    if (s != FLR_OK) return s;
+    if (dst[0]) {
+        cudaMemset(c->status, 0, 4 * sizeof(int));
+        s = status_to_code(dst[0]);
+        if (s == FLR_ENBR_OVERFLOW)
+            set_error("neighbour list overflow: an atom has " + std::to_string(gt.max_count) +
+                      " neighbours, max_nbr is " + std::to_string(nl->max_nbr));
+        return s;
+    }
+    return FLR_OK;
+}
+
+int check_batch(const flr_ctx *ctx, const flr_nbrlist *nl, const flr_batch *b)
+{
+    if (!b || !nl || nl->ctx != ctx || b->n_structs < 1 || b->n_atoms < 0 || b->n_atoms > nl->n_cap || !b->offsets ||
+        !b->cells || !b->pbc) {
+        set_error("invalid batch (n_structs >= 1, n_atoms within the list capacity, host offsets/cells/pbc)");
+        return FLR_EINVAL;
+    }
+    if (b->n_atoms > 0 && (!b->pos || !b->species || reinterpret_cast<uintptr_t>(b->pos) % 16)) {
+        set_error("batch pos must be 16-byte aligned float[n][4]; species required");
+        return FLR_EINVAL;
+    }
+    return FLR_OK;
 }
 
 }  // namespace
@@ -469,7 +525,7 @@ int flr_nbrlist_create(flr_ctx *c, int32_t n_atoms, flr_nbrlist **out)
     if (s == FLR_OK) s = dev_alloc(&nl->blk_group, 8 * ((N + 511) / 512 + 1) + 65536 + 1024, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->gtab, 1, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->flags, 4, "nbrlist");
-    if (s == FLR_OK) s = dev_alloc(&nl->bbox, 8, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->struct_of, N, "nbrlist");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->gtab, 0, sizeof(GroupTab)), "nbrlist");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->flags, 0, 4 * sizeof(int32_t)), "nbrlist");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->group, 0xff, N * sizeof(int32_t)), "nbrlist");
@@ -501,6 +557,12 @@ int flr_nbrlist_destroy(flr_nbrlist *nl)
     cudaFree(nl->gtab);
     cudaFree(nl->flags);
     cudaFree(nl->bbox);
+    cudaFree(nl->struct_of);
+    cudaFree(nl->offsets_d);
+    cudaFree(nl->cells_d);
+    cudaFree(nl->plans_d);
+    delete[] nl->plans_h;
+    delete[] nl->offsets_h;
     delete nl;
     return FLR_OK;
 }
@@ -521,62 +583,97 @@ int flr_build_neighbors(flr_ctx *c, const flr_system *sys, flr_nbrlist *nl, flr_
     int s = check_system(c, nl, sys);
     if (s != FLR_OK) return s;
     cudaSetDevice(c->device);
+    const int32_t offsets[2] = {0, sys->n_atoms};
+    return build_batch(c, nl, 1, offsets, sys->cell, sys->pbc, reinterpret_cast<const float4 *>(sys->pos),
+                       sys->species, sys->n_atoms, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int flr_build_neighbors_batch(flr_ctx *c, const flr_batch *b, flr_nbrlist *nl, flr_stream_t stream)
+{
+    if (!c) return FLR_EINVAL;
+    int s = check_batch(c, nl, b);
+    if (s != FLR_OK) return s;
+    cudaSetDevice(c->device);
+    return build_batch(c, nl, b->n_structs, b->offsets, b->cells, b->pbc, reinterpret_cast<const float4 *>(b->pos),
+                       b->species, b->n_atoms, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int flr_energy_forces_uncertainty_batch(flr_ctx *c, const flr_batch *b, const flr_nbrlist *nl, flr_outputs *out,
+                                        flr_stream_t stream)
+{
+    if (!c || !out) return FLR_EINVAL;
+    int s = check_batch(c, nl, b);
+    if (s == FLR_OK) s = check_model(c);
+    if (s != FLR_OK) return s;
+    if (b->n_atoms != nl->n || b->n_structs != nl->n_structs) {
+        set_error("batch differs from the neighbour list's last build");
+        return FLR_EINVAL;
+    }
+    if (b->n_atoms > 0 && (!out->forces || !out->energy)) {
+        set_error("flr_energy_forces_uncertainty_batch: energy and forces are required");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    s = ensure_workspace(c, b->n_atoms);
+    if (s != FLR_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int n = sys->n_atoms;
-    nl->n = n;
-    // inverse cell for the bounding box, then the plan
-    Plan &P = nl->plan;
-    for (int k = 0; k < 9; ++k) P.cell[k] = sys->cell[k];
-    {
-        const double *m = sys->cell;
-        double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
-                     m[2] * (m[3] * m[7] - m[4] * m[6]);
-        if (!(std::fabs(det) > 0.0)) {
-            set_error("flr_build_neighbors: singular cell");
-            return FLR_EINVAL;
-        }
-        double *inv = P.inv;
-        inv[0] = (m[4] * m[8] - m[5] * m[7]) / det;
-        inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
-        inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
-        inv[3] = (m[5] * m[6] - m[3] * m[8]) / det;
-        inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
-        inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
-        inv[6] = (m[3] * m[7] - m[4] * m[6]) / det;
-        inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
-        inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+    if (b->n_atoms == 0) {
+        if (out->totals)
+            return cuda_fail(cudaMemsetAsync(out->totals, 0, sizeof(double) * FLR_NTOTALS * b->n_structs, st), "totals");
+        return FLR_OK;
     }
-    float bb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (n > 0) {
-        s = launch_bbox(c, nl, reinterpret_cast<const float4 *>(sys->pos), n, st);
-        if (s != FLR_OK) return s;
-        s = cuda_fail(cudaMemcpyAsync(bb, nl->bbox, 6 * sizeof(float), cudaMemcpyDeviceToHost, st), "bbox");
-        if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "bbox");
-        if (s != FLR_OK) return s;
-    }
-    s = plan_bins(c, nl, sys->cell, sys->pbc, bb, 2.0 * (c->p.r_cut + c->p.skin));
+    KickArgs kick;
+    std::memset(&kick, 0, sizeof(kick));
+    if (!out->totals) return evaluate(c, nl, reinterpret_cast<const float4 *>(b->pos), b->species, b->n_atoms, out, kick, st);
+    return evaluate(c, nl, reinterpret_cast<const float4 *>(b->pos), b->species, b->n_atoms, out, kick, st, out->totals);
+}
+
+int flr_energy_backward(flr_ctx *c, const flr_batch *b, const flr_nbrlist *nl, const float *grad_energy,
+                        float *grad_pos, float *grad_beta, flr_stream_t stream)
+{
+    if (!c) return FLR_EINVAL;
+    int s = check_batch(c, nl, b);
+    if (s == FLR_OK) s = check_model(c);
     if (s != FLR_OK) return s;
-    if (n == 0) return FLR_OK;
-    s = launch_set_rebuild(c, nl, st);
+    if (b->n_atoms != nl->n || b->n_structs != nl->n_structs) {
+        set_error("batch differs from the neighbour list's last build");
+        return FLR_EINVAL;
+    }
+    if (b->n_atoms > 0 && (!grad_energy || !grad_pos)) {
+        set_error("flr_energy_backward: grad_energy and grad_pos are required");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    s = ensure_workspace(c, b->n_atoms);
+    if (s != FLR_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int n = b->n_atoms;
+    if (n == 0) {
+        if (grad_beta)
+            return cuda_fail(cudaMemsetAsync(grad_beta, 0,
+                                             sizeof(float) * (size_t)kSpecies * c->dims.d_full * c->dims.d_full, st),
+                             "clear dL/dbeta");
+        return FLR_OK;
+    }
+    const float4 *pos = reinterpret_cast<const float4 *>(b->pos);
+    // recompute the forward intermediates (descriptors, g); nothing is kept from the forward call
+    flr_outputs o;
+    o.energy = c->scratch_out;
+    o.variance = c->scratch_out + n;
+    o.sigma = c->scratch_out + 2 * (size_t)n;
+    o.forces = grad_pos;
+    o.totals = nullptr;
+    s = cuda_fail(cudaMemsetAsync(c->Facc, 0, sizeof(long long) * 3 * (size_t)n, st), "clear force accumulators");
+    if (s == FLR_OK) s = launch_desc(c, nl, pos, b->species, n, st);
     if (s == FLR_OK)
-        s = launch_rebuild(c, nl, reinterpret_cast<const float4 *>(sys->pos), sys->species, n, st, false, nullptr);
-    if (s != FLR_OK) return s;
-    s = cuda_fail(cudaStreamSynchronize(st), "neighbour build");
-    if (s != FLR_OK) return s;
-    int dst[4];
-    GroupTab gt;
-    s = cuda_fail(cudaMemcpy(dst, c->status, sizeof(dst), cudaMemcpyDeviceToHost), "status");
-    if (s == FLR_OK) s = cuda_fail(cudaMemcpy(&gt, nl->gtab, sizeof(gt), cudaMemcpyDeviceToHost), "status");
-    if (s != FLR_OK) return s;
-    if (dst[0]) {
-        cudaMemset(c->status, 0, 4 * sizeof(int));
-        s = status_to_code(dst[0]);
-        if (s == FLR_ENBR_OVERFLOW)
-            set_error("neighbour list overflow: an atom has " + std::to_string(gt.max_count) +
-                      " neighbours, max_nbr is " + std::to_string(nl->max_nbr));
-        return s;
-    }
-    return FLR_OK;
+        s = c->p.precision == FLR_PREC_FP32 ? launch_qform_simt(c, nl, &o, st) : launch_qform_tc(c, nl, &o, st);
+    // dL/dr = -(forces of sum_i u_i E_i): the force kernel with g_i scaled by u_i
+    if (s == FLR_OK) s = launch_force(c, nl, pos, b->species, n, &o, nullptr, grad_energy, st);
+    KickArgs none;
+    std::memset(&none, 0, sizeof(none));
+    if (s == FLR_OK) s = launch_finalize(c, nl, n, &o, none, -1.f, st);
+    if (s == FLR_OK && grad_beta) s = launch_dbeta(c, nl, grad_energy, grad_beta, st);
+    return s;
 }
 
 int flr_compute_descriptors(flr_ctx *c, const flr_system *sys, const flr_nbrlist *nl, float *d_hat, float *norm,

@@ -25,7 +25,7 @@ struct DescArgs {
     const int32_t *species;
     const int32_t *entries, *count, *group, *row;
     int max_nbr, n;
-    CellArg cell;
+    Cells cells;               // per-structure lattice vectors
     float rcut;
     const int32_t *tab[2];     // compact index -> (a, b, l)
     int K[2], kp32[2], kp64[2];
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 3) k_desc(DescArgs a)
         const int cls = group_cls(g);
         const int reg = group_region(g);
         const float4 pi = cur.pi;
+        const double *cl = a.cells.of(i);
         const int cnt = cur.cnt;
         const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
 
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 3) k_desc(DescArgs a)
                 int j, sx, sy, sz;
                 decode_entry(base == 0 ? cur.e0 : (base == 32 ? cur.e1 : rowp[q]), j, sx, sy, sz);
                 const float4 pj = a.pos[j];
-                r = pair_vector(pi, pj, sx, sy, sz, a.cell);
+                r = pair_vector(pi, pj, sx, sy, sz, cl);
                 ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
                 sj = a.species[j];
             }
@@ -299,7 +300,8 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.row = nl->row;
     a.max_nbr = nl->max_nbr;
     a.n = n;
-    for (int c = 0; c < 9; ++c) a.cell.c[c] = nl->plan.cell[c];
+    a.cells.cells = nl->cells_d;
+    a.cells.struct_of = nl->n_structs > 1 ? nl->struct_of : nullptr;
     a.rcut = (float)ctx->p.r_cut;
     a.tab[0] = ctx->tab_full;
     a.tab[1] = ctx->tab_single;

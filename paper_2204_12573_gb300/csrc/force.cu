@@ -38,7 +38,7 @@ struct ForceArgs {
     const int32_t *species;
     const int32_t *entries, *count, *group, *row;
     int max_nbr, n;
-    CellArg cell;
+    Cells cells;               // per-structure lattice vectors
     float rcut;
     int K[2];
     const float *G[2];         // g = dE/dB rows from the quadratic-form epilogue
@@ -46,6 +46,8 @@ struct ForceArgs {
     float *energy, *variance, *sigma;
     unsigned long long *Facc;
     double *vir_part;          // [gridDim.x][9]
+    float *vir_atom;           // [n][9] per-atom virial, or nullptr (batches of structures need it)
+    const float *weight;       // [n] per-atom weights u_i on E_i (backward pass), or nullptr
     int *status;
 };
 
@@ -56,6 +58,7 @@ struct ForceSmem {
     float W[kWarpsForce][kSlots * kWSlot];
     float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
     float F[kWarpsForce][kSlots][3];             // F_i of each slot's atom, summed in a fixed order
+    float V[kWarpsForce][kSlots][9];             // virial of each slot's atom (when requested)
     int atom[kWarpsForce][kSlots];
     int qseq[kWarpsForce][64];                  // atom sequence number of each queued pair
     float vir[kWarpsForce][9];
@@ -76,10 +79,11 @@ __device__ __forceinline__ long long to_fix(float v, int *status)
 // Evaluate m <= 32 queued pairs, one per lane.
 template <int N>
 __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, int m, float rc,
-                                            unsigned long long *Facc, int *status, float vir[9])
+                                            unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     int my_slot = -1;
     float f3[3] = {0.f, 0.f, 0.f};
+    float dv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (lane < m) {
         const float4 rec = sm.q[w][lane];
         const int packed = __float_as_int(rec.w);
@@ -124,9 +128,11 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
         atomicAdd(dj + 0, (unsigned long long)(-ix));
         atomicAdd(dj + 1, (unsigned long long)(-iy));
         atomicAdd(dj + 2, (unsigned long long)(-iz));
-        vir[0] -= rec.x * fx; vir[1] -= rec.x * fy; vir[2] -= rec.x * fz;
-        vir[3] -= rec.y * fx; vir[4] -= rec.y * fy; vir[5] -= rec.y * fz;
-        vir[6] -= rec.z * fx; vir[7] -= rec.z * fy; vir[8] -= rec.z * fz;
+        dv[0] = -rec.x * fx; dv[1] = -rec.x * fy; dv[2] = -rec.x * fz;
+        dv[3] = -rec.y * fx; dv[4] = -rec.y * fy; dv[5] = -rec.y * fz;
+        dv[6] = -rec.z * fx; dv[7] = -rec.z * fy; dv[8] = -rec.z * fz;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) vir[k] += dv[k];
         my_slot = slot;
         f3[0] = fx;
         f3[1] = fy;
@@ -149,6 +155,15 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
             sm.F[w][s][1] += v[1];
             sm.F[w][s][2] += v[2];
         }
+        if (want_vatom) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                float x = my_slot == s ? dv[c] : 0.f;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) sm.V[w][s][c] += x;
+            }
+        }
     }
     __syncwarp();
 }
@@ -156,11 +171,11 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
 // Evaluate every queued pair and compact the queue.
 template <int N>
 __device__ __forceinline__ void drain(ForceSmem<N> &sm, int w, int lane, int &nq, bool all, float rc,
-                                      unsigned long long *Facc, int *status, float vir[9])
+                                      unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     while (nq >= 32 || (all && nq > 0)) {
         const int m = nq < 32 ? nq : 32;
-        force_batch<N>(sm, w, lane, m, rc, Facc, status, vir);
+        force_batch<N>(sm, w, lane, m, rc, Facc, status, vir, want_vatom);
         const int rest = nq - m;
         float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
         int sq = 0;
@@ -181,12 +196,16 @@ __device__ __forceinline__ void drain(ForceSmem<N> &sm, int w, int lane, int &nq
 // Move a slot's accumulated F_i to the global accumulator and clear it.
 template <int N>
 __device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, int slot,
-                                           unsigned long long *Facc, int *status)
+                                           unsigned long long *Facc, int *status, float *vir_atom)
 {
     const int i = sm.atom[w][slot];
     if (lane < 3 && i >= 0) {
         atomicAdd(Facc + 3 * (size_t)i + lane, (unsigned long long)to_fix(sm.F[w][slot][lane], status));
         sm.F[w][slot][lane] = 0.f;
+    }
+    if (lane < 9) {
+        if (vir_atom && i >= 0) vir_atom[9 * (size_t)i + lane] = sm.V[w][slot][lane];
+        sm.V[w][slot][lane] = 0.f;
     }
     __syncwarp();
     if (lane == 0) sm.atom[w][slot] = -1;
@@ -276,6 +295,8 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
     if (lane < kSlots) sm.atom[w][lane] = -1;
     if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0.f;
+    for (int k = lane; k < 9 * kSlots; k += 32) sm.V[w][k / 9][k % 9] = 0.f;
+    const bool want_vatom = a.vir_atom != nullptr;
     __syncwarp();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
@@ -286,12 +307,14 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     for (; i < a.n; i += stride) {
         const AtomPre nxt = preload(a, i + stride, lane);
         const int g = cur.g;
-        if (g < 0) {
-            if (lane == 0) {
+        if (g < 0 || !(cur.nrm > 0.f)) {
+            // no environment inside r_cut: no forces from this centre
+            if (lane == 0 && g < 0) {
                 a.energy[i] = 0.f;
                 if (a.variance) a.variance[i] = 0.f;
                 if (a.sigma) a.sigma[i] = 0.f;
             }
+            if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
             cur = nxt;
             continue;
         }
@@ -312,11 +335,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 
         const int cls = group_cls(g), reg = group_region(g);
         const int K = a.K[reg];
-        // E, V and sigma were written by the quadratic-form epilogue
-        if (!(cur.nrm > 0.f)) {
-            cur = nxt;
-            continue;
-        }
+        // E, V and sigma were written by the quadratic-form epilogue.
         // g = dE/dB of this atom, in the compact order of its class
         const float4 *g4 = reinterpret_cast<const float4 *>(a.G[reg] + (size_t)cur.row * K);
         float4 gv[NK4];
@@ -324,12 +343,16 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         for (int k = 0; k < NK4; ++k) {
             const int o = lane + 32 * k;
             gv[k] = 4 * o < K ? g4[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.weight) {
+                const float u = a.weight[i];
+                gv[k].x *= u; gv[k].y *= u; gv[k].z *= u; gv[k].w *= u;
+            }
         }
 
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
         const int slot = seq & (kSlots - 1);
-        if (nq > 0 && sm.qseq[w][0] <= seq - kSlots) drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
-        flush_slot<N>(sm, w, lane, slot, a.Facc, a.status);
+        if (nq > 0 && sm.qseq[w][0] <= seq - kSlots) drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
+        flush_slot<N>(sm, w, lane, slot, a.Facc, a.status, a.vir_atom);
         if (lane == 0) sm.atom[w][slot] = i;
 
         float *sG = sm.G[w];
@@ -371,6 +394,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 
         // queue the pairs inside r_cut
         const float4 pi = cur.pi;
+        const double *cl = a.cells.of(i);
         const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
         for (int base = 0; base < cnt; base += 32) {
             const int q = base + lane;
@@ -393,7 +417,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
                     pj = a.pos[j];
                     sj = a.species[j];
                 }
-                rv = pair_vector(pi, pj, sx, sy, sz, a.cell);
+                rv = pair_vector(pi, pj, sx, sy, sz, cl);
                 ok = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z < rc2;
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -404,13 +428,13 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             }
             nq += __popc(m);
             __syncwarp();
-            drain<N>(sm, w, lane, nq, false, rc, a.Facc, a.status, vir);
+            drain<N>(sm, w, lane, nq, false, rc, a.Facc, a.status, vir, want_vatom);
         }
         ++seq;
         cur = nxt;
     }  // atoms
-    drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir);
-    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc, a.status);
+    drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
+    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc, a.status, a.vir_atom);
 
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
@@ -436,6 +460,7 @@ struct FinArgs {
     int n;
     double *part;          // [gridDim.x][4]
     KickArgs kick;
+    float sign;            // 1: forces; -1: gradient of the (weighted) energy
 };
 
 __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
@@ -450,7 +475,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
         float f[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            f[c] = (float)((double)(long long)a.Facc[3 * (size_t)i + c] * (1.0 / 4294967296.0));
+            f[c] = a.sign * (float)((double)(long long)a.Facc[3 * (size_t)i + c] * (1.0 / 4294967296.0));
         a.forces[3 * (size_t)i + 0] = f[0];
         a.forces[3 * (size_t)i + 1] = f[1];
         a.forces[3 * (size_t)i + 2] = f[2];
@@ -556,10 +581,78 @@ __global__ void __launch_bounds__(1024) k_totals(TotArgs a)
     }
 }
 
+// Per-structure totals of a batch: one block per structure sums its atoms in
+// a fixed order (E in FP64, the per-atom virials, max sigma, isolated atoms).
+struct SegArgs {
+    const int32_t *offsets;
+    int n_structs;
+    const float *energy, *sigma, *norm, *vir_atom;
+    double *totals;   // [n_structs][FLR_NTOTALS]
+};
+
+__global__ void __launch_bounds__(256) k_seg_totals(SegArgs a)
+{
+    __shared__ double red[8][12];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int s = blockIdx.x; s < a.n_structs; s += gridDim.x) {
+        double acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+        for (int i = a.offsets[s] + threadIdx.x; i < a.offsets[s + 1]; i += blockDim.x) {
+            acc[0] += (double)a.energy[i];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[1 + k] += (double)a.vir_atom[9 * (size_t)i + k];
+            if (a.sigma) acc[10] = fmax(acc[10], (double)a.sigma[i]);
+            acc[11] += a.norm[i] > 0.f ? 0.0 : 1.0;
+        }
+        for (int o = 16; o; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            acc[10] = fmax(acc[10], __shfl_xor_sync(0xffffffffu, acc[10], o));
+            acc[11] += __shfl_xor_sync(0xffffffffu, acc[11], o);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) red[w][k] = acc[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t[12] = {0};
+            for (int q = 0; q < 8; ++q) {
+                for (int k = 0; k < 10; ++k) t[k] += red[q][k];
+                t[10] = fmax(t[10], red[q][10]);
+                t[11] += red[q][11];
+            }
+            double *o = a.totals + (size_t)s * FLR_NTOTALS;
+            for (int k = 0; k < FLR_NTOTALS; ++k) o[k] = 0.0;
+            o[FLR_TOT_ENERGY] = t[0];
+            for (int k = 0; k < 9; ++k) o[FLR_TOT_VIRIAL + k] = t[1 + k];
+            o[FLR_TOT_MAX_SIGMA] = t[10];
+            o[FLR_TOT_N_ISOLATED] = t[11];
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
+int launch_seg_totals(flr_ctx *ctx, const flr_nbrlist *nl, const flr_outputs *out, const float *vir_atom,
+                      double *totals, cudaStream_t st)
+{
+    SegArgs s;
+    s.offsets = nl->offsets_d;
+    s.n_structs = nl->n_structs;
+    s.energy = out->energy;
+    s.sigma = out->sigma;
+    s.norm = ctx->norm;
+    s.vir_atom = vir_atom;
+    s.totals = totals;
+    k_seg_totals<<<std::max(1, std::min(nl->n_structs, ctx->num_sms * 8)), 256, 0, st>>>(s);
+    count_launch(ctx);
+    return cuda_fail(cudaGetLastError(), "per-structure totals");
+}
+
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
-                 flr_outputs *out, cudaStream_t st)
+                 flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st)
 {
     ForceArgs a;
     a.pos = pos;
@@ -570,7 +663,8 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.row = nl->row;
     a.max_nbr = nl->max_nbr;
     a.n = n;
-    for (int c = 0; c < 9; ++c) a.cell.c[c] = nl->plan.cell[c];
+    a.cells.cells = nl->cells_d;
+    a.cells.struct_of = nl->n_structs > 1 ? nl->struct_of : nullptr;
     a.rcut = (float)ctx->p.r_cut;
     for (int r = 0; r < 2; ++r) {
         a.K[r] = ctx->dims.K[r];
@@ -583,6 +677,8 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.sigma = out->sigma;
     a.Facc = reinterpret_cast<unsigned long long *>(ctx->Facc);
     a.vir_part = ctx->partials;
+    a.vir_atom = vir_atom;
+    a.weight = weight;
     a.status = ctx->status;
     const long long work = (n + kWarpsForce - 1) / kWarpsForce;
     int grid;
@@ -598,7 +694,7 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     return cuda_fail(cudaGetLastError(), "force kernel");
 }
 
-int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick,
+int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick, float sign,
                     cudaStream_t st)
 {
     (void)nl;
@@ -613,6 +709,7 @@ int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out
     f.n = n;
     f.part = ctx->partials + (size_t)kMaxPartials * 9;
     f.kick = kick;
+    f.sign = sign;
     k_finalize<<<nfin, 256, 0, st>>>(f);
     TotArgs t;
     t.vir_part = ctx->partials;

@@ -65,6 +65,7 @@ struct Plan {
     double inv[9];      // inverse of the cell matrix (frac = pos . inv)
     int pbc[3];
     long long nbins;
+    long long bin_base; // first global bin of this structure in a batch
 };
 
 }  // namespace flr
@@ -88,10 +89,20 @@ struct flr_nbrlist {
     int32_t *blk_group;    // [n_blocks][8] per-block group counts
     flr::GroupTab *gtab;   // device
     int32_t *flags;        // device [4]: [0] rebuild needed, [1] rebuild counter
-    float *bbox;           // device [6] fractional min / max
+    float *bbox;           // device [structs_cap][8] fractional min / max
     long long nbins_cap;
-    flr::Plan plan;
+    flr::Plan plan;        // structure 0 (the single-structure calls)
     bool planned;
+    // batches of structures: atoms of structure s are [offsets[s], offsets[s+1])
+    int n_structs;
+    int structs_cap;
+    int32_t *struct_of;    // device [n_cap] structure of each atom (nullptr when n_structs == 1)
+    int32_t *offsets_d;    // device [structs_cap + 1]
+    double *cells_d;       // device [structs_cap][9]
+    flr::Plan *plans_d;    // device [structs_cap]
+    flr::Plan *plans_h;    // host  [structs_cap]
+    int32_t *offsets_h;    // host  [structs_cap + 1]
+    long long nbins_total; // bins of all structures
 };
 
 // TMA tensor maps of the tcgen05 path: A operands per region (BF16 hi / lo,
@@ -128,6 +139,8 @@ struct flr_ctx {
     float *P[2];               // [n][2K[r]] quadratic-form products (FP32 SIMT path only)
     float *G[2];               // [n][K[r]]  g = dE/dB rows, consumed by the force kernel
     long long *Facc;           // [n][3] fixed point
+    float *vir_atom;           // [n][9] per-atom virial (batches)
+    float *scratch_out;        // [3][n] E, V, sigma of the backward pass
     double *partials;          // [n_blocks][16]
     int n_part;
     TcMaps *maps;              // host copy of the current tensor maps
@@ -166,7 +179,8 @@ inline void count_launch(flr_ctx *ctx, int k = 1) { ctx->launches += k; }
 // ---- launchers (one per translation unit) ----
 int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                    cudaStream_t st, bool wrap_positions, float4 *pos_mut);
-int launch_bbox(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, int n, cudaStream_t st);
+int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
+               const int32_t *pbc, const float4 *pos, int n, cudaStream_t st);
 int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                 cudaStream_t st);
 int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat, float *norm,
@@ -174,7 +188,9 @@ int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat,
 int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
 int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
-                 flr_outputs *out, cudaStream_t st);
+                 flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st);
+int launch_seg_totals(flr_ctx *ctx, const flr_nbrlist *nl, const flr_outputs *out, const float *vir_atom,
+                      double *totals, cudaStream_t st);
 struct KickArgs {
     float4 *vel;
     const int *species;
@@ -182,8 +198,9 @@ struct KickArgs {
     float half_m[kSpecies];            // m_s / 2 / FTM2V  (kinetic energy in eV from A/ps)
     int enabled;
 };
-int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick,
+int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick, float sign,
                     cudaStream_t st);
+int launch_dbeta(flr_ctx *ctx, const flr_nbrlist *nl, const float *u, float *grad_beta, cudaStream_t st);
 int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, const float *forces,
                     const int *species, int n, const KickArgs &kick, float dt, float disp2_max,
                     cudaStream_t st);
@@ -220,19 +237,35 @@ struct CellArg {
     double c[9];
 };
 
+// Lattice vectors of the structure atom i belongs to: per-structure cells
+// live in device memory (rows = lattice vectors, 9 doubles each).
+struct Cells {
+    const double *cells;       // [n_structs][9]
+    const int32_t *struct_of;  // [n] or nullptr (one structure)
+    __device__ __forceinline__ const double *of(int i) const
+    {
+        return cells + 9 * (struct_of ? struct_of[i] : 0);
+    }
+};
+
 // Pair vector r_ij = r_j + S.cell - r_i in FP32.  Without an image shift the
 // FP32 difference is correctly rounded; with one, the sum is formed in FP64
 // from the exact FP32 inputs so large coordinates lose no accuracy.
 __device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, int sx, int sy,
-                                              int sz, const CellArg &cell)
+                                              int sz, const double *c)
 {
     if ((sx | sy | sz) == 0) return make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z);
-    double tx = sx * cell.c[0] + sy * cell.c[3] + sz * cell.c[6];
-    double ty = sx * cell.c[1] + sy * cell.c[4] + sz * cell.c[7];
-    double tz = sx * cell.c[2] + sy * cell.c[5] + sz * cell.c[8];
+    double tx = sx * c[0] + sy * c[3] + sz * c[6];
+    double ty = sx * c[1] + sy * c[4] + sz * c[7];
+    double tz = sx * c[2] + sy * c[5] + sz * c[8];
     return make_float3((float)(((double)pj.x - (double)pi.x) + tx),
                        (float)(((double)pj.y - (double)pi.y) + ty),
                        (float)(((double)pj.z - (double)pi.z) + tz));
+}
+__device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, int sx, int sy,
+                                              int sz, const CellArg &cell)
+{
+    return pair_vector(pi, pj, sx, sy, sz, cell.c);
 }
 
 }  // namespace flr

@@ -5,12 +5,18 @@
 // descriptors"; Sec. V-C: the list is built once and reused while atoms
 // move less than half the skin).  Atoms are binned by fractional coordinate;
 // each bin is at least (r_cut + skin) wide so a fixed stencil of bins covers
-// every neighbour.  All steps run on the device; every kernel of the rebuild
-// sequence first reads the list's "rebuild needed" flag and returns at once
-// when it is clear, so an MD loop can enqueue the sequence every step and
-// let the device decide.
+// every neighbour.  A batch of structures is handled in one pass: each
+// structure has its own cell, bin grid (a contiguous range of global bins)
+// and plan in device memory, and each atom knows its structure.  All steps
+// run on the device; every kernel of the rebuild sequence first reads the
+// list's "rebuild needed" flag and returns at once when it is clear, so an
+// MD loop can enqueue the sequence every step and let the device decide.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -27,65 +33,86 @@ __device__ __forceinline__ int ordered(float f)
 }
 __device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
-struct InvArg {
-    double m[9];
-};
-
-__device__ __forceinline__ void frac_of(const float4 &p, const InvArg &inv, double f[3])
+__device__ __forceinline__ void frac_of(const float4 &p, const double *inv, double f[3])
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-        f[d] = (double)p.x * inv.m[d] + (double)p.y * inv.m[3 + d] + (double)p.z * inv.m[6 + d];
+        f[d] = (double)p.x * inv[d] + (double)p.y * inv[3 + d] + (double)p.z * inv[6 + d];
 }
 
-__global__ void k_bbox_init(int *bb)
-{
-    if (threadIdx.x < 3) bb[threadIdx.x] = ordered(FLT_MAX);
-    else if (threadIdx.x < 6) bb[threadIdx.x] = ordered(-FLT_MAX);
-}
+__device__ __forceinline__ int structure_of(const int32_t *struct_of, int i) { return struct_of ? struct_of[i] : 0; }
 
-__global__ void k_bbox(const float4 *__restrict__ pos, int n, InvArg inv, int *bb)
+__global__ void k_bbox_init(int *bb, int n_structs)
 {
-    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double f[3];
-        frac_of(pos[i], inv, f);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            lo[d] = fminf(lo[d], (float)f[d]);
-            hi[d] = fmaxf(hi[d], (float)f[d]);
-        }
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        for (int o = 16; o; o >>= 1) {
-            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-        }
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            atomicMin(bb + d, ordered(lo[d]));
-            atomicMax(bb + 3 + d, ordered(hi[d]));
-        }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 8 * n_structs; k += gridDim.x * blockDim.x) {
+        const int d = k & 7;
+        bb[k] = d < 3 ? ordered(FLT_MAX) : ordered(-FLT_MAX);
     }
 }
 
-__global__ void k_bbox_finish(int *bb)
+// fractional bounding box of every structure (warp-reduced when a warp's
+// atoms share a structure, which is the common case)
+__global__ void k_bbox(const float4 *__restrict__ pos, int n, const Plan *plans, const int32_t *struct_of, int *bb)
 {
-    if (threadIdx.x < 6) reinterpret_cast<float *>(bb)[threadIdx.x] = unordered(bb[threadIdx.x]);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n; base += warps * 32) {
+        const int i = base + lane;
+        const bool valid = i < n;
+        const int s = valid ? structure_of(struct_of, i) : -1;
+        float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+        if (valid) {
+            double f[3];
+            frac_of(pos[i], plans[s].inv, f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = (float)f[d];
+                hi[d] = (float)f[d];
+            }
+        }
+        const int s0 = __shfl_sync(0xffffffffu, s, 0);
+        if (__all_sync(0xffffffffu, !valid || s == s0)) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                for (int o = 16; o; o >>= 1) {
+                    lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                    hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    atomicMin(bb + 8 * s0 + d, ordered(lo[d]));
+                    atomicMax(bb + 8 * s0 + 3 + d, ordered(hi[d]));
+                }
+        } else if (valid) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                atomicMin(bb + 8 * s + d, ordered(lo[d]));
+                atomicMax(bb + 8 * s + 3 + d, ordered(hi[d]));
+            }
+        }
+    }
+}
+
+__global__ void k_bbox_finish(int *bb, int n_structs)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 8 * n_structs; k += gridDim.x * blockDim.x)
+        if ((k & 7) < 6) reinterpret_cast<float *>(bb)[k] = unordered(bb[k]);
+}
+
+// structure id of every atom from the batch offsets
+__global__ void k_struct_of(const int32_t *offsets, int n_structs, int32_t *struct_of)
+{
+    for (int s = blockIdx.x; s < n_structs; s += gridDim.x)
+        for (int i = offsets[s] + threadIdx.x; i < offsets[s + 1]; i += blockDim.x) struct_of[i] = s;
 }
 
 struct BinArgs {
     const float4 *pos;
     float4 *pos_mut;      // non-null: wrap positions in place (MD)
     int n;
-    InvArg inv;
-    CellArg cell;
-    int nb[3];
-    int pbc[3];
-    float flo[3], fspan[3];
+    const Plan *plans;
+    const int32_t *struct_of;
     int32_t *atom_bin, *img, *bin_count;
     float4 *pos_ref;
     GroupTab *gtab;
@@ -106,39 +133,41 @@ __global__ void k_bin(BinArgs a)
     if (a.flags[0] == 0) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.gtab->max_count = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-    float4 p = a.pos_mut ? a.pos_mut[i] : a.pos[i];
-    double f[3];
-    frac_of(p, a.inv, f);
-    int im[3] = {0, 0, 0};
+        const Plan &P = a.plans[structure_of(a.struct_of, i)];
+        float4 p = a.pos_mut ? a.pos_mut[i] : a.pos[i];
+        double f[3];
+        frac_of(p, P.inv, f);
+        int im[3] = {0, 0, 0};
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-        if (a.pbc[d]) {
-            im[d] = (int)floor(f[d]);
-            f[d] -= im[d];
+        for (int d = 0; d < 3; ++d)
+            if (P.pbc[d]) {
+                im[d] = (int)floor(f[d]);
+                f[d] -= im[d];
+            }
+        if (a.pos_mut && (im[0] | im[1] | im[2])) {
+            // wrap in place: r -= img . cell, formed in FP64
+            const double *c = P.cell;
+            double x = (double)p.x - (im[0] * c[0] + im[1] * c[3] + im[2] * c[6]);
+            double y = (double)p.y - (im[0] * c[1] + im[1] * c[4] + im[2] * c[7]);
+            double z = (double)p.z - (im[0] * c[2] + im[1] * c[5] + im[2] * c[8]);
+            p.x = (float)x;
+            p.y = (float)y;
+            p.z = (float)z;
+            a.pos_mut[i] = p;
+            im[0] = im[1] = im[2] = 0;
         }
-    if (a.pos_mut && (im[0] | im[1] | im[2])) {
-        // wrap in place: r -= img . cell, formed in FP64
-        double x = (double)p.x - (im[0] * a.cell.c[0] + im[1] * a.cell.c[3] + im[2] * a.cell.c[6]);
-        double y = (double)p.y - (im[0] * a.cell.c[1] + im[1] * a.cell.c[4] + im[2] * a.cell.c[7]);
-        double z = (double)p.z - (im[0] * a.cell.c[2] + im[1] * a.cell.c[5] + im[2] * a.cell.c[8]);
-        p.x = (float)x;
-        p.y = (float)y;
-        p.z = (float)z;
-        a.pos_mut[i] = p;
-        im[0] = im[1] = im[2] = 0;
-    }
-    int b[3];
+        int b[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int k = (int)floor((f[d] - (double)a.flo[d]) / (double)a.fspan[d] * a.nb[d]);
-        b[d] = min(max(k, 0), a.nb[d] - 1);
-        if (im[d] < -100 || im[d] > 100) atomicOr(a.status, kErrShift);
-    }
-    int bin = (b[0] * a.nb[1] + b[1]) * a.nb[2] + b[2];
-    a.atom_bin[i] = bin;
-    a.img[i] = (im[0] & 0xFF) | ((im[1] & 0xFF) << 8) | ((im[2] & 0xFF) << 16);
-    a.pos_ref[i] = p;
-    atomicAdd(a.bin_count + bin, 1);
+        for (int d = 0; d < 3; ++d) {
+            int k = (int)floor((f[d] - (double)P.flo[d]) / (double)P.fspan[d] * P.nb[d]);
+            b[d] = min(max(k, 0), P.nb[d] - 1);
+            if (im[d] < -100 || im[d] > 100) atomicOr(a.status, kErrShift);
+        }
+        const int bin = (int)P.bin_base + (b[0] * P.nb[1] + b[1]) * P.nb[2] + b[2];
+        a.atom_bin[i] = bin;
+        a.img[i] = (im[0] & 0xFF) | ((im[1] & 0xFF) << 8) | ((im[2] & 0xFF) << 16);
+        a.pos_ref[i] = p;
+        atomicAdd(a.bin_count + bin, 1);
     }
 }
 
@@ -248,8 +277,8 @@ struct RowArgs {
     const int32_t *species;
     const int32_t *atom_bin, *img, *bin_start, *bin_atoms;
     int n, max_nbr, compaction;
-    int nb[3], R[3], pbc[3];
-    CellArg cell;
+    const Plan *plans;
+    const int32_t *struct_of;
     float rc2;
     double rc2d;
     int32_t *entries, *count, *group;
@@ -270,12 +299,13 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
     __shared__ int s_start[8][32], s_excl[8][32], s_shift[8][32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int warps = gridDim.x * (blockDim.x >> 5);
-    const int span[3] = {2 * a.R[0] + 1, 2 * a.R[1] + 1, 2 * a.R[2] + 1};
-    const int n_stencil = span[0] * span[1] * span[2];
     for (int i = blockIdx.x * (blockDim.x >> 5) + wl; i < a.n; i += warps) {
+        const Plan &P = a.plans[structure_of(a.struct_of, i)];
+        const int span[3] = {2 * P.R[0] + 1, 2 * P.R[1] + 1, 2 * P.R[2] + 1};
+        const int n_stencil = span[0] * span[1] * span[2];
         const float4 pi = a.pos[i];
-        const int bin = a.atom_bin[i];
-        const int bi[3] = {bin / (a.nb[1] * a.nb[2]), (bin / a.nb[2]) % a.nb[1], bin % a.nb[2]};
+        const int bin = a.atom_bin[i] - (int)P.bin_base;
+        const int bi[3] = {bin / (P.nb[1] * P.nb[2]), (bin / P.nb[2]) % P.nb[1], bin % P.nb[2]};
         const int imi = a.img[i];
         int32_t *row = a.entries + (size_t)i * a.max_nbr;
         int cnt = 0;
@@ -285,25 +315,25 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
             const int k = sbase + lane;
             int c = 0, start = 0, shift = 0;
             if (k < n_stencil) {
-                const int dd[3] = {k / (span[1] * span[2]) - a.R[0], (k / span[2]) % span[1] - a.R[1],
-                                   k % span[2] - a.R[2]};
+                const int dd[3] = {k / (span[1] * span[2]) - P.R[0], (k / span[2]) % span[1] - P.R[1],
+                                   k % span[2] - P.R[2]};
                 int bj[3], sb[3];
                 bool skip = false;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
                     const int kk = bi[d] + dd[d];
-                    if (a.pbc[d]) {
-                        const int q = (kk >= 0) ? kk / a.nb[d] : -((-kk + a.nb[d] - 1) / a.nb[d]);
+                    if (P.pbc[d]) {
+                        const int q = (kk >= 0) ? kk / P.nb[d] : -((-kk + P.nb[d] - 1) / P.nb[d]);
                         sb[d] = q;
-                        bj[d] = kk - q * a.nb[d];
+                        bj[d] = kk - q * P.nb[d];
                     } else {
-                        skip |= (kk < 0 || kk >= a.nb[d]);
+                        skip |= (kk < 0 || kk >= P.nb[d]);
                         sb[d] = 0;
                         bj[d] = kk;
                     }
                 }
                 if (!skip) {
-                    const int b = (bj[0] * a.nb[1] + bj[1]) * a.nb[2] + bj[2];
+                    const int b = (int)P.bin_base + (bj[0] * P.nb[1] + bj[1]) * P.nb[2] + bj[2];
                     start = a.bin_start[b];
                     c = a.bin_start[b + 1] - start;
                     shift = (sb[0] & 0xFF) | ((sb[1] & 0xFF) << 8) | ((sb[2] & 0xFF) << 16);
@@ -343,7 +373,7 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                     if (!in_range) atomicOr(a.status, kErrShift);
                     if (in_range && !(j == i && S[0] == 0 && S[1] == 0 && S[2] == 0)) {
                         const float4 pj = a.pos[j];
-                        const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], a.cell);
+                        const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], P.cell);
                         const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
                         if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
                             ok = d2 < a.rc2;
@@ -352,7 +382,7 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                             double tv[3];
 #pragma unroll
                             for (int cc = 0; cc < 3; ++cc)
-                                tv[cc] = S[0] * a.cell.c[cc] + S[1] * a.cell.c[3 + cc] + S[2] * a.cell.c[6 + cc];
+                                tv[cc] = S[0] * P.cell[cc] + S[1] * P.cell[3 + cc] + S[2] * P.cell[6 + cc];
                             const double x = ((double)pj.x - (double)pi.x) + tv[0];
                             const double y = ((double)pj.y - (double)pi.y) + tv[1];
                             const double z = ((double)pj.z - (double)pi.z) + tv[2];
@@ -547,29 +577,28 @@ double width(const double *cell, int d)
     return vol / std::sqrt(x * x + y * y + z * z);
 }
 
-}  // namespace
-
-// Plan the bin grid from a fractional bounding box (host).  Along open
-// directions the grid covers the box plus a margin of `margin` A on both
-// sides; atoms that later leave it are clamped into the edge bins, which
-// stays correct because every bin is at least r_c wide.
-int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc, const float *bb,
-              double margin)
+// Cell and inverse of one structure (host); false for a singular cell.
+bool plan_cell(Plan &P, const double *cell, const int *pbc)
 {
-    Plan &P = nl->plan;
-    const double rc = ctx->p.r_cut + ctx->p.skin;
-    for (int c = 0; c < 9; ++c) P.cell[c] = cell[c];
+    for (int k = 0; k < 9; ++k) P.cell[k] = cell[k];
     inverse3(cell, P.inv);
-    if (!std::isfinite(P.inv[0]) || !std::isfinite(P.inv[4]) || !std::isfinite(P.inv[8])) {
-        set_error("flr_build_neighbors: singular cell matrix");
-        return FLR_EINVAL;
-    }
+    for (int d = 0; d < 3; ++d) P.pbc[d] = pbc[d] ? 1 : 0;
+    for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(P.inv[k])) return false;
+    return true;
+}
+
+// Bin grid of one structure from its fractional bounding box (host).  Along
+// open directions the grid covers the box plus `margin` A on both sides;
+// atoms that later leave it are clamped into the edge bins, which stays
+// correct because every bin is at least r_c wide.
+int plan_grid(Plan &P, const float *bb, double rc, double margin)
+{
     long long nbins = 1;
     for (int d = 0; d < 3; ++d) {
-        const double w = width(cell, d);
-        P.pbc[d] = pbc[d] ? 1 : 0;
+        const double w = width(P.cell, d);
         double flo, fspan;
-        if (pbc[d]) {
+        if (P.pbc[d]) {
             flo = 0.0;
             fspan = 1.0;
         } else {
@@ -582,9 +611,9 @@ int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc,
         int nb = (int)std::floor(extent / (rc * 1.0001));
         nb = std::max(1, std::min(nb, 4096));
         int R = (int)std::ceil(rc / (extent / nb) * (1.0 + 1e-6));
-        if (!pbc[d]) R = std::min(R, nb);
-        if (pbc[d] && R > 2 * nb + 1) {
-            set_error("flr_build_neighbors: periodic cell too narrow for r_cut + skin");
+        if (!P.pbc[d]) R = std::min(R, nb);
+        if (P.pbc[d] && R > 2 * nb + 1) {
+            set_error("neighbour build: periodic cell too narrow for r_cut + skin");
             return FLR_EINVAL;
         }
         P.nb[d] = nb;
@@ -594,52 +623,133 @@ int plan_bins(flr_ctx *ctx, flr_nbrlist *nl, const double *cell, const int *pbc,
         nbins *= nb;
     }
     if (nbins > (1ll << 26)) {
-        set_error("flr_build_neighbors: bin grid too large");
+        set_error("neighbour build: bin grid too large");
         return FLR_EINVAL;
     }
     P.nbins = nbins;
-    if (nbins + 1 > nl->nbins_cap) {
+    return FLR_OK;
+}
+
+}  // namespace
+
+// Plan the bin grids of a batch of structures (host, synchronizes once to
+// read the bounding boxes) and upload the per-structure tables.
+int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
+               const int32_t *pbc, const float4 *pos, int n, cudaStream_t st)
+{
+    if (n_structs < 1 || offsets[0] != 0 || offsets[n_structs] != n) {
+        set_error("neighbour build: batch offsets must start at 0 and end at n_atoms");
+        return FLR_EINVAL;
+    }
+    for (int s = 0; s < n_structs; ++s)
+        if (offsets[s + 1] < offsets[s]) {
+            set_error("neighbour build: batch offsets must be non-decreasing");
+            return FLR_EINVAL;
+        }
+    if (n_structs > nl->structs_cap) {
+        cudaFree(nl->offsets_d);
+        cudaFree(nl->cells_d);
+        cudaFree(nl->plans_d);
+        cudaFree(nl->bbox);
+        delete[] nl->plans_h;
+        delete[] nl->offsets_h;
+        const int cap = std::max(n_structs, 2 * nl->structs_cap);
+        nl->offsets_d = nullptr;
+        nl->cells_d = nullptr;
+        nl->plans_d = nullptr;
+        nl->bbox = nullptr;
+        cudaError_t e = cudaMalloc(&nl->offsets_d, sizeof(int32_t) * (cap + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&nl->cells_d, sizeof(double) * 9 * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&nl->plans_d, sizeof(Plan) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&nl->bbox, sizeof(float) * 8 * cap);
+        nl->plans_h = new Plan[cap];
+        nl->offsets_h = new int32_t[cap + 1];
+        nl->structs_cap = cap;
+        if (e != cudaSuccess) return cuda_fail(e, "batch tables");
+    }
+    nl->n_structs = n_structs;
+    for (int s = 0; s <= n_structs; ++s) nl->offsets_h[s] = offsets[s];
+    for (int s = 0; s < n_structs; ++s) {
+        Plan &P = nl->plans_h[s];
+        std::memset(&P, 0, sizeof(Plan));
+        if (!plan_cell(P, cells + 9 * s, pbc + 3 * s)) {
+            set_error("neighbour build: singular cell matrix (structure " + std::to_string(s) + ")");
+            return FLR_EINVAL;
+        }
+    }
+    int r = cuda_fail(cudaMemcpyAsync(nl->plans_d, nl->plans_h, sizeof(Plan) * n_structs, cudaMemcpyHostToDevice, st),
+                      "plans");
+    if (r == FLR_OK)
+        r = cuda_fail(cudaMemcpyAsync(nl->offsets_d, offsets, sizeof(int32_t) * (n_structs + 1), cudaMemcpyHostToDevice,
+                                      st),
+                      "offsets");
+    if (r != FLR_OK) return r;
+    std::vector<double> cl(9 * (size_t)n_structs);
+    for (int s = 0; s < n_structs; ++s)
+        for (int k = 0; k < 9; ++k) cl[9 * s + k] = nl->plans_h[s].cell[k];
+    r = cuda_fail(cudaMemcpyAsync(nl->cells_d, cl.data(), sizeof(double) * cl.size(), cudaMemcpyHostToDevice, st),
+                  "cells");
+    if (r != FLR_OK) return r;
+    if (n_structs > 1) {
+        k_struct_of<<<std::min(n_structs, 65535), 256, 0, st>>>(nl->offsets_d, n_structs, nl->struct_of);
+        count_launch(ctx);
+    }
+    const int32_t *sof = n_structs > 1 ? nl->struct_of : nullptr;
+    std::vector<float> bb(8 * (size_t)n_structs, 0.f);
+    if (n > 0) {
+        const int nb8 = std::max(1, std::min((8 * n_structs + 255) / 256, 1024));
+        k_bbox_init<<<nb8, 256, 0, st>>>(reinterpret_cast<int *>(nl->bbox), n_structs);
+        const int grid = std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));
+        k_bbox<<<grid, 256, 0, st>>>(pos, n, nl->plans_d, sof, reinterpret_cast<int *>(nl->bbox));
+        k_bbox_finish<<<nb8, 256, 0, st>>>(reinterpret_cast<int *>(nl->bbox), n_structs);
+        count_launch(ctx, 3);
+        r = cuda_fail(cudaMemcpyAsync(bb.data(), nl->bbox, sizeof(float) * bb.size(), cudaMemcpyDeviceToHost, st),
+                      "bbox");
+        if (r == FLR_OK) r = cuda_fail(cudaStreamSynchronize(st), "bbox");
+        if (r != FLR_OK) return r;
+    }
+    const double rc = ctx->p.r_cut + ctx->p.skin;
+    long long base = 0;
+    for (int s = 0; s < n_structs; ++s) {
+        Plan &P = nl->plans_h[s];
+        r = plan_grid(P, bb.data() + 8 * s, rc, 2.0 * rc);
+        if (r != FLR_OK) return r;
+        P.bin_base = base;
+        base += P.nbins;
+    }
+    if (base > (1ll << 28)) {
+        set_error("neighbour build: too many bins in the batch");
+        return FLR_EINVAL;
+    }
+    nl->nbins_total = base;
+    if (base + 1 > nl->nbins_cap) {
         cudaFree(nl->bin_start);
         cudaFree(nl->bin_fill);
         nl->bin_start = nullptr;
         nl->bin_fill = nullptr;
-        long long cap = nbins + 1024;
+        const long long cap = base + 1024;
         cudaError_t e = cudaMalloc(&nl->bin_start, sizeof(int32_t) * (cap + 1));
         if (e == cudaSuccess) e = cudaMalloc(&nl->bin_fill, sizeof(int32_t) * (cap + 1));
         if (e != cudaSuccess) return cuda_fail(e, "allocating bins");
         nl->nbins_cap = cap;
     }
+    nl->plan = nl->plans_h[0];
     nl->planned = true;
-    return FLR_OK;
-}
-
-int launch_bbox(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, int n, cudaStream_t st)
-{
-    InvArg inv;
-    for (int c = 0; c < 9; ++c) inv.m[c] = nl->plan.inv[c];
-    k_bbox_init<<<1, 32, 0, st>>>(reinterpret_cast<int *>(nl->bbox));
-    int grid = std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));
-    k_bbox<<<grid, 256, 0, st>>>(pos, n, inv, reinterpret_cast<int *>(nl->bbox));
-    k_bbox_finish<<<1, 32, 0, st>>>(reinterpret_cast<int *>(nl->bbox));
-    count_launch(ctx, 3);
-    return cuda_fail(cudaGetLastError(), "bbox");
+    return cuda_fail(cudaMemcpyAsync(nl->plans_d, nl->plans_h, sizeof(Plan) * n_structs, cudaMemcpyHostToDevice, st),
+                     "plans");
 }
 
 int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                    cudaStream_t st, bool wrap_positions, float4 *pos_mut)
 {
-    const Plan &P = nl->plan;
     const Dims &D = ctx->dims;
-    const long long nbins = P.nbins;
+    const long long nbins = nl->nbins_total;
     const int nbb = (int)((nbins + kScanBlock - 1) / kScanBlock);
     if (nbb > kScanBlock * 64) {
-        set_error("flr_build_neighbors: too many bins");
+        set_error("neighbour build: too many bins");
         return FLR_EINVAL;
     }
-    InvArg inv;
-    for (int c = 0; c < 9; ++c) inv.m[c] = P.inv[c];
-    CellArg cell;
-    for (int c = 0; c < 9; ++c) cell.c[c] = P.cell[c];
+    const int32_t *sof = nl->n_structs > 1 ? nl->struct_of : nullptr;
 
     k_zero_bins<<<std::max(1, (int)std::min<long long>((nbins + 255) / 256, 65535)), 256, 0, st>>>(
         nl->bin_fill, nbins, nl->flags);
@@ -648,14 +758,8 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     b.pos = pos;
     b.pos_mut = wrap_positions ? pos_mut : nullptr;
     b.n = n;
-    b.inv = inv;
-    b.cell = cell;
-    for (int d = 0; d < 3; ++d) {
-        b.nb[d] = P.nb[d];
-        b.pbc[d] = P.pbc[d];
-        b.flo[d] = P.flo[d];
-        b.fspan[d] = P.fspan[d];
-    }
+    b.plans = nl->plans_d;
+    b.struct_of = sof;
     b.atom_bin = nl->atom_bin;
     b.img = nl->img;
     b.bin_count = nl->bin_fill;
@@ -663,17 +767,17 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     b.gtab = nl->gtab;
     b.flags = nl->flags;
     b.status = ctx->status;
-    k_bin<<<std::min((n + 255) / 256, ctx->num_sms * 8), 256, 0, st>>>(b);
+    k_bin<<<std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8)), 256, 0, st>>>(b);
 
     // bin_start = exclusive scan of counts; block sums live in blk_group's tail
     int32_t *bsums = nl->blk_group + (size_t)8 * ((nl->n_cap + kGroupBlock - 1) / kGroupBlock + 1);
     k_scan_blocks<<<nbb, kScanBlock, 0, st>>>(nl->bin_fill, nl->bin_start, bsums, nbins, nl->flags);
     k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, nl->bin_start + nbins, nl->flags, ctx->status);
     k_scan_add<<<nbb, kScanBlock, 0, st>>>(nl->bin_start, nl->bin_fill, bsums, nbins, nl->flags);
-    k_scatter<<<std::min((n + 255) / 256, ctx->num_sms * 8), 256, 0, st>>>(nl->atom_bin, nl->bin_fill,
-                                                                          nl->bin_atoms, n, nl->flags);
-    k_sort_bins<<<(int)std::min<long long>((nbins + 255) / 256, ctx->num_sms * 8), 256, 0, st>>>(
-        nl->bin_start, nl->bin_atoms, nbins, nl->flags);
+    k_scatter<<<std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8)), 256, 0, st>>>(nl->atom_bin, nl->bin_fill,
+                                                                                        nl->bin_atoms, n, nl->flags);
+    k_sort_bins<<<(int)std::max<long long>(1, std::min<long long>((nbins + 255) / 256, ctx->num_sms * 8)), 256, 0,
+                  st>>>(nl->bin_start, nl->bin_atoms, nbins, nl->flags);
 
     RowArgs r;
     r.pos = wrap_positions ? pos_mut : pos;
@@ -685,12 +789,8 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.n = n;
     r.max_nbr = nl->max_nbr;
     r.compaction = ctx->p.compaction;
-    for (int d = 0; d < 3; ++d) {
-        r.nb[d] = P.nb[d];
-        r.R[d] = P.R[d];
-        r.pbc[d] = P.pbc[d];
-    }
-    r.cell = cell;
+    r.plans = nl->plans_d;
+    r.struct_of = sof;
     const double rc = ctx->p.r_cut + ctx->p.skin;
     r.rc2 = (float)(rc * rc);
     r.rc2d = rc * rc;
@@ -734,9 +834,10 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
 // pool) and callers that hold no library context.  This entry point runs the
 // same cell-list kernels as flr_build_neighbors, but every buffer besides the
 // caller's inputs and outputs (bin counts and starts, the per-atom bin and
-// image tables, the bin-sorted atom order, scan block sums, the status word)
-// lives in one file-scope device array of fixed size, kNoAllocBytes (about
-// 2.6 MB), that each GPU loading this library keeps until the process exits.
+// image tables, the bin-sorted atom order, scan block sums, the grid plan,
+// the status word) lives in one file-scope device array of fixed size,
+// kNoAllocBytes (about 2.6 MB), that each GPU loading this library keeps
+// until the process exits.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -749,7 +850,7 @@ constexpr size_t kNoAllocBytes =
     (size_t)kNoAllocMaxAtoms * (5 * sizeof(int32_t) + sizeof(float4)) +   // bin, img, sorted atoms, group, spare; pos_ref
     (size_t)2 * (kNoAllocMaxBins + 2) * sizeof(int32_t) +                  // bin starts, bin fill
     (size_t)(kNoAllocMaxBins / kScanBlock + 2) * sizeof(int32_t) +         // scan block sums
-    4096;                                                                   // flags, status, bbox, group table
+    4096;                                                                   // flags, status, bbox, plan, group table
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[256];   // device address of g_noalloc_scratch, per device ordinal
@@ -826,6 +927,7 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     int32_t *flags = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * 4));
     int *status = reinterpret_cast<int *>(take(sizeof(int) * 4));
     float *bbox = reinterpret_cast<float *>(take(sizeof(float) * 8));
+    Plan *plan_d = reinterpret_cast<Plan *>(take(sizeof(Plan)));
     GroupTab *gtab = reinterpret_cast<GroupTab *>(take(sizeof(GroupTab)));
     if (q > static_cast<unsigned char *>(base) + kNoAllocBytes) {
         set_error("flr_build_neighbors_noalloc: scratch layout exceeds the array");
@@ -834,77 +936,46 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
 
     // bin grid from the fractional bounding box (host reads six floats)
     Plan P;
-    for (int k = 0; k < 9; ++k) P.cell[k] = sys->cell[k];
-    inverse3(sys->cell, P.inv);
-    if (!std::isfinite(P.inv[0]) || !std::isfinite(P.inv[4]) || !std::isfinite(P.inv[8])) {
+    std::memset(&P, 0, sizeof(P));
+    if (!plan_cell(P, sys->cell, sys->pbc)) {
         set_error("flr_build_neighbors_noalloc: singular cell");
         return FLR_EINVAL;
     }
-    InvArg inv;
-    for (int c = 0; c < 9; ++c) inv.m[c] = P.inv[c];
+    s = cuda_fail(cudaMemcpyAsync(plan_d, &P, sizeof(Plan), cudaMemcpyHostToDevice, st), "plan");
+    if (s != FLR_OK) return s;
     const float4 *pos = reinterpret_cast<const float4 *>(sys->pos);
-    k_bbox_init<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox));
-    k_bbox<<<std::max(1, std::min((n + 255) / 256, num_sms * 8)), 256, 0, st>>>(pos, n, inv,
+    k_bbox_init<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox), 1);
+    k_bbox<<<std::max(1, std::min((n + 255) / 256, num_sms * 8)), 256, 0, st>>>(pos, n, plan_d, nullptr,
                                                                               reinterpret_cast<int *>(bbox));
-    k_bbox_finish<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox));
-    float bb[6];
+    k_bbox_finish<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox), 1);
+    float bb[8];
     s = cuda_fail(cudaMemcpyAsync(bb, bbox, sizeof(bb), cudaMemcpyDeviceToHost, st), "bbox");
     if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "bbox");
     if (s != FLR_OK) return s;
-    const double margin = 2.0 * r_list;
-    long long nbins = 1;
-    for (int d = 0; d < 3; ++d) {
-        const double wd = width(sys->cell, d);
-        double flo = 0.0, fspan = 1.0;
-        P.pbc[d] = sys->pbc[d] ? 1 : 0;
-        if (!sys->pbc[d]) {
-            double lo = bb[d], hi = bb[3 + d];
-            if (!(hi >= lo)) { lo = 0.0; hi = 0.0; }
-            flo = lo - margin / wd;
-            fspan = (hi - lo) + 2.0 * margin / wd;
-        }
-        const double extent = fspan * wd;
-        int nb = (int)std::floor(extent / (r_list * 1.0001));
-        nb = std::max(1, std::min(nb, 4096));
-        int R = (int)std::ceil(r_list / (extent / nb) * (1.0 + 1e-6));
-        if (!sys->pbc[d]) R = std::min(R, nb);
-        if (sys->pbc[d] && R > 2 * nb + 1) {
-            set_error("flr_build_neighbors_noalloc: periodic cell too narrow for r_list");
-            return FLR_EINVAL;
-        }
-        P.nb[d] = nb;
-        P.R[d] = R;
-        P.flo[d] = (float)flo;
-        P.fspan[d] = (float)fspan;
-        nbins *= nb;
-    }
+    s = plan_grid(P, bb, r_list, 2.0 * r_list);
+    if (s != FLR_OK) return s;
+    const long long nbins = P.nbins;
     if (nbins > kNoAllocMaxBins) {
         set_error("flr_build_neighbors_noalloc: the bin grid needs " + std::to_string(nbins) +
                   " bins, above the fixed scratch limit of " + std::to_string(kNoAllocMaxBins));
         return FLR_EINVAL;
     }
+    P.bin_base = 0;
     // the array keeps the previous call's contents: reset what must start at zero
-    s = cuda_fail(cudaMemsetAsync(status, 0, sizeof(int) * 4, st), "reset scratch");
+    s = cuda_fail(cudaMemcpyAsync(plan_d, &P, sizeof(Plan), cudaMemcpyHostToDevice, st), "plan");
+    if (s == FLR_OK) s = cuda_fail(cudaMemsetAsync(status, 0, sizeof(int) * 4, st), "reset scratch");
     if (s == FLR_OK) s = cuda_fail(cudaMemsetAsync(flags, 0, sizeof(int32_t) * 4, st), "reset scratch");
     if (s == FLR_OK) s = cuda_fail(cudaMemsetAsync(flags, 1, 1, st), "reset scratch");   // rebuild flag on
     if (s != FLR_OK) return s;
 
-    CellArg cell;
-    for (int c = 0; c < 9; ++c) cell.c[c] = P.cell[c];
     k_zero_bins<<<std::max(1, (int)std::min<long long>((nbins + 255) / 256, 65535)), 256, 0, st>>>(bin_fill, nbins,
                                                                                                    flags);
     BinArgs b;
     b.pos = pos;
     b.pos_mut = nullptr;
     b.n = n;
-    b.inv = inv;
-    b.cell = cell;
-    for (int d = 0; d < 3; ++d) {
-        b.nb[d] = P.nb[d];
-        b.pbc[d] = P.pbc[d];
-        b.flo[d] = P.flo[d];
-        b.fspan[d] = P.fspan[d];
-    }
+    b.plans = plan_d;
+    b.struct_of = nullptr;
     b.atom_bin = atom_bin;
     b.img = img;
     b.bin_count = bin_fill;
@@ -912,14 +983,15 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     b.gtab = gtab;
     b.flags = flags;
     b.status = status;
-    k_bin<<<std::min((n + 255) / 256, num_sms * 8), 256, 0, st>>>(b);
+    k_bin<<<std::max(1, std::min((n + 255) / 256, num_sms * 8)), 256, 0, st>>>(b);
     const int nbb = (int)((nbins + kScanBlock - 1) / kScanBlock);
     k_scan_blocks<<<nbb, kScanBlock, 0, st>>>(bin_fill, bin_start, bsums, nbins, flags);
     k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, bin_start + nbins, flags, status);
     k_scan_add<<<nbb, kScanBlock, 0, st>>>(bin_start, bin_fill, bsums, nbins, flags);
-    k_scatter<<<std::min((n + 255) / 256, num_sms * 8), 256, 0, st>>>(atom_bin, bin_fill, bin_atoms, n, flags);
-    k_sort_bins<<<(int)std::min<long long>((nbins + 255) / 256, num_sms * 8), 256, 0, st>>>(bin_start, bin_atoms,
-                                                                                             nbins, flags);
+    k_scatter<<<std::max(1, std::min((n + 255) / 256, num_sms * 8)), 256, 0, st>>>(atom_bin, bin_fill, bin_atoms, n,
+                                                                                  flags);
+    k_sort_bins<<<(int)std::max<long long>(1, std::min<long long>((nbins + 255) / 256, num_sms * 8)), 256, 0, st>>>(
+        bin_start, bin_atoms, nbins, flags);
     RowArgs r;
     r.pos = pos;
     r.species = sys->species;
@@ -930,12 +1002,8 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     r.n = n;
     r.max_nbr = max_nbr;
     r.compaction = 1;
-    for (int d = 0; d < 3; ++d) {
-        r.nb[d] = P.nb[d];
-        r.R[d] = P.R[d];
-        r.pbc[d] = P.pbc[d];
-    }
-    r.cell = cell;
+    r.plans = plan_d;
+    r.struct_of = nullptr;
     r.rc2 = (float)(r_list * r_list);
     r.rc2d = r_list * r_list;
     r.entries = entries;

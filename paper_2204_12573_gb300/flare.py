@@ -257,3 +257,79 @@ def md_step(ff: FlareGB, state: MDState, nl: NbrList, n_steps: int, out, stream=
 
 def sync(ff: FlareGB, stream=None):
     ff.sync(stream)
+
+
+class Batch:
+    """Several structures of different sizes and cells evaluated together.
+
+    Atoms are concatenated on the device (pos [n, 4] float32, species [n]
+    int32); offsets, cells and pbc stay on the host (they describe the batch
+    to the library, which copies what the kernels need)."""
+
+    def __init__(self, pos, species, offsets, cells, pbc):
+        self.pos = pos
+        self.species = species
+        self.offsets = np.ascontiguousarray(offsets, np.int32)
+        self.cells = np.ascontiguousarray(np.asarray(cells, np.float64).reshape(-1, 9))
+        self.pbc = np.ascontiguousarray(np.asarray(pbc, np.int32).reshape(-1, 3))
+
+    @property
+    def n_atoms(self):
+        return int(self.pos.shape[0])
+
+    @property
+    def n_structs(self):
+        return int(len(self.offsets) - 1)
+
+    @staticmethod
+    def from_structures(structs, device="cuda"):
+        """structs: objects with .pos (float64 [n, 3]), .species, .cell, .pbc."""
+        from .synth import as_f32_positions
+        pos = np.concatenate([as_f32_positions(s.pos) for s in structs], axis=0)
+        sp = np.concatenate([np.asarray(s.species, np.int32) for s in structs])
+        offsets = np.concatenate([[0], np.cumsum([len(s.species) for s in structs])]).astype(np.int32)
+        return Batch(torch.as_tensor(pos, device=device), torch.as_tensor(sp, device=device), offsets,
+                     np.stack([np.asarray(s.cell, np.float64).ravel() for s in structs]),
+                     np.stack([np.asarray(s.pbc, np.int32) for s in structs]))
+
+    def c_struct(self):
+        b = N.Batch()
+        b.n_structs = self.n_structs
+        b.n_atoms = self.n_atoms
+        b.pos = _ptr(self.pos)
+        b.species = _ptr(self.species)
+        b.offsets = self.offsets.ctypes.data_as(ctypes.c_void_p)
+        b.cells = self.cells.ctypes.data_as(ctypes.c_void_p)
+        b.pbc = self.pbc.ctypes.data_as(ctypes.c_void_p)
+        return b
+
+
+def build_neighbors_batch(ff: FlareGB, batch: Batch, nl: NbrList, stream=None):
+    """Neighbour lists of every structure of a batch (synchronizes once)."""
+    b = batch.c_struct()
+    N.check(ff.lib.flr_build_neighbors_batch(ff.handle, ctypes.byref(b), nl.handle, _stream(stream)))
+
+
+def energy_forces_uncertainty_batch(ff: FlareGB, batch: Batch, nl: NbrList, out=None, stream=None):
+    """Per-atom outputs over the whole batch; out["totals"] is [n_structs, 16]."""
+    if out is None:
+        out = make_outputs(batch.n_atoms)
+        out["totals"] = torch.zeros((batch.n_structs, N.NTOTALS), dtype=torch.float64, device="cuda")
+    b = batch.c_struct()
+    o = _outputs_struct(out)
+    N.check(ff.lib.flr_energy_forces_uncertainty_batch(ff.handle, ctypes.byref(b), nl.handle, ctypes.byref(o),
+                                                       _stream(stream)))
+    return out
+
+
+def energy_backward(ff: FlareGB, batch: Batch, nl: NbrList, grad_energy, want_beta=True, stream=None):
+    """(dL/dpos [n, 3], dL/dbeta [S, d, d] or None) for L = sum_i grad_energy[i] * E_i."""
+    n = batch.n_atoms
+    gpos = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    gbeta = (torch.empty((ff.n_species, ff.d_full, ff.d_full), dtype=torch.float32, device="cuda")
+             if want_beta else None)
+    u = grad_energy.detach().to(device="cuda", dtype=torch.float32).contiguous()
+    b = batch.c_struct()
+    N.check(ff.lib.flr_energy_backward(ff.handle, ctypes.byref(b), nl.handle, _ptr(u), _ptr(gpos), _ptr(gbeta),
+                                       _stream(stream)))
+    return gpos, gbeta
