@@ -422,6 +422,10 @@ def run_ours(args):
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "note": "per step: H2D pos+vel (pinned), md_step, D2H energy, forces, sigma, pos, vel"}
 
+    serving = None
+    if args.serving_seconds > 0:
+        serving = run_serving(args, beta, sigma)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(struct, beta, sigma, target_s=args.ref_seconds)
@@ -438,10 +442,44 @@ def run_ours(args):
                 "kernels_ms_per_step_fp32": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_fp32.items()}
                 if prof_fp32 else None,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk}
+                "clocks": clk, "serving": serving}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+SERVING_RATES = (50, 150, 500, 1500, 5000)
+
+
+def run_serving(args, beta, sigma):
+    """Open-loop serving: Poisson arrivals at each rate, requests drawn from
+    a pool of 64 Pt(111)+H2 structures whose sizes are the midpoints of 64
+    equal-probability strata of log-uniform[32, 200000] atoms (mean 22.9k);
+    3xBF16; 150 GB admission budget.  Latency = output written - scheduled
+    arrival (host pinned staging, H2D, neighbour build, evaluation, D2H)."""
+    from paper_2204_12573_gb300 import flare as F
+    from paper_2204_12573_gb300 import synth
+    from paper_2204_12573_gb300.serving import Server, log_uniform_sizes, open_loop
+    rng = np.random.default_rng(4)
+    pool = []
+    for n in log_uniform_sizes(64):
+        s = synth.serving_structure(rng, int(n))
+        pool.append((synth.as_f32_positions(s.pos), s.species, s.cell, s.pbc))
+    ff = F.FlareGB(precision="bf16x3", max_nbr=64)
+    ff.set_model(beta, sigma)
+    res = []
+    with Server(ff, budget_bytes=150e9) as srv:
+        open_loop(srv, pool, rate=5000, seconds=0.5, seed=99)   # warm-up: grows the buffers
+        for rate in SERVING_RATES:
+            r = open_loop(srv, pool, rate=rate, seconds=args.serving_seconds, seed=4)
+            res.append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()})
+        st = srv.stats()
+    mean_atoms = float(np.mean([len(p[1]) for p in pool]))
+    return {"rates": res, "budget_gb": 150, "seconds_per_rate": args.serving_seconds,
+            "pool": f"64 structures, {min(len(p[1]) for p in pool)}-{max(len(p[1]) for p in pool)} atoms, "
+                    f"mean {mean_atoms:.0f}", "precision": "bf16x3",
+            "bytes_per_atom": st["bytes_per_atom"], "reserved_gb": round(st["reserved_bytes"] / 1e9, 2),
+            "max_batch_atoms": st["max_batch_atoms_seen"]}
 
 
 def main():
@@ -456,6 +494,8 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="time only the MD steps at --precision (for ncu launch lists)")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--serving-seconds", type=float, default=3.0,
+                    help="open-loop serving run per arrival rate (0: skip)")
     ap.add_argument("--small", action="store_true",
                     help="64x64x32 slab + 1024 H2 (132k atoms) instead of the 2.1M-atom slab")
     args = ap.parse_args()

@@ -271,6 +271,100 @@ int64_t flr_launch_count(const flr_ctx *ctx);
 int flr_build_neighbors_noalloc(const flr_system *sys, double r_list, int32_t max_nbr, int32_t *entries,
                                 int32_t *count, flr_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching evaluation loop.  (No counterpart in the
+ * paper, whose structures run one per MD job; each request is evaluated by
+ * the same calls as flr_energy_forces_uncertainty_batch, Eq. 1 and Eq. 2
+ * per atom, so a request's per-atom results do not depend on what else
+ * shares its batch.)
+ *
+ * A server owns one worker thread and one CUDA stream on the context's
+ * device.  flr_server_submit() queues a request (host inputs, host outputs)
+ * and returns at once.  The worker takes queued requests in arrival order
+ * into one batch while the batch's device memory stays within the budget
+ * (and within max_batch_structs / max_batch_atoms), packs them into pinned
+ * memory, copies them to the device in one transfer per array, plans the
+ * bin grids on the host (no mid-batch synchronization), runs the neighbour
+ * build and evaluation, copies the results back and writes them to each
+ * request's output arrays.  Packing the next batch and unpacking the last
+ * one overlap the GPU work of the current one.  Finished requests are
+ * collected with flr_server_poll().
+ *
+ * While a server exists its worker is the only user of the context: make no
+ * other call on that context (or its neighbour lists) until
+ * flr_server_destroy() returns.
+ * ------------------------------------------------------------------------ */
+typedef struct flr_server flr_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;     /* device memory the batches may use (workspace, neighbour list, I/O);
+                                    the model tables (a few MB) are outside it */
+    int32_t max_batch_structs;   /* <= 0: no limit besides memory */
+    int32_t max_batch_atoms;     /* <= 0: no limit besides memory */
+} flr_server_params;
+
+/* One structure to evaluate.  Inputs are host arrays read during
+ * flr_server_submit() (copied; they may be reused when it returns).
+ * Outputs are host arrays written by the worker before the request's
+ * completion is reported; they must stay valid until then.  Any output
+ * may be NULL. */
+typedef struct {
+    int32_t n_atoms;
+    const float *pos;            /* host float[n][4] (x, y, z, unused) */
+    const int32_t *species;      /* host int32[n] */
+    double cell[9];              /* rows are lattice vectors */
+    int32_t pbc[3];
+    float *energy;               /* host float[n] */
+    float *forces;               /* host float[n][3] */
+    float *variance;             /* host float[n] */
+    float *sigma;                /* host float[n] */
+    double *totals;              /* host double[FLR_NTOTALS] */
+    uint64_t tag;                /* returned in the completion */
+} flr_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;              /* FLR_OK, or the error of the batch that held the request */
+    int32_t batch_structs;       /* structures in that batch */
+    int64_t batch_atoms;         /* atoms in that batch */
+    int64_t t_submit_ns;         /* steady-clock times: submitted, batch enqueued on the GPU, */
+    int64_t t_start_ns;          /* outputs written */
+    int64_t t_done_ns;
+} flr_completion;
+
+typedef struct {
+    int64_t requests;            /* completed requests */
+    int64_t batches;
+    int64_t atoms;               /* atoms evaluated */
+    int64_t max_batch_atoms_seen;
+    int64_t queued;              /* requests waiting now */
+    int64_t reserved_bytes;      /* device memory the server holds now */
+    int64_t bytes_per_atom;      /* admission cost of one atom */
+    char last_error[256];        /* message of the last failed batch ("" if none) */
+} flr_server_stats;
+
+/* Device bytes one atom of a batch costs (workspace, neighbour list row,
+ * I/O), the figure the admission check multiplies by the atom count. */
+int flr_bytes_per_atom(const flr_ctx *ctx, int64_t *bytes);
+
+/* Start a server on ctx (the model must be set).  FLR_EBUDGET if the budget
+ * cannot hold a single atom. */
+int flr_server_create(flr_ctx *ctx, const flr_server_params *params, flr_server **out);
+
+/* Queue one request (thread-safe).  FLR_EBUDGET if the request alone
+ * exceeds the budget or max_batch_atoms; FLR_EINVAL for invalid input. */
+int flr_server_submit(flr_server *srv, const flr_request *req);
+
+/* Collect up to max finished requests into out[0 .. *n_out - 1], waiting up
+ * to wait_seconds for the first one (0: do not wait). */
+int flr_server_poll(flr_server *srv, flr_completion *out, int32_t max, int32_t *n_out, double wait_seconds);
+
+int flr_server_stats_read(flr_server *srv, flr_server_stats *stats);
+
+/* Stop the worker after the batch in flight and free the server.  Requests
+ * still queued are dropped without a completion. */
+int flr_server_destroy(flr_server *srv);
+
 /* Kernel classes of flr_profile_read. */
 #define FLR_KERNEL_DESCRIPTOR 0   /* A, B2, normalization (one launch per evaluation) */
 #define FLR_KERNEL_QFORM 1        /* quadratic-form GEMM (SIMT or tcgen05) */

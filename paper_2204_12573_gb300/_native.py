@@ -39,6 +39,8 @@ EXPORTED = [
     "flr_energy_forces_uncertainty", "flr_md_step", "flr_sync", "flr_launch_count",
     "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
     "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
+    "flr_bytes_per_atom", "flr_server_create", "flr_server_submit", "flr_server_poll", "flr_server_stats_read",
+    "flr_server_destroy",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
@@ -71,6 +73,31 @@ class MDState(ctypes.Structure):
                 ("species", ctypes.c_void_p), ("cell", ctypes.c_double * 9), ("pbc", ctypes.c_int32 * 3),
                 ("masses", ctypes.c_double * 8), ("dt", ctypes.c_double), ("rebuild_every", ctypes.c_int32),
                 ("forces_valid", ctypes.c_int32), ("step", ctypes.c_int64)]
+
+
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_structs", ctypes.c_int32),
+                ("max_batch_atoms", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("pos", ctypes.c_void_p), ("species", ctypes.c_void_p),
+                ("cell", ctypes.c_double * 9), ("pbc", ctypes.c_int32 * 3), ("energy", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("totals", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_structs", ctypes.c_int32),
+                ("batch_atoms", ctypes.c_int64), ("t_submit_ns", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("batches", ctypes.c_int64), ("atoms", ctypes.c_int64),
+                ("max_batch_atoms_seen", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("reserved_bytes", ctypes.c_int64), ("bytes_per_atom", ctypes.c_int64),
+                ("last_error", ctypes.c_char * 256)]
 
 
 class FlareError(RuntimeError):
@@ -115,6 +142,13 @@ def lib():
             "flr_energy_forces_uncertainty_batch": (ctypes.c_int, [P, ctypes.POINTER(Batch), P,
                                                                    ctypes.POINTER(Outputs), P]),
             "flr_energy_backward": (ctypes.c_int, [P, ctypes.POINTER(Batch), P, P, P, P, P]),
+            "flr_bytes_per_atom": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int64)]),
+            "flr_server_create": (ctypes.c_int, [P, ctypes.POINTER(ServerParams), ctypes.POINTER(P)]),
+            "flr_server_submit": (ctypes.c_int, [P, ctypes.POINTER(Request)]),
+            "flr_server_poll": (ctypes.c_int, [P, ctypes.POINTER(Completion), ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_double]),
+            "flr_server_stats_read": (ctypes.c_int, [P, ctypes.POINTER(ServerStats)]),
+            "flr_server_destroy": (ctypes.c_int, [P]),
             "flr_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_int64)]),
         }

@@ -49,8 +49,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     objdir = os.path.join(OUT, "obj")
     os.makedirs(objdir, exist_ok=True)
     hdrs = _headers()
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-             "-I", INCLUDE] + ARCH + list(extra_flags or [])
+    # host code: no floating-point contraction (the host-side bounding boxes
+    # of the serving loop must round like the device's)
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+             "--expt-relaxed-constexpr", "-I", INCLUDE] + ARCH + list(extra_flags or [])
     if verbose:
         flags += ["-Xptxas", "-v"]
     jobs = []
@@ -70,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
                 raise RuntimeError(f"nvcc failed on {cmd[2]}")
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -313,6 +313,36 @@ int check_batch(const flr_ctx *ctx, const flr_nbrlist *nl, const flr_batch *b)
 }
 
 }  // namespace
+
+// Entry points of the serving loop (server.cu) into this file's helpers.
+int srv_reserve_workspace(flr_ctx *ctx, int n) { return ensure_workspace(ctx, n); }
+
+int srv_evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                 flr_outputs *out, double *seg_totals, cudaStream_t st)
+{
+    KickArgs none;
+    std::memset(&none, 0, sizeof(none));
+    return evaluate(ctx, nl, pos, species, n, out, none, st, seg_totals);
+}
+
+int srv_status_code(int st) { return status_to_code(st); }
+
+int srv_check_model(const flr_ctx *ctx) { return check_model(ctx); }
+
+// Device bytes per atom of one evaluation: the workspace (ensure_workspace),
+// a neighbour-list row and its per-atom tables (flr_nbrlist_create), and
+// the serving I/O arrays (positions, species, E, F, V, sigma).
+int64_t bytes_per_atom(const flr_ctx *ctx)
+{
+    const Dims &D = ctx->dims;
+    int64_t b = 4 * (int64_t)D.nA + 4;
+    for (int r = 0; r < 2; ++r) b += 4 * (int64_t)D.kp32[r] + 2 * 2 * (int64_t)D.kp64[r] + 4 * 3 * (int64_t)D.K[r];
+    b += 8 * 3 + 4 * 9 + 4 * 3;
+    b += 4 * (int64_t)ctx->p.max_nbr + 4 * 8 + 16 + 1;
+    b += 16 + 4 + 4 * 6;
+    return b;
+}
+
 }  // namespace flr
 
 using namespace flr;

@@ -32,6 +32,7 @@ constexpr int kAStride = 20;                  // float4-aligned, conflict-free A
 constexpr int kSlots = 4;                     // atoms whose w may be referenced by queued pairs
 constexpr int kWSlot = 2 * 16 * 8 + 4;        // floats per w slot: [species][lm][n (8, padded)] + pad
 constexpr float kFixScale = 4294967296.0f;    // 2^32
+constexpr double kFixInv = 1.0 / 4294967296.0;
 
 struct ForceArgs {
     const float4 *pos;
@@ -57,8 +58,8 @@ struct ForceSmem {
     float A[kWarpsForce][2 * N * kAStride];
     float W[kWarpsForce][kSlots * kWSlot];
     float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
-    float F[kWarpsForce][kSlots][3];             // F_i of each slot's atom, summed in a fixed order
-    float V[kWarpsForce][kSlots][9];             // virial of each slot's atom (when requested)
+    long long F[kWarpsForce][kSlots][3];         // F_i of each slot's atom, fixed point
+    long long V[kWarpsForce][kSlots][9];         // virial of each slot's atom (when requested), fixed point
     int atom[kWarpsForce][kSlots];
     int qseq[kWarpsForce][64];                  // atom sequence number of each queued pair
     float vir[kWarpsForce][9];
@@ -82,7 +83,7 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
                                             unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     int my_slot = -1;
-    float f3[3] = {0.f, 0.f, 0.f};
+    long long f3[3] = {0, 0, 0};   // f_ij in fixed point: F_i gets exactly what F_j loses
     float dv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (lane < m) {
         const float4 rec = sm.q[w][lane];
@@ -134,35 +135,40 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
 #pragma unroll
         for (int k = 0; k < 9; ++k) vir[k] += dv[k];
         my_slot = slot;
-        f3[0] = fx;
-        f3[1] = fy;
-        f3[2] = fz;
+        f3[0] = ix;
+        f3[1] = iy;
+        f3[2] = iz;
     }
-    // F_i: the batch's pairs belong to at most kSlots atoms; sum each atom's
-    // pairs with a fixed-order warp reduction (deterministic) into its slot
+    // F_i (and the atom's virial): the queue is filled atom by atom, so each
+    // slot's pairs occupy consecutive lanes.  A segmented inclusive scan over
+    // the lanes sums every slot at once; the sums are integers (fixed point),
+    // so they do not depend on how an atom's pairs were split over batches.
+    const int prev_slot = __shfl_up_sync(0xffffffffu, my_slot, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane < m && (lane == 0 || my_slot != prev_slot));
+    const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // -1 when no head at or below
+    const bool next_is_head = lane < 31 && ((heads >> (lane + 1)) & 1u);
+    const unsigned tails = __ballot_sync(0xffffffffu, lane < m && (lane == m - 1 || next_is_head));
+    const bool is_tail = (tails >> lane) & 1u;
 #pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-        if (!__any_sync(0xffffffffu, my_slot == s)) continue;
-        float v[3];
+    for (int c = 0; c < 3; ++c) {
+        long long x = f3[c];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            v[c] = my_slot == s ? f3[c] : 0.f;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane - o >= head) x += y;
         }
-        if (lane == 0) {
-            sm.F[w][s][0] += v[0];
-            sm.F[w][s][1] += v[1];
-            sm.F[w][s][2] += v[2];
-        }
-        if (want_vatom) {
+        if (is_tail) sm.F[w][my_slot][c] += x;
+    }
+    if (want_vatom) {
 #pragma unroll
-            for (int c = 0; c < 9; ++c) {
-                float x = my_slot == s ? dv[c] : 0.f;
+        for (int c = 0; c < 9; ++c) {
+            long long x = lane < m ? to_fix(dv[c], status) : 0;
 #pragma unroll
-                for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0) sm.V[w][s][c] += x;
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane - o >= head) x += y;
             }
+            if (is_tail) sm.V[w][my_slot][c] += x;
         }
     }
     __syncwarp();
@@ -200,12 +206,12 @@ __device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, in
 {
     const int i = sm.atom[w][slot];
     if (lane < 3 && i >= 0) {
-        atomicAdd(Facc + 3 * (size_t)i + lane, (unsigned long long)to_fix(sm.F[w][slot][lane], status));
-        sm.F[w][slot][lane] = 0.f;
+        atomicAdd(Facc + 3 * (size_t)i + lane, (unsigned long long)sm.F[w][slot][lane]);
+        sm.F[w][slot][lane] = 0;
     }
     if (lane < 9) {
-        if (vir_atom && i >= 0) vir_atom[9 * (size_t)i + lane] = sm.V[w][slot][lane];
-        sm.V[w][slot][lane] = 0.f;
+        if (vir_atom && i >= 0) vir_atom[9 * (size_t)i + lane] = (float)((double)sm.V[w][slot][lane] * kFixInv);
+        sm.V[w][slot][lane] = 0;
     }
     __syncwarp();
     if (lane == 0) sm.atom[w][slot] = -1;
@@ -294,8 +300,8 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
     if (lane < kSlots) sm.atom[w][lane] = -1;
-    if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0.f;
-    for (int k = lane; k < 9 * kSlots; k += 32) sm.V[w][k / 9][k % 9] = 0.f;
+    if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0;
+    for (int k = lane; k < 9 * kSlots; k += 32) sm.V[w][k / 9][k % 9] = 0;
     const bool want_vatom = a.vir_atom != nullptr;
     __syncwarp();
     int nq = 0;        // queued pairs

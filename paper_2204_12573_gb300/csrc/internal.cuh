@@ -179,8 +179,20 @@ inline void count_launch(flr_ctx *ctx, int k = 1) { ctx->launches += k; }
 // ---- launchers (one per translation unit) ----
 int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                    cudaStream_t st, bool wrap_positions, float4 *pos_mut);
+// host_bb: per-structure fractional bounding boxes float[n_structs][8]
+// computed on the host (host_frac_bbox); nullptr: computed on the device,
+// which synchronizes the stream once.
 int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
-               const int32_t *pbc, const float4 *pos, int n, cudaStream_t st);
+               const int32_t *pbc, const float4 *pos, int n, cudaStream_t st, const float *host_bb = nullptr);
+void host_frac_bbox(const double *cell, const float *pos4, int n, float bb[8]);
+int launch_set_rebuild(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
+// serving-loop access to the context (api.cu)
+int srv_reserve_workspace(flr_ctx *ctx, int n);
+int srv_evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                 flr_outputs *out, double *seg_totals, cudaStream_t st);
+int srv_status_code(int st);
+int srv_check_model(const flr_ctx *ctx);
+int64_t bytes_per_atom(const flr_ctx *ctx);
 int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                 cudaStream_t st);
 int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat, float *norm,

@@ -33,11 +33,14 @@ __device__ __forceinline__ int ordered(float f)
 }
 __device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
+// Fractional coordinates, FP64 products and sums rounded one by one (no
+// fused multiply-add), so host_frac_bbox reproduces them bit for bit.
 __device__ __forceinline__ void frac_of(const float4 &p, const double *inv, double f[3])
 {
 #pragma unroll
     for (int d = 0; d < 3; ++d)
-        f[d] = (double)p.x * inv[d] + (double)p.y * inv[3 + d] + (double)p.z * inv[6 + d];
+        f[d] = __dadd_rn(__dadd_rn(__dmul_rn((double)p.x, inv[d]), __dmul_rn((double)p.y, inv[3 + d])),
+                         __dmul_rn((double)p.z, inv[6 + d]));
 }
 
 __device__ __forceinline__ int structure_of(const int32_t *struct_of, int i) { return struct_of ? struct_of[i] : 0; }
@@ -634,8 +637,35 @@ int plan_grid(Plan &P, const float *bb, double rc, double margin)
 
 // Plan the bin grids of a batch of structures (host, synchronizes once to
 // read the bounding boxes) and upload the per-structure tables.
+// Fractional bounding box of one structure on the host with the device's
+// arithmetic (k_bbox): FP64 products and sums without fused multiply-add
+// (this file is compiled with contraction off), rounded to float.
+void host_frac_bbox(const double *cell, const float *pos4, int n, float bb[8])
+{
+    double inv[9];
+    inverse3(cell, inv);
+    float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int i = 0; i < n; ++i) {
+        const double x = pos4[4 * (size_t)i], y = pos4[4 * (size_t)i + 1], z = pos4[4 * (size_t)i + 2];
+        for (int d = 0; d < 3; ++d) {
+            const double a = x * inv[d];
+            const double b = y * inv[3 + d];
+            const double c = z * inv[6 + d];
+            const double s = a + b;
+            const float f = (float)(s + c);
+            lo[d] = std::min(lo[d], f);
+            hi[d] = std::max(hi[d], f);
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        bb[d] = lo[d];
+        bb[3 + d] = hi[d];
+    }
+    bb[6] = bb[7] = 0.f;
+}
+
 int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
-               const int32_t *pbc, const float4 *pos, int n, cudaStream_t st)
+               const int32_t *pbc, const float4 *pos, int n, cudaStream_t st, const float *host_bb)
 {
     if (n_structs < 1 || offsets[0] != 0 || offsets[n_structs] != n) {
         set_error("neighbour build: batch offsets must start at 0 and end at n_atoms");
@@ -696,7 +726,9 @@ int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offs
     }
     const int32_t *sof = n_structs > 1 ? nl->struct_of : nullptr;
     std::vector<float> bb(8 * (size_t)n_structs, 0.f);
-    if (n > 0) {
+    if (host_bb) {
+        std::memcpy(bb.data(), host_bb, sizeof(float) * bb.size());
+    } else if (n > 0) {
         const int nb8 = std::max(1, std::min((8 * n_structs + 255) / 256, 1024));
         k_bbox_init<<<nb8, 256, 0, st>>>(reinterpret_cast<int *>(nl->bbox), n_structs);
         const int grid = std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8));

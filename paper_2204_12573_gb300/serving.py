@@ -1,0 +1,202 @@
+"""Continuous-batching evaluation service (flr_server_* in the C ABI) and an
+open-loop load generator that measures its latency.
+
+    srv = Server(ff, budget_bytes=150e9)
+    tag = srv.submit(pos4, species, cell, pbc)
+    done = srv.poll(wait=0.1)          # [(tag, result dict, completion dict)]
+
+The worker loop, admission control, packing and all GPU work are native;
+this module marshals arguments and keeps each request's host output arrays
+alive until its completion is polled.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import threading
+import time
+
+import numpy as np
+
+from . import _native as N
+
+FIELDS = ("energy", "forces", "variance", "sigma", "totals")
+
+
+class Server:
+    def __init__(self, ff, budget_bytes=150e9, max_batch_structs=0, max_batch_atoms=0):
+        self.ff = ff
+        self.lib = ff.lib
+        p = N.ServerParams(int(budget_bytes), int(max_batch_structs), int(max_batch_atoms))
+        h = ctypes.c_void_p()
+        N.check(self.lib.flr_server_create(ff.handle, ctypes.byref(p), ctypes.byref(h)))
+        self.handle = h
+        self._pending = {}
+        self._lock = threading.Lock()
+        self._tags = itertools.count(1)
+        self._buf = (N.Completion * 4096)()
+
+    @staticmethod
+    def bytes_per_atom(ff):
+        b = ctypes.c_int64()
+        N.check(ff.lib.flr_bytes_per_atom(ff.handle, ctypes.byref(b)))
+        return int(b.value)
+
+    def submit(self, pos4, species, cell, pbc=(1, 1, 0), fields=FIELDS, tag=None):
+        """Queue one structure (host arrays: pos4 float32 [n, 4], species
+        int32 [n]).  Returns the request's tag."""
+        pos4 = np.ascontiguousarray(pos4, np.float32)
+        species = np.ascontiguousarray(species, np.int32)
+        n = int(pos4.shape[0])
+        out = {}
+        if "energy" in fields:
+            out["energy"] = np.empty(n, np.float32)
+        if "forces" in fields:
+            out["forces"] = np.empty((n, 3), np.float32)
+        if "variance" in fields:
+            out["variance"] = np.empty(n, np.float32)
+        if "sigma" in fields:
+            out["sigma"] = np.empty(n, np.float32)
+        if "totals" in fields:
+            out["totals"] = np.empty(N.NTOTALS, np.float64)
+        if tag is None:
+            tag = next(self._tags)
+        r = N.Request()
+        r.n_atoms = n
+        r.pos = pos4.ctypes.data_as(ctypes.c_void_p)
+        r.species = species.ctypes.data_as(ctypes.c_void_p)
+        r.cell = (ctypes.c_double * 9)(*np.asarray(cell, np.float64).ravel().tolist())
+        r.pbc = (ctypes.c_int32 * 3)(*[int(bool(v)) for v in pbc])
+        for k in ("energy", "forces", "variance", "sigma", "totals"):
+            setattr(r, k, out[k].ctypes.data_as(ctypes.c_void_p) if k in out else None)
+        r.tag = tag
+        with self._lock:
+            self._pending[tag] = out
+        code = self.lib.flr_server_submit(self.handle, ctypes.byref(r))
+        if code != N.FLR_OK:
+            with self._lock:
+                self._pending.pop(tag, None)
+            N.check(code)
+        return tag
+
+    def poll(self, wait=0.0, max_items=4096):
+        """Finished requests: a list of (tag, outputs, completion dict)."""
+        n = ctypes.c_int32()
+        N.check(self.lib.flr_server_poll(self.handle, self._buf, min(max_items, len(self._buf)), ctypes.byref(n),
+                                         float(wait)))
+        res = []
+        for k in range(n.value):
+            c = self._buf[k]
+            with self._lock:
+                out = self._pending.pop(c.tag)
+            res.append((c.tag, out, dict(status=c.status, batch_structs=c.batch_structs,
+                                         batch_atoms=c.batch_atoms, t_submit_ns=c.t_submit_ns,
+                                         t_start_ns=c.t_start_ns, t_done_ns=c.t_done_ns)))
+        return res
+
+    def wait_all(self, tags, timeout=120.0):
+        """Poll until every tag in `tags` has completed; returns {tag: (outputs, completion)}."""
+        want = set(tags)
+        got = {}
+        t_end = time.monotonic() + timeout
+        while want - set(got):
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"{len(want - set(got))} requests still pending")
+            for tag, out, c in self.poll(wait=0.05):
+                got[tag] = (out, c)
+        return got
+
+    def stats(self):
+        s = N.ServerStats()
+        N.check(self.lib.flr_server_stats_read(self.handle, ctypes.byref(s)))
+        return dict(requests=s.requests, batches=s.batches, atoms=s.atoms,
+                    max_batch_atoms_seen=s.max_batch_atoms_seen, queued=s.queued,
+                    reserved_bytes=s.reserved_bytes, bytes_per_atom=s.bytes_per_atom,
+                    last_error=s.last_error.decode())
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self.lib.flr_server_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def log_uniform_sizes(k, lo=32, hi=200_000):
+    """k sizes at the midpoints of k equal-probability strata of the
+    log-uniform distribution on [lo, hi]."""
+    q = (np.arange(k) + 0.5) / k
+    return np.exp(np.log(lo) + q * (np.log(hi) - np.log(lo))).round().astype(int)
+
+
+def percentile_ms(lat_ns, q):
+    return float(np.percentile(np.asarray(lat_ns, np.float64), q) / 1e6) if len(lat_ns) else None
+
+
+def open_loop(server, pool, rate, seconds, seed=4, drain_timeout=120.0):
+    """Poisson arrivals at `rate` requests/s for `seconds`; each request is a
+    structure drawn uniformly from `pool` (list of (pos4, species, cell,
+    pbc)).  Latency is measured from the scheduled arrival time to the moment
+    the request's outputs were written.  Returns a summary dict."""
+    rng = np.random.default_rng(seed)
+    n_req = max(1, int(rng.poisson(rate * seconds)))
+    arrivals = np.sort(rng.uniform(0.0, seconds, n_req))
+    picks = rng.integers(0, len(pool), n_req)
+    sched = {}
+    lat = []
+    atoms_done = [0]
+    batch_sizes = []
+    errors = [0]
+    finished = threading.Event()
+
+    def collect():
+        while not finished.is_set() or len(lat) + errors[0] < len(sched):
+            for tag, out, c in server.poll(wait=0.02):
+                if c["status"] != N.FLR_OK:
+                    errors[0] += 1
+                    continue
+                lat.append(c["t_done_ns"] - sched[tag][0])
+                atoms_done[0] += sched[tag][1]
+                batch_sizes.append(c["batch_structs"])
+            if finished.is_set() and time.monotonic() > t_drain_end[0]:
+                break
+
+    t_drain_end = [float("inf")]
+    th = threading.Thread(target=collect, daemon=True)
+    t0 = time.monotonic_ns()
+    th.start()
+    late = 0
+    for k in range(n_req):
+        t_arr = t0 + int(arrivals[k] * 1e9)
+        dt = (t_arr - time.monotonic_ns()) / 1e9
+        if dt > 0:
+            time.sleep(dt)
+        elif dt < -1e-3:
+            late += 1
+        pos4, species, cell, pbc = pool[picks[k]]
+        tag = k + 1
+        sched[tag] = (t_arr, len(species))
+        server.submit(pos4, species, cell, pbc, fields=("energy", "forces", "sigma"), tag=tag)
+    t_drain_end[0] = time.monotonic() + drain_timeout
+    finished.set()
+    th.join()
+    t_last = time.monotonic_ns()
+    wall = (t_last - t0) / 1e9
+    return dict(rate=rate, seconds=seconds, requests=n_req, completed=len(lat), errors=errors[0],
+                p50_ms=percentile_ms(lat, 50), p99_ms=percentile_ms(lat, 99), mean_ms=(
+                    float(np.mean(lat) / 1e6) if lat else None),
+                atoms_per_s=atoms_done[0] / wall, offered_atoms_per_s=float(
+                    sum(len(pool[p][1]) for p in picks) / seconds),
+                mean_batch_structs=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+                late_submits=late)
