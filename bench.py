@@ -191,10 +191,17 @@ class OracleSample:
         self.struct, self.beta, self.sigma = struct, beta, sigma
         self.pos = synth.f32_exact_f64(synth.as_f32_positions(struct.pos))
         self.h = O.Hyper()
-        pilot = self._block(10.0)
-        t0 = time.time()
-        self._run(pilot)
-        self.rate = len(pilot) / max(time.time() - t0, 1e-3)
+        # two pilots give the fixed cost (neighbour search over the whole slab) and the cost per atom
+        self.t_fixed, self.t_atom = 0.0, 1e-3
+        pts = []
+        for side in (10.0, 25.0):
+            blk = self._block(side)
+            t0 = time.time()
+            self._run(blk)
+            pts.append((len(blk), time.time() - t0))
+        (n1, t1), (n2, t2) = pts
+        self.t_atom = max((t2 - t1) / max(n2 - n1, 1), 1e-7)
+        self.t_fixed = max(t1 - self.t_atom * n1, 0.0)
 
     def _block(self, side):
         return np.nonzero((self.pos[:, 0] < side) & (self.pos[:, 1] < side))[0]
@@ -204,8 +211,9 @@ class OracleSample:
         self.O.forces_subset(self.h, self.pos, s.species, s.cell, s.pbc, self.beta, self.sigma, atoms, skin=0.5)
 
     def step(self, target_s):
-        pilot_n = len(self._block(10.0))
-        side = float(np.clip(10.0 * np.sqrt(self.rate * target_s / max(pilot_n, 1)), 10.0, 300.0))
+        n25 = len(self._block(25.0))
+        want = max(target_s - self.t_fixed, 0.1 * target_s) / self.t_atom
+        side = float(np.clip(25.0 * np.sqrt(want / max(n25, 1)), 10.0, 300.0))
         blk = self._block(side)
         t0 = time.time()
         self._run(blk)

@@ -339,6 +339,7 @@ int64_t bytes_per_atom(const flr_ctx *ctx)
     for (int r = 0; r < 2; ++r) b += 4 * (int64_t)D.kp32[r] + 2 * 2 * (int64_t)D.kp64[r] + 4 * 3 * (int64_t)D.K[r];
     b += 8 * 3 + 4 * 9 + 4 * 3;
     b += 4 * (int64_t)ctx->p.max_nbr + 4 * 8 + 16 + 1;
+    b += 16 * (int64_t)ctx->p.max_nbr + 4;   // pair records
     b += 16 + 4 + 4 * 6;
     return b;
 }
@@ -556,6 +557,8 @@ int flr_nbrlist_create(flr_ctx *c, int32_t n_atoms, flr_nbrlist **out)
     if (s == FLR_OK) s = dev_alloc(&nl->gtab, 1, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->flags, 4, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->struct_of, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->pair_rec, N * nl->max_nbr, "nbrlist pair records");
+    if (s == FLR_OK) s = dev_alloc(&nl->pair_cnt, N, "nbrlist pair records");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->gtab, 0, sizeof(GroupTab)), "nbrlist");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->flags, 0, 4 * sizeof(int32_t)), "nbrlist");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(nl->group, 0xff, N * sizeof(int32_t)), "nbrlist");
@@ -588,6 +591,8 @@ int flr_nbrlist_destroy(flr_nbrlist *nl)
     cudaFree(nl->flags);
     cudaFree(nl->bbox);
     cudaFree(nl->struct_of);
+    cudaFree(nl->pair_rec);
+    cudaFree(nl->pair_cnt);
     cudaFree(nl->offsets_d);
     cudaFree(nl->cells_d);
     cudaFree(nl->plans_d);

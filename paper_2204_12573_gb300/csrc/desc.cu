@@ -34,6 +34,8 @@ struct DescArgs {
     float *D32[2];
     __nv_bfloat16 *Dhi[2], *Dlo[2];
     int bf16;                  // also write BF16 hi/lo rows
+    float4 *pair_rec;          // [n][max_nbr] out: pairs inside r_cut (r_ij, j | s_j << 25)
+    int32_t *pair_cnt;         // [n] out: their number
 };
 
 template <int N>
@@ -97,13 +99,15 @@ __device__ __forceinline__ DescPre desc_preload(const DescArgs &a, int i, int la
     p.pi = make_float4(0.f, 0.f, 0.f, 0.f);
     p.e0 = p.e1 = 0;
     if (i < a.n) {
-        p.g = a.group[i];
-        p.cnt = a.count[i];
-        p.row = a.row[i];
-        p.pi = a.pos[i];
+        // read-only loads (ld.global.nc): they may be reordered around the
+        // kernel's global stores, which cannot alias them
+        p.g = __ldg(a.group + i);
+        p.cnt = __ldg(a.count + i);
+        p.row = __ldg(a.row + i);
+        p.pi = __ldg(a.pos + i);
         const int32_t *rp = a.entries + (size_t)i * a.max_nbr;
-        p.e0 = rp[lane];
-        p.e1 = a.max_nbr > 32 ? rp[32 + lane] : 0;
+        p.e0 = __ldg(rp + lane);
+        p.e1 = a.max_nbr > 32 ? __ldg(rp + 32 + lane) : 0;
     }
     return p;
 }
@@ -125,7 +129,7 @@ __device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
 }
 
 template <int N>
-__global__ void __launch_bounds__(kWarpsDesc * 32, 3) k_desc(DescArgs a)
+__global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
 {
     constexpr int C = 2 * N;
     constexpr int NPF = C * (C + 1) / 2;          // channel pairs of the full descriptor
@@ -156,22 +160,30 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 3) k_desc(DescArgs a)
 
         float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
         int nv = 0;   // staged pairs
+        int np = 0;   // pairs inside r_cut so far
+        float4 *prec = a.pair_rec + (size_t)i * a.max_nbr;
         for (int base = 0; base < cnt; base += 32) {
             const int q = base + lane;
             bool ok = false;
             float3 r = make_float3(0.f, 0.f, 0.f);
-            int sj = 0;
+            int sj = 0, j = 0;
             if (q < cnt) {
-                int j, sx, sy, sz;
-                decode_entry(base == 0 ? cur.e0 : (base == 32 ? cur.e1 : rowp[q]), j, sx, sy, sz);
-                const float4 pj = a.pos[j];
+                int sx, sy, sz;
+                decode_entry(base == 0 ? cur.e0 : (base == 32 ? cur.e1 : __ldg(rowp + q)), j, sx, sy, sz);
+                const float4 pj = __ldg(a.pos + j);
+                sj = __ldg(a.species + j);
                 r = pair_vector(pi, pj, sx, sy, sz, cl);
                 ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
-                sj = a.species[j];
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (ok) sm.rec[w][nv + __popc(m & ((1u << lane) - 1u))] = make_float4(r.x, r.y, r.z, __int_as_float(sj));
+            if (ok) {
+                const int at = __popc(m & ((1u << lane) - 1u));
+                sm.rec[w][nv + at] = make_float4(r.x, r.y, r.z, __int_as_float(sj));
+                // the force kernel reuses the pair vector instead of gathering and filtering again
+                prec[np + at] = make_float4(r.x, r.y, r.z, __int_as_float(j | ((sj & 1) << 25)));
+            }
             nv += __popc(m);
+            np += __popc(m);
             __syncwarp();
             if (nv >= 32) {
                 desc_batch<N>(sm, w, lane, 32, rc, acc0, acc1);
@@ -181,6 +193,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 3) k_desc(DescArgs a)
             }
         }
         if (nv > 0) desc_batch<N>(sm, w, lane, nv, rc, acc0, acc1);
+        if (lane == 0) a.pair_cnt[i] = np;
 
         // A to shared memory (padded rows) and to global memory (blocks in use only)
         float *sA = sm.A[w];
@@ -316,6 +329,8 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.A = ctx->A;
     a.norm = ctx->norm;
     a.bf16 = ctx->p.precision == FLR_PREC_BF16X3;
+    a.pair_rec = nl->pair_rec;
+    a.pair_cnt = nl->pair_cnt;
     if (ctx->dims.N == 8) {
         const int grid = persistent_grid(k_desc<8>, kWarpsDesc * 32, ctx->num_sms, (n + kWarpsDesc - 1) / kWarpsDesc);
         k_desc<8><<<grid, kWarpsDesc * 32, 0, st>>>(a);

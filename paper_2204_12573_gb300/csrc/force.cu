@@ -11,16 +11,19 @@
 //   f_ij = dE_i/dr_ij = sum_{n,lm} w_{(s_j,n),lm} grad phi_{n,lm}(r_ij),
 // which costs O(N L^2) per pair instead of O(d).  F_i += f_ij, F_j -= f_ij.
 //
-// Work layout: persistent warps walk the atoms.  For each atom a warp forms
-// E, V, g and w (w goes to one of four shared-memory slots), then appends
-// the atom's pairs inside r_cut to a per-warp FIFO queue; whenever 32 pairs
-// are queued they are evaluated with one pair per lane, whatever atoms they
-// belong to, so the expensive per-pair path always runs with full lanes.
-// Forces are accumulated as 64-bit fixed point (2^-32 eV/A): F_j through
-// global atomics (integer sums do not depend on arrival order), F_i by
-// fixed-order warp reductions into a per-slot FP32 sum that is added once
-// per atom.  Forces are therefore bitwise reproducible; the virial is
-// accumulated per lane in a fixed order.
+// Work layout: persistent warps walk the atoms.  For each atom a warp reads
+// g (E, V and sigma were already written by the quadratic-form epilogue),
+// unpacks it into a dense symmetric channel matrix G~ in shared memory,
+// forms w = G~ A (w goes to one of four shared-memory slots), then appends
+// the atom's pairs inside r_cut -- recorded by the descriptor kernel as
+// (r_ij, j, s_j), so nothing is gathered or filtered again -- to a per-warp
+// FIFO queue; whenever 32 pairs are queued they are evaluated with one pair
+// per lane, whatever atoms they belong to, so the expensive per-pair path
+// always runs with full lanes.  Forces are accumulated as 64-bit fixed point
+// (2^-32 eV/A): F_j through global atomics, F_i by warp reductions over the
+// lanes of each atom; integer sums do not depend on order or on how an
+// atom's pairs were split over batches, so forces are bitwise reproducible
+// and independent of what else is evaluated alongside.
 #include "basis.cuh"
 #include "internal.cuh"
 
@@ -49,12 +52,22 @@ struct ForceArgs {
     double *vir_part;          // [gridDim.x][9]
     float *vir_atom;           // [n][9] per-atom virial, or nullptr (batches of structures need it)
     const float *weight;       // [n] per-atom weights u_i on E_i (backward pass), or nullptr
+    const float4 *pair_rec;    // [n][max_nbr] pairs inside r_cut from the descriptor kernel
+    const int32_t *pair_cnt;   // [n]
+    const int32_t *tab[2];     // compact index -> channel pair (a | b << 8), per region
     int *status;
 };
 
+// Dense G~ layout for a class of CG channels: lane half h owns channels
+// [h * gd_half(CG), ...), rows b are gd_row(CG) floats apart (a multiple of
+// 8, so every float4 load is aligned), planes l are gd_plane(CG) apart.
+__host__ __device__ constexpr int gd_half(int CG) { return ((CG + 1) / 2 + 3) / 4 * 4; }
+__host__ __device__ constexpr int gd_row(int CG) { return 2 * gd_half(CG); }
+__host__ __device__ constexpr int gd_plane(int CG) { return CG * gd_row(CG) + 8; }
+
 template <int N>
 struct ForceSmem {
-    float G[kWarpsForce][(2 * N) * (2 * N + 1) / 2 * 4];
+    float Gd[kWarpsForce][4 * gd_plane(2 * N)];          // G~[l][b][a] of the widest class
     float A[kWarpsForce][2 * N * kAStride];
     float W[kWarpsForce][kSlots * kWSlot];
     float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
@@ -65,12 +78,12 @@ struct ForceSmem {
     float vir[kWarpsForce][9];
 };
 
-__device__ __forceinline__ int tri(int a, int b, int C) { return a * C - a * (a - 1) / 2 + (b - a); }
-
+// |v| must stay below 2^15 eV/A (else the status word reports a non-finite
+// or overflowing force), which keeps the warp sums below in 32-bit range.
 __device__ __forceinline__ long long to_fix(float v, int *status)
 {
     const float s = v * kFixScale;
-    if (!(fabsf(s) < 9.0e18f)) {   // also catches NaN
+    if (!(fabsf(s) < 140737488355328.0f)) {   // 2^47; also catches NaN
         atomicOr(status, kErrNonFinite);
         return 0;
     }
@@ -140,35 +153,39 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
         f3[2] = iz;
     }
     // F_i (and the atom's virial): the queue is filled atom by atom, so each
-    // slot's pairs occupy consecutive lanes.  A segmented inclusive scan over
-    // the lanes sums every slot at once; the sums are integers (fixed point),
-    // so they do not depend on how an atom's pairs were split over batches.
+    // slot's pairs occupy consecutive lanes.  Every lane finds the mask of
+    // its segment and the segment is summed with warp reductions on 32-bit
+    // halves of the fixed-point values (|v| < 2^47, so the high parts of 32
+    // lanes cannot overflow); integer sums do not depend on how an atom's
+    // pairs were split over batches.
     const int prev_slot = __shfl_up_sync(0xffffffffu, my_slot, 1);
     const unsigned heads = __ballot_sync(0xffffffffu, lane < m && (lane == 0 || my_slot != prev_slot));
-    const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // -1 when no head at or below
-    const bool next_is_head = lane < 31 && ((heads >> (lane + 1)) & 1u);
-    const unsigned tails = __ballot_sync(0xffffffffu, lane < m && (lane == m - 1 || next_is_head));
-    const bool is_tail = (tails >> lane) & 1u;
+    const unsigned valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
+    unsigned seg;
+    if (lane < m) {
+        const unsigned below = heads & (0xffffffffu >> (31 - lane));          // heads at or below this lane
+        const unsigned start = 1u << (31 - __clz(below));
+        const unsigned above = heads & ~(0xffffffffu >> (31 - lane));         // heads above this lane
+        const unsigned stop = above ? (above & (0u - above)) : 0u;            // lowest of them, or none
+        seg = (stop ? (stop - start) : (valid & ~(start - 1u)));
+    } else {
+        seg = ~valid;   // idle lanes form one group of their own
+    }
+    const bool leader = (seg & (0u - seg)) == (1u << lane);                    // lowest lane of the segment
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        long long x = f3[c];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane - o >= head) x += y;
-        }
-        if (is_tail) sm.F[w][my_slot][c] += x;
+        const long long x = f3[c];
+        const unsigned lo = __reduce_add_sync(seg, (unsigned)(x & 0x3FFFFF));
+        const int hi = __reduce_add_sync(seg, (int)(x >> 22));
+        if (leader && lane < m) sm.F[w][my_slot][c] += (long long)hi * 4194304ll + (long long)lo;
     }
     if (want_vatom) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            long long x = lane < m ? to_fix(dv[c], status) : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane - o >= head) x += y;
-            }
-            if (is_tail) sm.V[w][my_slot][c] += x;
+            const long long x = lane < m ? to_fix(dv[c], status) : 0;
+            const unsigned lo = __reduce_add_sync(seg, (unsigned)(x & 0x3FFFFF));
+            const int hi = __reduce_add_sync(seg, (int)(x >> 22));
+            if (leader && lane < m) sm.V[w][my_slot][c] += (long long)hi * 4194304ll + (long long)lo;
         }
     }
     __syncwarp();
@@ -218,39 +235,38 @@ __device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, in
     __syncwarp();
 }
 
-// w_{a,lm} = sum_b G~_{ab,l} A_{b,lm} for the channels a0 .. a0+na-1 (na <= NA)
-// of a class with Cg channels, harmonic lm of this lane.  G~ is read with
-// triangular indices kept incrementally per channel.
-template <int NA, int N>
-__device__ __forceinline__ void w_channels(const float *sG, const float *sA, float *ws, int Cg, int choff, int a0,
-                                           int na, int lm)
+// w_{a,lm} = sum_b G~_{ab,l} A_{b,lm} over the CG channels of a class.  Lane
+// (lm, half) owns harmonic lm of half of the channels a; G~ is dense in
+// shared memory as [l][b][a] (row b contiguous in a), so each b costs one
+// A value and H/4 float4 loads of G~ for H FMAs per lane.
+template <int CG, int N>
+__device__ __forceinline__ void w_dense(const float *sGd, const float *sA, float *ws, int choff, int half, int lm)
 {
+    constexpr int H = gd_half(CG);
+    constexpr int RS = gd_row(CG);
+    constexpr int LS = gd_plane(CG);
     const int l = l_of(lm);
-    float acc[NA];
-    int idx[NA];   // tri(min(a, b), max(a, b)) for a = a0 + k at the current b
+    const int a0 = half * H;
+    const float *gp = sGd + l * LS + a0;
+    float acc[H];
 #pragma unroll
-    for (int k = 0; k < NA; ++k) {
-        acc[k] = 0.f;
-        idx[k] = a0 + k;   // tri(0, a) = a
-    }
-    for (int b = 0; b < Cg; ++b) {
+    for (int k = 0; k < H; ++k) acc[k] = 0.f;
+#pragma unroll
+    for (int b = 0; b < CG; ++b) {
         const float av = sA[(choff + b) * kAStride + lm];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            if (k < na) {
-                const int a_ = a0 + k;
-                const float gv = sG[4 * idx[k] + l];
-                acc[k] += (a_ == b ? 2.f * gv : gv) * av;
-                // step to b + 1: above the diagonal the row of b grows by (Cg - b - 1),
-                // from the diagonal on the column index just steps
-                idx[k] += (b < a_) ? (Cg - b - 1) : 1;
-            }
+        for (int k = 0; k < H; k += 4) {
+            const float4 gv = *reinterpret_cast<const float4 *>(gp + b * RS + k);
+            acc[k] += gv.x * av;
+            acc[k + 1] += gv.y * av;
+            acc[k + 2] += gv.z * av;
+            acc[k + 3] += gv.w * av;
         }
     }
 #pragma unroll
-    for (int k = 0; k < NA; ++k) {
-        if (k < na) {
-            const int ch = choff + a0 + k;            // channel = species * N + n
+    for (int k = 0; k < H; ++k) {
+        if (a0 + k < CG) {                         // the last half may be padded
+            const int ch = choff + a0 + k;        // channel = species * N + n
             ws[(ch / N) * 128 + lm * 8 + (ch % N)] = acc[k];
         }
     }
@@ -259,30 +275,28 @@ __device__ __forceinline__ void w_channels(const float *sG, const float *sA, flo
 // Per-atom values loaded one iteration ahead, so their latency overlaps the
 // previous atom's work.
 struct AtomPre {
-    int g, cnt, row;
+    int g, row, np;
     float nrm;
-    float4 pi;
-    int e0, e1;     // the first 64 neighbour-list entries (lane, 32 + lane)
+    float4 r0;      // pair record `lane` of the atom
 };
 
 __device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int lane)
 {
     AtomPre p;
     p.g = -2;
-    p.cnt = 0;
     p.row = 0;
+    p.np = 0;
     p.nrm = 0.f;
-    p.pi = make_float4(0.f, 0.f, 0.f, 0.f);
-    p.e0 = p.e1 = 0;
+    p.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < a.n) {
-        p.g = a.group[i];
-        p.cnt = a.count[i];
-        p.row = a.row[i];
-        p.nrm = a.norm[i];
-        p.pi = a.pos[i];
-        const int32_t *rp = a.entries + (size_t)i * a.max_nbr;
-        p.e0 = rp[lane];
-        p.e1 = a.max_nbr > 32 ? rp[32 + lane] : 0;
+        // read-only loads (ld.global.nc): free to move across the force atomics
+        p.g = __ldg(a.group + i);
+        p.row = __ldg(a.row + i);
+        p.nrm = __ldg(a.norm + i);
+        if (p.g >= 0 && p.nrm > 0.f) {
+            p.np = __ldg(a.pair_cnt + i);
+            if (lane < p.np) p.r0 = __ldg(a.pair_rec + (size_t)i * a.max_nbr + lane);
+        }
     }
     return p;
 }
@@ -291,11 +305,9 @@ template <int N>
 __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 {
     constexpr int C = 2 * N;
-    constexpr int KF = C * (C + 1) / 2 * 4;
-    constexpr int NK4 = (KF / 4 + 31) / 32;        // float4 groups per lane of a descriptor row
     __shared__ __align__(16) ForceSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float rc = a.rcut, rc2 = rc * rc;
+    const float rc = a.rcut;
     float vir[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
@@ -324,36 +336,10 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             cur = nxt;
             continue;
         }
-        // start the neighbour gathers of the first 64 entries now
-        const int cnt = cur.cnt;
-        float4 pj0 = make_float4(0.f, 0.f, 0.f, 0.f), pj1 = pj0;
-        int sj0 = 0, sj1 = 0;
-        if (lane < cnt) {
-            const int j = (int)((unsigned)cur.e0 >> 7);
-            pj0 = a.pos[j];
-            sj0 = a.species[j];
-        }
-        if (32 + lane < cnt) {
-            const int j = (int)((unsigned)cur.e1 >> 7);
-            pj1 = a.pos[j];
-            sj1 = a.species[j];
-        }
-
         const int cls = group_cls(g), reg = group_region(g);
         const int K = a.K[reg];
-        // E, V and sigma were written by the quadratic-form epilogue.
-        // g = dE/dB of this atom, in the compact order of its class
-        const float4 *g4 = reinterpret_cast<const float4 *>(a.G[reg] + (size_t)cur.row * K);
-        float4 gv[NK4];
-#pragma unroll
-        for (int k = 0; k < NK4; ++k) {
-            const int o = lane + 32 * k;
-            gv[k] = 4 * o < K ? g4[o] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a.weight) {
-                const float u = a.weight[i];
-                gv[k].x *= u; gv[k].y *= u; gv[k].z *= u; gv[k].w *= u;
-            }
-        }
+        const int Cg = cls == 0 ? C : N;
+        const int choff = cls == 0 ? 0 : (cls - 1) * N;
 
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
         const int slot = seq & (kSlots - 1);
@@ -361,78 +347,69 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         flush_slot<N>(sm, w, lane, slot, a.Facc, a.status, a.vir_atom);
         if (lane == 0) sm.atom[w][slot] = i;
 
-        float *sG = sm.G[w];
-#pragma unroll
-        for (int k = 0; k < NK4; ++k) {
-            const int o = lane + 32 * k;
-            if (4 * o < K) *reinterpret_cast<float4 *>(sG + 4 * o) = gv[k];
-        }
-        // A of the blocks in use (zero elsewhere)
-        float *sA = sm.A[w];
-        const float4 *Ag = reinterpret_cast<const float4 *>(a.A + (size_t)i * (C * 16));
-        for (int k = lane; k < C * 4; k += 32) {
-            const int ch = k >> 2;
-            const bool used = cls == 0 || (ch / N) == (cls - 1);
-            *reinterpret_cast<float4 *>(sA + ch * kAStride + 4 * (k & 3)) = used ? Ag[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        __syncwarp();
-        // w = G~ A over the class's channels -> slot layout [species][lm][n].
-        // Lane (lm = lane & 15, half = lane >> 4) owns harmonic lm of half of
-        // the class's channels; each A[b][lm] is loaded once and used for all
-        // of them, and G~[a][b][l] is walked with incremental triangular indices.
+        // g = dE/dB of this atom (compact order of its class, written by the
+        // quadratic-form epilogue; scaled by u_i in the backward pass) ->
+        // dense symmetric G~[l][b][a] with the diagonal doubled
         {
-            const int Cg = cls == 0 ? C : N;
-            const int choff = cls == 0 ? 0 : (cls - 1) * N;
-            float *ws = sm.W[w] + slot * kWSlot;
+            const float4 *g4 = reinterpret_cast<const float4 *>(a.G[reg] + (size_t)cur.row * K);
+            const int32_t *tab = a.tab[reg];
+            const float u = a.weight ? __ldg(a.weight + i) : 1.f;
+            const int RS = cls == 0 ? gd_row(C) : gd_row(N);
+            const int LS = cls == 0 ? gd_plane(C) : gd_plane(N);
+            float *sGd = sm.Gd[w];
+            for (int t = lane; 4 * t < K; t += 32) {
+                const int e = __ldg(tab + 4 * t);
+                const int ca = e & 255, cb = (e >> 8) & 255;
+                float4 v = __ldg(g4 + t);
+                const float sc = ca == cb ? 2.f * u : u;
+                v.x *= sc;
+                v.y *= sc;
+                v.z *= sc;
+                v.w *= sc;
+                const int o1 = cb * RS + ca, o2 = ca * RS + cb;
+                sGd[o1] = v.x;
+                sGd[o2] = v.x;
+                sGd[LS + o1] = v.y;
+                sGd[LS + o2] = v.y;
+                sGd[2 * LS + o1] = v.z;
+                sGd[2 * LS + o2] = v.z;
+                sGd[3 * LS + o1] = v.w;
+                sGd[3 * LS + o2] = v.w;
+            }
+        }
+        // A of the class's channels
+        float *sA = sm.A[w];
+        {
+            const float4 *Ag = reinterpret_cast<const float4 *>(a.A + (size_t)i * (C * 16));
+            for (int k = lane; k < Cg * 4; k += 32) {
+                const int ch = choff + (k >> 2);
+                *reinterpret_cast<float4 *>(sA + ch * kAStride + 4 * (k & 3)) = __ldg(Ag + ch * 4 + (k & 3));
+            }
+        }
+        float *ws = sm.W[w] + slot * kWSlot;
+        for (int k = lane; k < 256; k += 32) ws[k] = 0.f;   // both species blocks of the slot
+        __syncwarp();
+        {
             const int lm = lane & 15, half = lane >> 4;
-            const int per = (Cg + 1) / 2;
-            const int a0 = half * per;
-            const int na = min(per, Cg - a0);
-            // zero both species blocks of the slot, then place this class's w
-            for (int k = lane; k < 256; k += 32) ws[k] = 0.f;
-            __syncwarp();
             if (cls == 0)
-                w_channels<N, N>(sG, sA, ws, Cg, choff, a0, na, lm);
+                w_dense<C, N>(sm.Gd[w], sA, ws, 0, half, lm);
             else
-                w_channels<(N + 1) / 2, N>(sG, sA, ws, Cg, choff, a0, na, lm);
+                w_dense<N, N>(sm.Gd[w], sA, ws, choff, half, lm);
         }
         __syncwarp();
 
-        // queue the pairs inside r_cut
-        const float4 pi = cur.pi;
-        const double *cl = a.cells.of(i);
-        const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
-        for (int base = 0; base < cnt; base += 32) {
-            const int q = base + lane;
-            bool ok = false;
-            float3 rv = make_float3(0.f, 0.f, 0.f);
-            int j = 0, sj = 0;
-            if (q < cnt) {
-                int sx, sy, sz;
-                float4 pj;
-                if (base == 0) {
-                    decode_entry(cur.e0, j, sx, sy, sz);
-                    pj = pj0;
-                    sj = sj0;
-                } else if (base == 32) {
-                    decode_entry(cur.e1, j, sx, sy, sz);
-                    pj = pj1;
-                    sj = sj1;
-                } else {
-                    decode_entry(rowp[q], j, sx, sy, sz);
-                    pj = a.pos[j];
-                    sj = a.species[j];
-                }
-                rv = pair_vector(pi, pj, sx, sy, sz, cl);
-                ok = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z < rc2;
+        // queue the atom's pairs inside r_cut (recorded by the descriptor kernel)
+        const int np = cur.np;
+        const float4 *pr = a.pair_rec + (size_t)i * a.max_nbr;
+        for (int base = 0; base < np; base += 32) {
+            const int take = min(32, np - base);
+            if (lane < take) {
+                float4 r = base == 0 ? cur.r0 : __ldg(pr + base + lane);
+                r.w = __int_as_float(__float_as_int(r.w) | (slot << 26));
+                sm.q[w][nq + lane] = r;
+                sm.qseq[w][nq + lane] = seq;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                const int at = nq + __popc(m & ((1u << lane) - 1u));
-                sm.q[w][at] = make_float4(rv.x, rv.y, rv.z, __int_as_float(j | ((sj & 1) << 25) | (slot << 26)));
-                sm.qseq[w][at] = seq;
-            }
-            nq += __popc(m);
+            nq += take;
             __syncwarp();
             drain<N>(sm, w, lane, nq, false, rc, a.Facc, a.status, vir, want_vatom);
         }
@@ -685,6 +662,10 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.vir_part = ctx->partials;
     a.vir_atom = vir_atom;
     a.weight = weight;
+    a.pair_rec = nl->pair_rec;
+    a.pair_cnt = nl->pair_cnt;
+    a.tab[0] = ctx->tab_full;
+    a.tab[1] = ctx->tab_single;
     a.status = ctx->status;
     const long long work = (n + kWarpsForce - 1) / kWarpsForce;
     int grid;

@@ -80,6 +80,9 @@ struct flr_nbrlist {
     int32_t *group;        // [n_cap]
     int32_t *row;          // [n_cap] row inside the group's region
     int32_t *atom_of_row;  // [2][n_cap]
+    float4 *pair_rec;      // [n_cap][max_nbr] pairs inside r_cut of the last descriptor pass:
+                           // (r_ij, j | s_j << 25), written by k_desc, read by k_force
+    int32_t *pair_cnt;     // [n_cap] pairs inside r_cut
     float4 *pos_ref;       // positions at the last build
     int32_t *img;          // [n_cap] packed image offset of the wrapped position
     int32_t *atom_bin;     // [n_cap]
@@ -256,7 +259,7 @@ struct Cells {
     const int32_t *struct_of;  // [n] or nullptr (one structure)
     __device__ __forceinline__ const double *of(int i) const
     {
-        return cells + 9 * (struct_of ? struct_of[i] : 0);
+        return cells + 9 * (struct_of ? __ldg(struct_of + i) : 0);
     }
 };
 
@@ -267,9 +270,9 @@ __device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj
                                               int sz, const double *c)
 {
     if ((sx | sy | sz) == 0) return make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z);
-    double tx = sx * c[0] + sy * c[3] + sz * c[6];
-    double ty = sx * c[1] + sy * c[4] + sz * c[7];
-    double tz = sx * c[2] + sy * c[5] + sz * c[8];
+    double tx = sx * __ldg(c + 0) + sy * __ldg(c + 3) + sz * __ldg(c + 6);
+    double ty = sx * __ldg(c + 1) + sy * __ldg(c + 4) + sz * __ldg(c + 7);
+    double tz = sx * __ldg(c + 2) + sy * __ldg(c + 5) + sz * __ldg(c + 8);
     return make_float3((float)(((double)pj.x - (double)pi.x) + tx),
                        (float)(((double)pj.y - (double)pi.y) + ty),
                        (float)(((double)pj.z - (double)pi.z) + tz));

@@ -9,8 +9,9 @@
 //     product keeps about 16 significant bits (kind::f16, FP32 accumulate).
 // Operand tiles arrive by TMA (128-byte swizzle) into a 4-stage shared
 // memory ring guarded by mbarriers; one thread issues the MMAs, which
-// accumulate in tensor memory (288 of 512 columns).  Four epilogue warps
-// read the accumulator back with tcgen05.ld, one atom (row) per thread:
+// accumulate in tensor memory (288 of 512 columns).  Eight epilogue warps
+// (two per TMEM lane quarter, each taking alternate 16-column groups) read
+// the accumulator back with tcgen05.ld, one atom (row) per thread:
 //   E = d . (beta d),  V = d . (Sigma d),  sigma = sqrt(V),
 //   g = dE/dB = (2/||B||)(beta d - E d)
 // and store E, V, sigma per atom and g as the row the force kernel needs,
@@ -38,7 +39,8 @@ constexpr int kTileA = BM * 128;   // bytes (128-byte rows)
 constexpr int kTileB = NC * 128;
 constexpr int kStageBytes = kTileA + kTileB;
 constexpr int kTmemCols = 512;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;        // two per TMEM lane quarter, alternating 16-column groups
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr unsigned long long kDeadlineNs = 2000000000ull;
 
 struct TcArgs {
@@ -191,14 +193,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
     uint8_t *sA = base;
     uint8_t *sB = base + kStages * kTileA;
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + kStages * kStageBytes);
-    // bars: full[kStages], empty[kStages], tfull, tempty, drain
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 3);
+    // bars: full[kStages], empty[kStages], tfull, tempty, drain, evx
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    // partial (E, V) of each row from the two column halves, double-buffered by tile
+    float2 *evx_buf = reinterpret_cast<float2 *>(base + kStages * kStageBytes + 128);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
     const uint32_t tfull = smem_u32(bars + 2 * kStages), tempty = smem_u32(bars + 2 * kStages + 1);
     const uint32_t drain = smem_u32(bars + 2 * kStages + 2);
+    const uint32_t evx = smem_u32(bars + 2 * kStages + 3);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -211,8 +216,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(tfull, 1);
-        mbar_init(tempty, 4);
+        mbar_init(tempty, kEpiWarps);
         mbar_init(drain, 1);
+        mbar_init(evx, kEpiWarps);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -320,14 +326,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
         }
     } else {
         // ---------------- epilogue: TMEM -> E, V, sigma, g ----------------
+        // Warp (quarter qw, half sub) reads TMEM lanes 32 qw .. 32 qw + 31 (one
+        // row per thread) and the 16-column groups whose index has parity sub.
+        // The two halves of a row exchange their partial E and V through shared
+        // memory (double-buffered by tile, guarded by a bounded mbarrier wait).
         const int qw = warp & 3;                // TMEM lane quarter of this warp
+        const int sub = (warp - 2) >> 2;        // which alternate 16-column groups
         const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
+        const int rloc = qw * 32 + lane;        // row within the tile
         int it = 0;
+        int tl = 0;                             // tiles done by this CTA
         bool alive = true;
-        for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
+        for (int t = blockIdx.x; t < total && alive; t += gridDim.x, ++tl) {
             const TileInfo ti = decode_tile(T, a.nch, t);
             const int K = a.K[ti.reg];
-            const int row = ti.row0 + qw * 32 + lane;
+            const int row = ti.row0 + rloc;
             const bool valid = row < ti.rend;
             const int atom = valid ? a.atom_of_row[(size_t)ti.reg * a.n_cap + row] : 0;
             const float nrm = valid ? a.norm[atom] : 0.f;
@@ -353,13 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     // one chunk holding [beta d | Sigma d]: read both halves together,
                     // one load of d serves E and V; beta d is parked in the g row
 #pragma unroll 1
-                    for (int c = 0; c < K; c += 16) {
-                        float vb[16], vs[16];
+                    for (int c = 16 * sub; c < K; c += 32) {
+                        float dv[16], vb[16], vs[16];
+                        if (valid) load16(d + c, dv);
                         tmem_ld16(tbase + (uint32_t)c, vb);
                         tmem_ld16(tbase + (uint32_t)(K + c), vs);
                         if (valid) {
-                            float dv[16];
-                            load16(d + c, dv);
 #pragma unroll
                             for (int k = 0; k < 16; ++k) {
                                 E += dv[k] * vb[k];
@@ -373,22 +385,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 } else {
                     const int c0 = ch * NC;
 #pragma unroll 1
-                    for (int c = 0; c < NC; c += 16) {
-                        float v[16];
-                        tmem_ld16(tbase + (uint32_t)c, v);
+                    for (int c = 16 * sub; c < NC; c += 32) {
                         const int cg = c0 + c;
+                        float v[16], dv[16];
+                        const bool beta_cols = cg + 16 <= K, sigma_cols = cg >= K && cg + 16 <= 2 * K;
+                        if (valid && beta_cols) load16(d + cg, dv);
+                        else if (valid && sigma_cols) load16(d + cg - K, dv);
+                        tmem_ld16(tbase + (uint32_t)c, v);
                         if (valid && cg < 2 * K) {
-                            if (cg + 16 <= K) {                       // beta d columns
-                                float dv[16];
-                                load16(d + cg, dv);
+                            if (beta_cols) {
 #pragma unroll
                                 for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
 #pragma unroll
                                 for (int k = 0; k < 16; k += 4)
                                     *reinterpret_cast<float4 *>(grow + cg + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-                            } else if (cg >= K && cg + 16 <= 2 * K) { // Sigma d columns
-                                float dv[16];
-                                load16(d + cg - K, dv);
+                            } else if (sigma_cols) {
 #pragma unroll
                                 for (int k = 0; k < 16; ++k) V += dv[k] * v[k];
                             } else {                                  // a group straddling K or 2K
@@ -406,26 +417,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                         }
                     }
                 }
-                // the accumulator is free again: the next MMAs overlap the fix-up below
+                // the accumulator is free again: the next MMAs overlap the rest below
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty);
             }
             if (!alive) break;
+            // combine the two halves' partial sums (fixed order: half 0 + half 1)
+            float2 *xb = evx_buf + (tl & 1) * (2 * BM);
+            xb[sub * BM + rloc] = make_float2(E, V);
+            __syncwarp();
+            int okx = 1;
+            if (lane == 0) {
+                mbar_arrive(evx);
+                okx = mbar_wait(evx, (uint32_t)(tl & 1), abort_flag) ? 1 : 0;
+            }
+            okx = __shfl_sync(0xffffffffu, okx, 0);
+            __syncwarp();
+            if (!okx) {
+                if (lane == 0) {
+                    atomicOr(a.status, kErrTimeout);
+                    *abort_flag = 1;
+                }
+                alive = false;
+                break;
+            }
+            const float2 p0 = xb[rloc], p1 = xb[BM + rloc];
+            E = p0.x + p1.x;
+            V = p0.y + p1.y;
             if (valid) {
-                // g = (2/||B||)(beta d - E d) from the parked beta d columns
+                // g = (2/||B||)(beta d - E d) over the 16-column groups this half parked
                 float4 *g4 = reinterpret_cast<float4 *>(grow);
                 const float4 *d4 = reinterpret_cast<const float4 *>(d);
-#pragma unroll 4
-                for (int k = 0; k < K / 4; ++k) {
-                    const float4 p = g4[k];
-                    const float4 q = __ldg(d4 + k);
-                    g4[k] = make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
-                                        s2 * (p.w - E * q.w));
+                const int nk = K / 4;
+#pragma unroll 1
+                for (int k0 = 4 * sub; k0 < nk; k0 += 8) {
+                    float4 p[4], q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (k0 + u < nk) {
+                            p[u] = g4[k0 + u];
+                            q[u] = __ldg(d4 + k0 + u);
+                        }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (k0 + u < nk)
+                            g4[k0 + u] = make_float4(s2 * (p[u].x - E * q[u].x), s2 * (p[u].y - E * q[u].y),
+                                                     s2 * (p[u].z - E * q[u].z), s2 * (p[u].w - E * q[u].w));
                 }
-                a.energy[atom] = E;
-                if (a.variance) a.variance[atom] = V;
-                if (a.sigma) a.sigma[atom] = sqrtf(fmaxf(V, 0.f));
+                if (sub == 0) {
+                    a.energy[atom] = E;
+                    if (a.variance) a.variance[atom] = V;
+                    if (a.sigma) a.sigma[atom] = sqrtf(fmaxf(V, 0.f));
+                }
             }
         }
     }
@@ -536,7 +580,8 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaS
     a.sigma = out->sigma;
     a.gtab = nl->gtab;
     a.status = ctx->status;
-    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 256;
+    // ring + barriers (128 B) + the E / V exchange (2 tiles x 2 halves x BM float2)
+    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 128 + 2 * 2 * BM * sizeof(float2);
     cudaError_t e;
     if (bf16) {
         e = cudaFuncSetAttribute(k_qform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
