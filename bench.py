@@ -360,20 +360,32 @@ def run_ours(args):
     _, _, groups = nl.view(n)
     groups = groups.cpu().numpy()
     rng = np.random.default_rng(2)
+    # 4,096 atoms drawn with seed 2, at least a quarter of them from the mixed (two-species) class
     mixed = np.nonzero(groups % 3 == 0)[0]
     rest = np.nonzero(groups % 3 != 0)[0]
-    sample = np.concatenate([rng.choice(mixed, min(16, len(mixed)), replace=False),
-                             rng.choice(rest, 48, replace=False)])
+    n_mixed = min(args.err_atoms // 4, len(mixed))
+    sample = np.sort(np.concatenate([rng.choice(mixed, n_mixed, replace=False),
+                                     rng.choice(rest, args.err_atoms - n_mixed, replace=False)]))
     pos_now = sysg.pos.detach().cpu().numpy()
     o = O.forces_subset(O.Hyper(), pos_now[:, :3].astype(np.float64), struct.species, struct.cell,
                         struct.pbc, beta, sigma, sample, skin=0.5)
-    ferr = {}
+    ferr, errs = {}, {}
     for prec in ("bf16x3", "tf32", "fp32"):
         ff.set_precision(prec)
         r = F.energy_forces_uncertainty(ff, sysg, nl, F.make_outputs(n))
         ff.sync()
-        ferr[prec] = float(np.abs(r["forces"].cpu().numpy()[sample] - o["F"]).max())
+        r = {k: v.cpu().numpy() for k, v in r.items()}
+        ferr[prec] = float(np.abs(r["forces"][sample] - o["F"]).max())
+        okv = o["V"] > 0
+        errs[prec] = {
+            "force_max_ev_per_A": ferr[prec],
+            "energy_max_rel": float((np.abs(r["energy"][sample] - o["E"]) / np.maximum(np.abs(o["E"]), 1.0)).max()),
+            "variance_max_rel": float((np.abs(r["variance"][sample][okv] - o["V"][okv]) / o["V"][okv]).max()),
+            "sigma_max_rel": float((np.abs(r["sigma"][sample][okv] - np.sqrt(o["V"][okv])) / np.sqrt(o["V"][okv])).max()),
+        }
     ff.set_precision("bf16x3")
+    err_sample = f"{len(sample)} atoms (seed 2; {n_mixed} mixed-class), FP64 oracle at the same positions"
+
 
     # roofline of the dominant kernel (mixed run)
     peaks, peak_kind = _peaks()
@@ -445,6 +457,7 @@ def run_ours(args):
                 "config": _config(n, "3xBF16 tcgen05 quadratic forms, FP32 elsewhere, FP64 totals"),
                 "plain_fp32": {"value": round(value_fp32, 3), "ms_per_step": round(ms_fp32 / args.steps, 4)},
                 "force_err_ev_per_A": ferr,
+                "errors_vs_oracle": {"sample": err_sample, **errs},
                 "rebuilds_in_timed_steps": rebuild_count,
                 "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
                 "kernels_ms_per_step_fp32": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_fp32.items()}
@@ -502,6 +515,8 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="time only the MD steps at --precision (for ncu launch lists)")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--err-atoms", type=int, default=4096,
+                    help="atoms sampled for the error report against the FP64 oracle")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
                     help="open-loop serving run per arrival rate (0: skip)")
     ap.add_argument("--small", action="store_true",

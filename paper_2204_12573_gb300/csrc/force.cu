@@ -69,6 +69,7 @@ template <int N>
 struct ForceSmem {
     float Gd[kWarpsForce][4 * gd_plane(2 * N)];          // G~[l][b][a] of the widest class
     float A[kWarpsForce][2 * N * kAStride];
+    float gr[kWarpsForce][(2 * N) * (2 * N + 1) / 2 * 4];   // raw g row of the next atom (cp.async)
     float W[kWarpsForce][kSlots * kWSlot];
     float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
     long long F[kWarpsForce][kSlots][3];         // F_i of each slot's atom, fixed point
@@ -301,6 +302,34 @@ __device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int lane)
     return p;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// Start copying atom i's g row (raw, compact order) and the A rows of its
+// class's channels into the warp's shared buffers (cp.async; lane t % 32
+// copies chunk t).  The buffers must no longer be in use.
+template <int N>
+__device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p, int i, float *gr, float *sA, int lane)
+{
+    constexpr int C = 2 * N;
+    if (i >= a.n || p.g < 0 || !(p.nrm > 0.f)) return;
+    const int cls = group_cls(p.g), reg = group_region(p.g);
+    const int K = a.K[reg];
+    const int Cg = cls == 0 ? C : N;
+    const int choff = cls == 0 ? 0 : (cls - 1) * N;
+    const float *g = a.G[reg] + (size_t)p.row * K;
+    for (int t = lane; 4 * t < K; t += 32) cp_async16(gr + 4 * t, g + 4 * t);
+    const float *Ag = a.A + (size_t)i * (C * 16);
+    for (int k = lane; k < Cg * 4; k += 32) {
+        const int ch = choff + (k >> 2);
+        cp_async16(sA + ch * kAStride + 4 * (k & 3), Ag + ch * 16 + 4 * (k & 3));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <int N>
 __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 {
@@ -321,6 +350,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     const int stride = gridDim.x * kWarpsForce;
     int i = blockIdx.x * kWarpsForce + w;
     AtomPre cur = preload(a, i, lane);
+    rows_async<N>(a, cur, i, sm.gr[w], sm.A[w], lane);
 
     for (; i < a.n; i += stride) {
         const AtomPre nxt = preload(a, i + stride, lane);
@@ -334,11 +364,11 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             }
             if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
             cur = nxt;
+            rows_async<N>(a, cur, i + stride, sm.gr[w], sm.A[w], lane);
             continue;
         }
         const int cls = group_cls(g), reg = group_region(g);
         const int K = a.K[reg];
-        const int Cg = cls == 0 ? C : N;
         const int choff = cls == 0 ? 0 : (cls - 1) * N;
 
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
@@ -347,11 +377,15 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         flush_slot<N>(sm, w, lane, slot, a.Facc, a.status, a.vir_atom);
         if (lane == 0) sm.atom[w][slot] = i;
 
+        // this atom's g row and A rows were copied into shared memory while the
+        // previous atom was processed
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncwarp();
         // g = dE/dB of this atom (compact order of its class, written by the
         // quadratic-form epilogue; scaled by u_i in the backward pass) ->
         // dense symmetric G~[l][b][a] with the diagonal doubled
         {
-            const float4 *g4 = reinterpret_cast<const float4 *>(a.G[reg] + (size_t)cur.row * K);
+            const float4 *g4 = reinterpret_cast<const float4 *>(sm.gr[w]);
             const int32_t *tab = a.tab[reg];
             const float u = a.weight ? __ldg(a.weight + i) : 1.f;
             const int RS = cls == 0 ? gd_row(C) : gd_row(N);
@@ -360,7 +394,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             for (int t = lane; 4 * t < K; t += 32) {
                 const int e = __ldg(tab + 4 * t);
                 const int ca = e & 255, cb = (e >> 8) & 255;
-                float4 v = __ldg(g4 + t);
+                float4 v = g4[t];
                 const float sc = ca == cb ? 2.f * u : u;
                 v.x *= sc;
                 v.y *= sc;
@@ -377,15 +411,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
                 sGd[3 * LS + o2] = v.w;
             }
         }
-        // A of the class's channels
-        float *sA = sm.A[w];
-        {
-            const float4 *Ag = reinterpret_cast<const float4 *>(a.A + (size_t)i * (C * 16));
-            for (int k = lane; k < Cg * 4; k += 32) {
-                const int ch = choff + (k >> 2);
-                *reinterpret_cast<float4 *>(sA + ch * kAStride + 4 * (k & 3)) = __ldg(Ag + ch * 4 + (k & 3));
-            }
-        }
+        float *sA = sm.A[w];   // A rows of the class's channels (already copied)
         float *ws = sm.W[w] + slot * kWSlot;
         for (int k = lane; k < 256; k += 32) ws[k] = 0.f;   // both species blocks of the slot
         __syncwarp();
@@ -397,6 +423,8 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
                 w_dense<N, N>(sm.Gd[w], sA, ws, choff, half, lm);
         }
         __syncwarp();
+        // the g and A buffers are free: start copying the next atom's rows
+        rows_async<N>(a, nxt, i + stride, sm.gr[w], sm.A[w], lane);
 
         // queue the atom's pairs inside r_cut (recorded by the descriptor kernel)
         const int np = cur.np;

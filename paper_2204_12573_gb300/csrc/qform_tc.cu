@@ -26,6 +26,8 @@
 // its tensor memory and returns.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace flr {
@@ -34,7 +36,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int NH = 144;            // N of one MMA
 constexpr int NC = 2 * NH;         // columns per chunk (one accumulator)
-constexpr int kStages = 4;
+constexpr int kStages = 2;          // two stages keep the MMAs fed and leave L1 room for prefetched rows
 constexpr int kTileA = BM * 128;   // bytes (128-byte rows)
 constexpr int kTileB = NC * 128;
 constexpr int kStageBytes = kTileA + kTileB;
@@ -423,6 +425,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 if (lane == 0) mbar_arrive(tempty);
             }
             if (!alive) break;
+            // While the MMAs of the next tile run, pull this thread's descriptor
+            // row of that tile towards the SM (into L1 for one-species rows,
+            // which fit, into L2 for two-species rows), so the accumulator
+            // read-back of the next tile does not wait on memory.
+            {
+                const int tn = t + gridDim.x;
+                if (tn < total) {
+                    const TileInfo tj = decode_tile(T, a.nch, tn);
+                    const int rown = tj.row0 + rloc;
+                    if (rown < tj.rend) {
+                        const char *dn = reinterpret_cast<const char *>(a.D32[tj.reg] + (size_t)rown * a.kp32[tj.reg]);
+                        const int bytes = 4 * a.K[tj.reg];
+                        if (tj.reg == 1) {
+                            for (int o = 128 * sub; o < bytes; o += 256)
+                                asm volatile("prefetch.global.L1 [%0];" ::"l"(dn + o));
+                        } else {
+                            for (int o = 128 * sub; o < bytes; o += 256)
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(dn + o));
+                        }
+                    }
+                }
+            }
             // combine the two halves' partial sums (fixed order: half 0 + half 1)
             float2 *xb = evx_buf + (tl & 1) * (2 * BM);
             xb[sub * BM + rloc] = make_float2(E, V);
@@ -580,8 +604,10 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaS
     a.sigma = out->sigma;
     a.gtab = nl->gtab;
     a.status = ctx->status;
-    // ring + barriers (128 B) + the E / V exchange (2 tiles x 2 halves x BM float2)
-    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 128 + 2 * 2 * BM * sizeof(float2);
+    // ring + barriers (128 B) + the E / V exchange (2 tiles x 2 halves x BM float2),
+    // and at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM
+    const size_t smem = std::max<size_t>(1024 + (size_t)kStages * kStageBytes + 128 + 2 * 2 * BM * sizeof(float2),
+                                         116 * 1024);
     cudaError_t e;
     if (bf16) {
         e = cudaFuncSetAttribute(k_qform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
