@@ -40,8 +40,6 @@ struct DescArgs {
 
 template <int N>
 struct DescSmem {
-    float4 pj[kWarpsDesc][64];           // positions of the atom's first 64 list entries (cp.async gather)
-    int sj[kWarpsDesc][64];              // their species
     float4 rec[kWarpsDesc][64];          // compacted pairs inside r_cut: r_ij, species of j
     float Rf[kWarpsDesc][32][N];         // staged radial values of up to 32 pairs
     float Y[kWarpsDesc][32][16];         // staged harmonics
@@ -92,7 +90,7 @@ struct DescPre {
     int e0, e1;     // the first 64 neighbour-list entries (lane, 32 + lane)
 };
 
-__device__ __forceinline__ DescPre desc_preload(const DescArgs &a, int i, int lane)
+__device__ __forceinline__ DescPre desc_preload(const DescArgs &a, int i, int i_end, int lane)
 {
     DescPre p;
     p.g = -2;
@@ -100,7 +98,7 @@ __device__ __forceinline__ DescPre desc_preload(const DescArgs &a, int i, int la
     p.row = 0;
     p.pi = make_float4(0.f, 0.f, 0.f, 0.f);
     p.e0 = p.e1 = 0;
-    if (i < a.n) {
+    if (i < i_end) {
         // read-only loads (ld.global.nc): they may be reordered around the
         // kernel's global stores, which cannot alias them
         p.g = __ldg(a.group + i);
@@ -113,30 +111,6 @@ __device__ __forceinline__ DescPre desc_preload(const DescArgs &a, int i, int la
     }
     return p;
 }
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-// Start gathering the positions and species of an atom's first 64 list
-// entries into the warp's shared buffer (cp.async, no registers held); lane
-// q % 32 copies entry q and is the lane that later reads it, after its own
-// cp.async.wait_group, so no cross-lane synchronization is needed.
-__device__ __forceinline__ void gather_async(const DescArgs &a, const DescPre &p, float4 *bpos, int *bsp, int lane)
-{
-    if (p.g < 0) return;
-    if (lane < p.cnt) {
-        const int j = (int)((unsigned)p.e0 >> 7);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(bpos + lane)), "l"(a.pos + j) : "memory");
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(bsp + lane)), "l"(a.species + j) : "memory");
-    }
-    if (32 + lane < p.cnt) {
-        const int j = (int)((unsigned)p.e1 >> 7);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(bpos + 32 + lane)), "l"(a.pos + j) : "memory");
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(bsp + 32 + lane)), "l"(a.species + j) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ void gather_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // B2 for one radial-channel pair (a, b): all four l at once from two rows of A.
 __device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
@@ -164,19 +138,21 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
     __shared__ __align__(16) DescSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float rc = a.rcut, rc2 = rc * rc;
-    // persistent warps: a fixed grid walks the atoms; each atom's scalars and
-    // first 64 list entries are loaded one iteration ahead
-    const int stride = gridDim.x * kWarpsDesc;
-    int i = blockIdx.x * kWarpsDesc + w;
-    DescPre cur = desc_preload(a, i, lane);
-    gather_async(a, cur, sm.pj[w], sm.sj[w], lane);
-    for (; i < a.n; i += stride) {
-        const DescPre nxt = desc_preload(a, i + stride, lane);
+    // persistent warps: each CTA walks one contiguous block of atoms with its
+    // warps interleaved, so atoms in flight together are spatial neighbours
+    // and share most of their neighbours' positions in L1; each atom's
+    // scalars and first 64 list entries are loaded one iteration ahead
+    const int span = (int)(((long long)a.n + gridDim.x - 1) / gridDim.x);
+    const int i_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * span);
+    const int stride = kWarpsDesc;
+    int i = blockIdx.x * span + w;
+    DescPre cur = desc_preload(a, i, i_end, lane);
+    for (; i < i_end; i += stride) {
+        const DescPre nxt = desc_preload(a, i + stride, i_end, lane);
         const int g = cur.g;
         if (g < 0) {
             if (lane == 0) a.norm[i] = 0.f;
             cur = nxt;
-            gather_async(a, cur, sm.pj[w], sm.sj[w], lane);
             continue;
         }
         const int cls = group_cls(g);
@@ -190,7 +166,6 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         int nv = 0;   // staged pairs
         int np = 0;   // pairs inside r_cut so far
         float4 *prec = a.pair_rec + (size_t)i * a.max_nbr;
-        gather_wait();
         for (int base = 0; base < cnt; base += 32) {
             const int q = base + lane;
             bool ok = false;
@@ -199,14 +174,8 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
             if (q < cnt) {
                 int sx, sy, sz;
                 decode_entry(base == 0 ? cur.e0 : (base == 32 ? cur.e1 : __ldg(rowp + q)), j, sx, sy, sz);
-                float4 pj;
-                if (q < 64) {
-                    pj = sm.pj[w][q];
-                    sj = sm.sj[w][q];
-                } else {
-                    pj = __ldg(a.pos + j);
-                    sj = __ldg(a.species + j);
-                }
+                const float4 pj = __ldg(a.pos + j);
+                sj = __ldg(a.species + j);
                 r = pair_vector(pi, pj, sx, sy, sz, cl);
                 ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
             }
@@ -227,8 +196,6 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
                 __syncwarp();
             }
         }
-        // this lane has consumed its gathered entries: start the next atom's gathers
-        gather_async(a, nxt, sm.pj[w], sm.sj[w], lane);
         if (nv > 0) desc_batch<N>(sm, w, lane, nv, rc, acc0, acc1);
         if (lane == 0) a.pair_cnt[i] = np;
 

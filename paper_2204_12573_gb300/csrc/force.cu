@@ -281,7 +281,7 @@ struct AtomPre {
     float4 r0;      // pair record `lane` of the atom
 };
 
-__device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int lane)
+__device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int i_end, int lane)
 {
     AtomPre p;
     p.g = -2;
@@ -289,7 +289,7 @@ __device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int lane)
     p.np = 0;
     p.nrm = 0.f;
     p.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < a.n) {
+    if (i < i_end) {
         // read-only loads (ld.global.nc): free to move across the force atomics
         p.g = __ldg(a.group + i);
         p.row = __ldg(a.row + i);
@@ -312,10 +312,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 // class's channels into the warp's shared buffers (cp.async; lane t % 32
 // copies chunk t).  The buffers must no longer be in use.
 template <int N>
-__device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p, int i, float *gr, float *sA, int lane)
+__device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p, int i, int i_end, float *gr, float *sA,
+                                           int lane)
 {
     constexpr int C = 2 * N;
-    if (i >= a.n || p.g < 0 || !(p.nrm > 0.f)) return;
+    if (i >= i_end || p.g < 0 || !(p.nrm > 0.f)) return;
     const int cls = group_cls(p.g), reg = group_region(p.g);
     const int K = a.K[reg];
     const int Cg = cls == 0 ? C : N;
@@ -347,13 +348,16 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     __syncwarp();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
-    const int stride = gridDim.x * kWarpsForce;
-    int i = blockIdx.x * kWarpsForce + w;
-    AtomPre cur = preload(a, i, lane);
-    rows_async<N>(a, cur, i, sm.gr[w], sm.A[w], lane);
+    // each CTA walks one contiguous block of atoms, its warps interleaved
+    const int span = (int)(((long long)a.n + gridDim.x - 1) / gridDim.x);
+    const int i_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * span);
+    const int stride = kWarpsForce;
+    int i = blockIdx.x * span + w;
+    AtomPre cur = preload(a, i, i_end, lane);
+    rows_async<N>(a, cur, i, i_end, sm.gr[w], sm.A[w], lane);
 
-    for (; i < a.n; i += stride) {
-        const AtomPre nxt = preload(a, i + stride, lane);
+    for (; i < i_end; i += stride) {
+        const AtomPre nxt = preload(a, i + stride, i_end, lane);
         const int g = cur.g;
         if (g < 0 || !(cur.nrm > 0.f)) {
             // no environment inside r_cut: no forces from this centre
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             }
             if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
             cur = nxt;
-            rows_async<N>(a, cur, i + stride, sm.gr[w], sm.A[w], lane);
+            rows_async<N>(a, cur, i + stride, i_end, sm.gr[w], sm.A[w], lane);
             continue;
         }
         const int cls = group_cls(g), reg = group_region(g);
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         }
         __syncwarp();
         // the g and A buffers are free: start copying the next atom's rows
-        rows_async<N>(a, nxt, i + stride, sm.gr[w], sm.A[w], lane);
+        rows_async<N>(a, nxt, i + stride, i_end, sm.gr[w], sm.A[w], lane);
 
         // queue the atom's pairs inside r_cut (recorded by the descriptor kernel)
         const int np = cur.np;
