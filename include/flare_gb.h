@@ -172,10 +172,12 @@ int flr_set_model(flr_ctx *ctx, int32_t species, const double *beta, const doubl
 int flr_nbrlist_create(flr_ctx *ctx, int32_t n_atoms, flr_nbrlist **out);
 int flr_nbrlist_destroy(flr_nbrlist *nl);
 
-/* Device views of a built list: entries[n][max_nbr] int32 = (j << 7) |
- * image code, code = (sx+2)*25 + (sy+2)*5 + (sz+2) for the lattice image
+/* Device views of a built list: entries[n][max_nbr] int32 =
+ * (j << 8) | (s_j << 7) | image code, with s_j the species of atom j (0 or 1)
+ * and code = (sx+2)*25 + (sy+2)*5 + (sz+2) for the lattice image
  * S = (sx, sy, sz) of atom j; count[n] int32 neighbours per row;
- * group[n] int32 compaction class (-1: no neighbours). */
+ * group[n] int32 compaction class (-1: no neighbours).  Lists hold fewer
+ * than 2^24 atoms. */
 int flr_nbrlist_view(const flr_nbrlist *nl, int32_t **entries, int32_t **count, int32_t **group,
                      int32_t *max_nbr);
 

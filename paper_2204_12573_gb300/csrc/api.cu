@@ -533,8 +533,8 @@ int flr_set_model(flr_ctx *c, int32_t species, const double *beta, const double 
 
 int flr_nbrlist_create(flr_ctx *c, int32_t n_atoms, flr_nbrlist **out)
 {
-    if (!c || !out || n_atoms < 0 || n_atoms >= (1 << 25)) {
-        set_error("flr_nbrlist_create: invalid argument (n_atoms must be < 2^25)");
+    if (!c || !out || n_atoms < 0 || n_atoms >= (1 << 24)) {
+        set_error("flr_nbrlist_create: invalid argument (n_atoms must be < 2^24)");
         return FLR_EINVAL;
     }
     cudaSetDevice(c->device);

@@ -173,9 +173,10 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
             int sj = 0, j = 0;
             if (q < cnt) {
                 int sx, sy, sz;
-                decode_entry(base == 0 ? cur.e0 : (base == 32 ? cur.e1 : __ldg(rowp + q)), j, sx, sy, sz);
+                const int e = base == 0 ? cur.e0 : (base == 32 ? cur.e1 : __ldg(rowp + q));
+                decode_entry(e, j, sx, sy, sz);
                 const float4 pj = __ldg(a.pos + j);
-                sj = __ldg(a.species + j);
+                sj = entry_species(e);   // the list carries the neighbour's species: no gather
                 r = pair_vector(pi, pj, sx, sy, sz, cl);
                 ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
             }

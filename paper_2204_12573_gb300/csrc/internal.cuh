@@ -236,10 +236,12 @@ constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
 
 // ---- shared device helpers ----
 
-// Decode a neighbour entry: (j << 7) | code, code = (sx+2)*25 + (sy+2)*5 + (sz+2).
+// Decode a neighbour entry: (j << 8) | (s_j << 7) | code,
+// code = (sx+2)*25 + (sy+2)*5 + (sz+2); s_j is the species of j (0 or 1).
+__device__ __forceinline__ int entry_species(int e) { return (e >> 7) & 1; }
 __device__ __forceinline__ void decode_entry(int e, int &j, int &sx, int &sy, int &sz)
 {
-    j = (int)((unsigned)e >> 7);
+    j = (int)((unsigned)e >> 8);
     int code = e & 127;
     sx = code / 25 - 2;
     sy = (code / 5) % 5 - 2;

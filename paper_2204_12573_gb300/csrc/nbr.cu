@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                             const double z = ((double)pj.z - (double)pi.z) + tv[2];
                             ok = x * x + y * y + z * z < a.rc2d;
                         }
-                        entry = (j << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
                         sj = a.species[j];
+                        entry = (j << 8) | ((sj & 1) << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, ok);

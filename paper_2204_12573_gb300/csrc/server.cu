@@ -223,7 +223,7 @@ void admit(flr_server *s, std::vector<Pending> &out)
     while (!s->queue.empty()) {
         const Pending &q = s->queue.front();
         const int64_t a = atoms + q.req.n_atoms, m = structs + 1;
-        if (m > max_s || a > max_a || a >= (1 << 25) || s->batch_bytes(a, m) > (int64_t)s->p.hbm_budget_bytes)
+        if (m > max_s || a > max_a || a >= (1 << 24) || s->batch_bytes(a, m) > (int64_t)s->p.hbm_budget_bytes)
             break;
         out.push_back(std::move(s->queue.front()));
         s->queue.pop_front();
@@ -452,7 +452,7 @@ int flr_server_submit(flr_server *s, const flr_request *req)
     }
     const int64_t max_a = s->p.max_batch_atoms > 0 ? s->p.max_batch_atoms : INT64_MAX;
     if (req->n_atoms > max_a || s->batch_bytes(req->n_atoms, 1) > (int64_t)s->p.hbm_budget_bytes ||
-        req->n_atoms >= (1 << 25)) {
+        req->n_atoms >= (1 << 24)) {
         set_error("flr_server_submit: " + std::to_string(req->n_atoms) + " atoms exceed the server's budget");
         return FLR_EBUDGET;
     }

@@ -25,7 +25,7 @@ def decode_entries(entries, count):
     rows = []
     for i in range(len(c)):
         v = e[i, :c[i]].astype(np.int64)
-        j = v >> 7
+        j = v >> 8
         code = v & 127
         sx = code // 25 - 2
         sy = (code // 5) % 5 - 2

@@ -46,6 +46,12 @@ def test_neighbor_sets_bit_exact(which):
     got = decode_entries(g["entries"], g["count"])
     assert got.shape == ref.shape
     assert np.array_equal(got, ref.astype(np.int64))
+    # every entry carries its neighbour's species in bit 7
+    e = g["entries"].cpu().numpy()
+    c = g["count"].cpu().numpy()
+    for i in range(len(c)):
+        v = e[i, :c[i]].astype(np.int64)
+        assert np.array_equal((v >> 7) & 1, s.species[v >> 8])
 
 
 def test_rows_are_deterministic():
