@@ -261,7 +261,7 @@ int64_t flr_launch_count(const flr_ctx *ctx);
  * flr_build_neighbors with r_cut + skin = r_list.
  *
  * Every other buffer lives in one fixed device array inside the library
- * (about 2.6 MB, held by every GPU that loads the library until the process
+ * (about 3.9 MB, held by every GPU that loads the library until the process
  * exits), so the sizes are bounded: at most 65,536 atoms and 65,536 cell-list
  * bins; larger inputs return FLR_EINVAL with a message naming the limit.
  * The first call on a device looks up the array's device address with that

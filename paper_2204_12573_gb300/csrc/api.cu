@@ -338,7 +338,7 @@ int64_t bytes_per_atom(const flr_ctx *ctx)
     int64_t b = 4 * (int64_t)D.nA + 4;
     for (int r = 0; r < 2; ++r) b += 4 * (int64_t)D.kp32[r] + 2 * 2 * (int64_t)D.kp64[r] + 4 * 3 * (int64_t)D.K[r];
     b += 8 * 3 + 4 * 9 + 4 * 3;
-    b += 4 * (int64_t)ctx->p.max_nbr + 4 * 8 + 16 + 1;
+    b += 4 * (int64_t)ctx->p.max_nbr + 4 * 8 + 16 + 16 + 1;
     b += 16 * (int64_t)ctx->p.max_nbr + 4;   // pair records
     b += 16 + 4 + 4 * 6;
     return b;
@@ -553,6 +553,7 @@ int flr_nbrlist_create(flr_ctx *c, int32_t n_atoms, flr_nbrlist **out)
     if (s == FLR_OK) s = dev_alloc(&nl->img, N, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->atom_bin, N, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->bin_atoms, N, "nbrlist");
+    if (s == FLR_OK) s = dev_alloc(&nl->pos_bin, N, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->blk_group, 8 * ((N + 511) / 512 + 1) + 65536 + 1024, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->gtab, 1, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->flags, 4, "nbrlist");
@@ -584,6 +585,7 @@ int flr_nbrlist_destroy(flr_nbrlist *nl)
     cudaFree(nl->img);
     cudaFree(nl->atom_bin);
     cudaFree(nl->bin_atoms);
+    cudaFree(nl->pos_bin);
     cudaFree(nl->bin_start);
     cudaFree(nl->bin_fill);
     cudaFree(nl->blk_group);

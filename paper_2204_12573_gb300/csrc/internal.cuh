@@ -87,6 +87,7 @@ struct flr_nbrlist {
     int32_t *img;          // [n_cap] packed image offset of the wrapped position
     int32_t *atom_bin;     // [n_cap]
     int32_t *bin_atoms;    // [n_cap]
+    float4 *pos_bin;       // [n_cap] positions in bin order, species bits in .w (list build only)
     int32_t *bin_start;    // [nbins_cap + 1]
     int32_t *bin_fill;     // [nbins_cap]
     int32_t *blk_group;    // [n_blocks][8] per-block group counts

@@ -275,10 +275,27 @@ __global__ void k_sort_bins(const int32_t *bin_start, int32_t *bin_atoms, long l
     }
 }
 
+// Positions in bin order with the packed image offset (bytes 0-2) and the
+// species (byte 3) in .w, so the candidate loop of the row builder reads one
+// 16-byte record per candidate instead of chasing bin_atoms -> pos, img,
+// species.
+__global__ void k_bin_positions(const int32_t *bin_atoms, const float4 *pos, const int32_t *img,
+                                const int32_t *species, int n, float4 *pos_bin, const int32_t *flags)
+{
+    if (flags[0] == 0) return;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int j = bin_atoms[s];
+        float4 p = pos[j];
+        p.w = __int_as_float((img[j] & 0xFFFFFF) | (species[j] << 24));
+        pos_bin[s] = p;
+    }
+}
+
 struct RowArgs {
     const float4 *pos;
     const int32_t *species;
     const int32_t *atom_bin, *img, *bin_start, *bin_atoms;
+    const float4 *pos_bin;     // positions in bin order (species in .w)
     int n, max_nbr, compaction;
     const Plan *plans;
     const int32_t *struct_of;
@@ -301,15 +318,20 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
     if (a.flags[0] == 0) return;
     __shared__ int s_start[8][32], s_excl[8][32], s_shift[8][32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + wl; i < a.n; i += warps) {
+    // atoms are taken in bin order, each CTA a contiguous block of it, so the
+    // warps of a CTA scan overlapping stencils and share candidates in L1
+    const int blk = (int)(((long long)a.n + gridDim.x - 1) / gridDim.x);
+    const int k_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * blk);
+    for (int kq = blockIdx.x * blk + wl; kq < k_end; kq += 8) {
+        const int i = a.bin_atoms[kq];
         const Plan &P = a.plans[structure_of(a.struct_of, i)];
         const int span[3] = {2 * P.R[0] + 1, 2 * P.R[1] + 1, 2 * P.R[2] + 1};
         const int n_stencil = span[0] * span[1] * span[2];
-        const float4 pi = a.pos[i];
+        const float4 pib = a.pos_bin[kq];
+        const float4 pi = pib;
         const int bin = a.atom_bin[i] - (int)P.bin_base;
         const int bi[3] = {bin / (P.nb[1] * P.nb[2]), (bin / P.nb[2]) % P.nb[1], bin % P.nb[2]};
-        const int imi = a.img[i];
+        const int imi = __float_as_int(pib.w) & 0xFFFFFF;
         int32_t *row = a.entries + (size_t)i * a.max_nbr;
         int cnt = 0;
         unsigned smask = 0;
@@ -365,9 +387,11 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                         if (s_excl[wl][mid] <= t) lo = mid;
                         else hi = mid - 1;
                     }
-                    const int j = a.bin_atoms[s_start[wl][lo] + (t - s_excl[wl][lo])];
+                    const int slot = s_start[wl][lo] + (t - s_excl[wl][lo]);
+                    const int j = a.bin_atoms[slot];
+                    const float4 pjb = a.pos_bin[slot];   // independent of j: no load chain
                     const int sh = s_shift[wl][lo];
-                    const int imj = a.img[j];
+                    const int imj = __float_as_int(pjb.w) & 0xFFFFFF;
                     int S[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) S[d] = img_comp(sh, d) + img_comp(imi, d) - img_comp(imj, d);
@@ -375,7 +399,7 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                                           S[2] <= 2;
                     if (!in_range) atomicOr(a.status, kErrShift);
                     if (in_range && !(j == i && S[0] == 0 && S[1] == 0 && S[2] == 0)) {
-                        const float4 pj = a.pos[j];
+                        const float4 pj = pjb;
                         const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], P.cell);
                         const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
                         if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
@@ -391,7 +415,7 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                             const double z = ((double)pj.z - (double)pi.z) + tv[2];
                             ok = x * x + y * y + z * z < a.rc2d;
                         }
-                        sj = a.species[j];
+                        sj = (int)((unsigned)__float_as_int(pjb.w) >> 24);
                         entry = (j << 8) | ((sj & 1) << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
                     }
                 }
@@ -810,6 +834,8 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
                                                                                         nl->bin_atoms, n, nl->flags);
     k_sort_bins<<<(int)std::max<long long>(1, std::min<long long>((nbins + 255) / 256, ctx->num_sms * 8)), 256, 0,
                   st>>>(nl->bin_start, nl->bin_atoms, nbins, nl->flags);
+    k_bin_positions<<<std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8)), 256, 0, st>>>(
+        nl->bin_atoms, wrap_positions ? pos_mut : pos, nl->img, species, n, nl->pos_bin, nl->flags);
 
     RowArgs r;
     r.pos = wrap_positions ? pos_mut : pos;
@@ -818,6 +844,7 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.img = nl->img;
     r.bin_start = nl->bin_start;
     r.bin_atoms = nl->bin_atoms;
+    r.pos_bin = nl->pos_bin;
     r.n = n;
     r.max_nbr = nl->max_nbr;
     r.compaction = ctx->p.compaction;
@@ -851,7 +878,7 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     k_group_rows<<<nblk, kGroupBlock, 0, st>>>(nl->group, n, nl->blk_group, nl->gtab, nl->row,
                                                nl->atom_of_row, nl->n_cap, nl->flags);
     k_rebuild_done<<<1, 1, 0, st>>>(nl->flags);
-    count_launch(ctx, 13);
+    count_launch(ctx, 14);
     return cuda_fail(cudaGetLastError(), "neighbour rebuild");
 }
 
@@ -868,7 +895,7 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
 // caller's inputs and outputs (bin counts and starts, the per-atom bin and
 // image tables, the bin-sorted atom order, scan block sums, the grid plan,
 // the status word) lives in one file-scope device array of fixed size,
-// kNoAllocBytes (about 2.6 MB), that each GPU loading this library keeps
+// kNoAllocBytes (about 3.9 MB), that each GPU loading this library keeps
 // until the process exits.
 // ---------------------------------------------------------------------------
 #include <mutex>
@@ -879,7 +906,8 @@ namespace {
 constexpr int kNoAllocMaxAtoms = 1 << 16;
 constexpr int kNoAllocMaxBins = 1 << 16;
 constexpr size_t kNoAllocBytes =
-    (size_t)kNoAllocMaxAtoms * (5 * sizeof(int32_t) + sizeof(float4)) +   // bin, img, sorted atoms, group, spare; pos_ref
+    (size_t)kNoAllocMaxAtoms * (5 * sizeof(int32_t) + 2 * sizeof(float4)) +   // bin, img, sorted atoms, group, spare;
+                                                                            // pos_ref, positions in bin order
     (size_t)2 * (kNoAllocMaxBins + 2) * sizeof(int32_t) +                  // bin starts, bin fill
     (size_t)(kNoAllocMaxBins / kScanBlock + 2) * sizeof(int32_t) +         // scan block sums
     4096;                                                                   // flags, status, bbox, plan, group table
@@ -953,6 +981,7 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     int32_t *bin_atoms = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * kNoAllocMaxAtoms));
     int32_t *group = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * kNoAllocMaxAtoms));
     float4 *pos_ref = reinterpret_cast<float4 *>(take(sizeof(float4) * kNoAllocMaxAtoms));
+    float4 *pos_bin = reinterpret_cast<float4 *>(take(sizeof(float4) * kNoAllocMaxAtoms));
     int32_t *bin_start = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (kNoAllocMaxBins + 2)));
     int32_t *bin_fill = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (kNoAllocMaxBins + 2)));
     int32_t *bsums = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * (kNoAllocMaxBins / kScanBlock + 2)));
@@ -1024,6 +1053,8 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
                                                                                   flags);
     k_sort_bins<<<(int)std::max<long long>(1, std::min<long long>((nbins + 255) / 256, num_sms * 8)), 256, 0, st>>>(
         bin_start, bin_atoms, nbins, flags);
+    k_bin_positions<<<std::max(1, std::min((n + 255) / 256, num_sms * 8)), 256, 0, st>>>(bin_atoms, pos, img,
+                                                                                        sys->species, n, pos_bin, flags);
     RowArgs r;
     r.pos = pos;
     r.species = sys->species;
@@ -1031,6 +1062,7 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     r.img = img;
     r.bin_start = bin_start;
     r.bin_atoms = bin_atoms;
+    r.pos_bin = pos_bin;
     r.n = n;
     r.max_nbr = max_nbr;
     r.compaction = 1;
