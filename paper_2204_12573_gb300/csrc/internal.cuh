@@ -66,6 +66,8 @@ struct Plan {
     int pbc[3];
     long long nbins;
     long long bin_base; // first global bin of this structure in a batch
+    float bw[3];        // bin width along each direction's plane normal (A)
+    int orth;           // 1: orthogonal cell (box distances are exact Euclidean distances)
 };
 
 }  // namespace flr

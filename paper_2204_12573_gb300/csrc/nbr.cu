@@ -332,6 +332,15 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
         const int bin = a.atom_bin[i] - (int)P.bin_base;
         const int bi[3] = {bin / (P.nb[1] * P.nb[2]), (bin / P.nb[2]) % P.nb[1], bin % P.nb[2]};
         const int imi = __float_as_int(pib.w) & 0xFFFFFF;
+        // the atom's offset inside its bin (bin units), for skipping stencil
+        // bins whose box lies farther than the list cutoff (orthogonal cells)
+        float u[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float f = pi.x * (float)P.inv[d] + pi.y * (float)P.inv[3 + d] + pi.z * (float)P.inv[6 + d];
+            if (P.pbc[d]) f -= floorf(f);
+            u[d] = (f - P.flo[d]) / P.fspan[d] * (float)P.nb[d] - (float)bi[d];
+        }
         int32_t *row = a.entries + (size_t)i * a.max_nbr;
         int cnt = 0;
         unsigned smask = 0;
@@ -356,6 +365,17 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                         sb[d] = 0;
                         bj[d] = kk;
                     }
+                }
+                if (!skip && P.orth) {
+                    // lower bound of the distance from the atom to the bin's box
+                    float d2 = 0.f;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float gap = dd[d] > 0 ? (float)dd[d] - u[d] : (dd[d] < 0 ? u[d] - (float)dd[d] - 1.f : 0.f);
+                        const float gm = fmaxf(gap, 0.f) * P.bw[d];
+                        d2 += gm * gm;
+                    }
+                    skip = d2 > a.rc2 * 1.0001f + 1e-3f;
                 }
                 if (!skip) {
                     const int b = (int)P.bin_base + (bj[0] * P.nb[1] + bj[1]) * P.nb[2] + bj[2];
@@ -647,8 +667,13 @@ int plan_grid(Plan &P, const float *bb, double rc, double margin)
         P.R[d] = R;
         P.flo[d] = (float)flo;
         P.fspan[d] = (float)fspan;
+        P.bw[d] = (float)(extent / nb);
         nbins *= nb;
     }
+    P.orth = 1;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            if (r != c && P.cell[3 * r + c] != 0.0) P.orth = 0;
     if (nbins > (1ll << 26)) {
         set_error("neighbour build: bin grid too large");
         return FLR_EINVAL;

@@ -37,9 +37,21 @@ def _slabs(k=3):
 
 # ------------------------------------------------------------ neighbours
 
-@pytest.mark.parametrize("which", ["tiny", "slab0", "slab1", "slab2"])
+def _ortho(n=3000, seed=21):
+    """An orthogonal-cell Pt(111)+H2 slab (the bin stencil is pruned by box distance there)."""
+    return synth.serving_structure(np.random.default_rng(seed), n)
+
+
+@pytest.mark.parametrize("which", ["tiny", "slab0", "slab1", "slab2", "ortho", "ortho_small"])
 def test_neighbor_sets_bit_exact(which):
-    s = _tiny() if which == "tiny" else _slabs()[int(which[-1])]
+    if which == "tiny":
+        s = _tiny()
+    elif which == "ortho":
+        s = _ortho()
+    elif which == "ortho_small":
+        s = _ortho(200, 22)
+    else:
+        s = _slabs()[int(which[-1])]
     g, *_ = gpu_run(s, BETA, SIGMA, max_nbr=96)
     pos = synth.f32_exact_f64(synth.as_f32_positions(s.pos))
     ref = O.neighbors(pos, s.cell, s.pbc, 5.0, method="brute" if s.n_atoms < 100 else "cells")
