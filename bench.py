@@ -166,7 +166,7 @@ def _pairs_within_cutoff(nl, sysg, n, r_cut):
         b = min(n, a + (1 << 18))
         e = entries[a:b].long()
         valid = torch.arange(e.shape[1], device="cuda")[None, :] < count[a:b, None]
-        j = e >> 7
+        j = e >> 8               # entry = (j << 8) | (s_j << 7) | image code
         code = e & 127
         s = torch.stack([code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2], -1).double()
         r = (pos[j.clamp(0, n - 1)].double() + s @ cell - pos[a:b, None, :].double())
