@@ -390,6 +390,7 @@ def run_ours(args):
         ferr[prec] = float(np.abs(r["forces"][sample] - o["F"]).max())
         okv = o["V"] > 0
         errs[prec] = {
+            "variance_fp64_atoms": int(r["totals"][14]),
             "force_max_ev_per_A": ferr[prec],
             "energy_max_rel": float((np.abs(r["energy"][sample] - o["E"]) / np.maximum(np.abs(o["E"]), 1.0)).max()),
             "variance_max_rel": float((np.abs(r["variance"][sample][okv] - o["V"][okv]) / o["V"][okv]).max()),

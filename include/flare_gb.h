@@ -57,6 +57,22 @@ typedef struct CUstream_st *flr_stream_t; /* == cudaStream_t; NULL = legacy defa
 #define FLR_PREC_TF32 1        /* tcgen05 kind::tf32, FP32 accumulate in tensor memory */
 #define FLR_PREC_BF16X3 2      /* tcgen05 kind::f16, hi/lo BF16 split, 3 products, FP32 accumulate */
 
+/* How the variance quadratic form V = d^T Sigma d (Eq. 2) is evaluated.
+ * DIRECT: the GEMM forms Sigma d and V = d . (Sigma d) in FP32.
+ * AUTO (the default): as DIRECT, and every atom whose V may have lost its
+ * digits gets V re-evaluated in FP64 from its FP32 descriptor and an FP64
+ * copy of Sigma (FLR_TOT_N_VAR_FP64 counts them): V below 1/32 of
+ * sum_k |d_k (Sigma d)_k| (the final sum cancelled), or V below 2e-3 (FP32
+ * GEMM) or 2e-2 (3xBF16) of |Sigma_c|_2 (the GEMM's absolute error scales
+ * with |Sigma_c|_2; this is how an ill-conditioned Sigma with d near its
+ * small-eigenvalue directions shows).  TF32 applies the first test only.  flr_set_model checks that Sigma is
+ * positive semi-definite (FP64 Cholesky).  FACTORED: the GEMM forms L^T d
+ * with Sigma_c = L L^T the Cholesky factor of each compaction class's block
+ * and V = |L^T d|^2, a sum of squares (no FP64 on the device). */
+#define FLR_VAR_AUTO 0
+#define FLR_VAR_DIRECT 1
+#define FLR_VAR_FACTORED 2
+
 /* indices into the per-evaluation totals array (double[FLR_NTOTALS], device) */
 #define FLR_TOT_ENERGY 0       /* sum_i E_i (eV), FP64 */
 #define FLR_TOT_VIRIAL 1       /* 9 entries, W_ab = -sum_pairs (r_ij)_a (dE_i/dr_ij)_b (eV), FP64 */
@@ -64,6 +80,7 @@ typedef struct CUstream_st *flr_stream_t; /* == cudaStream_t; NULL = legacy defa
 #define FLR_TOT_N_ISOLATED 11  /* atoms with no neighbour inside r_cut (descriptor defined as 0) */
 #define FLR_TOT_KINETIC 12     /* sum_i m_i v_i^2 / 2 (eV), written by flr_md_step only */
 #define FLR_TOT_N_REBUILDS 13  /* neighbour-list rebuilds performed by the last flr_md_step call */
+#define FLR_TOT_N_VAR_FP64 14  /* atoms whose variance was re-evaluated in FP64 (FLR_VAR_AUTO) */
 #define FLR_NTOTALS 16
 
 typedef struct flr_ctx flr_ctx;
@@ -166,6 +183,12 @@ int flr_set_precision(flr_ctx *ctx, int32_t precision);
  * flr_last_error as information).  Builds the per-class compacted blocks
  * and the FP32 / BF16-hi/lo copies on the device.  Synchronous. */
 int flr_set_model(flr_ctx *ctx, int32_t species, const double *beta, const double *sigma);
+
+/* Choose the variance evaluation (FLR_VAR_*) for models set afterwards and
+ * re-upload the models already set.  FLR_EINVAL if a Sigma block is not
+ * positive semi-definite (its Cholesky factorization fails even after a
+ * diagonal shift of 1e-10 of its trace). */
+int flr_set_variance_mode(flr_ctx *ctx, int32_t mode);
 
 /* Allocate a neighbour list for systems of up to n_atoms atoms (device
  * memory: n_atoms * max_nbr * 4 bytes plus O(n_atoms) bookkeeping). */

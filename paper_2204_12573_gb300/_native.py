@@ -23,6 +23,7 @@ FLR_EDEVICE = 7
 FLR_ENOMODEL = 8
 
 PREC = {"fp32": 0, "tf32": 1, "bf16x3": 2}
+VAR_MODE = {"auto": 0, "direct": 1, "factored": 2}
 
 TOT_ENERGY = 0
 TOT_VIRIAL = 1
@@ -30,6 +31,7 @@ TOT_MAX_SIGMA = 10
 TOT_N_ISOLATED = 11
 TOT_KINETIC = 12
 TOT_N_REBUILDS = 13
+TOT_N_VAR_FP64 = 14
 NTOTALS = 16
 
 EXPORTED = [
@@ -40,7 +42,7 @@ EXPORTED = [
     "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
     "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
     "flr_bytes_per_atom", "flr_server_create", "flr_server_submit", "flr_server_poll", "flr_server_stats_read",
-    "flr_server_destroy",
+    "flr_server_destroy", "flr_set_variance_mode",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
@@ -124,6 +126,7 @@ def lib():
             "flr_destroy": (ctypes.c_int, [P]),
             "flr_descriptor_dims": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
             "flr_set_precision": (ctypes.c_int, [P, ctypes.c_int32]),
+            "flr_set_variance_mode": (ctypes.c_int, [P, ctypes.c_int32]),
             "flr_set_model": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
             "flr_nbrlist_create": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P)]),
             "flr_nbrlist_destroy": (ctypes.c_int, [P]),

@@ -138,6 +138,8 @@ void free_workspace(flr_ctx *ctx)
     ctx->vir_atom = nullptr;
     cudaFree(ctx->scratch_out);
     ctx->scratch_out = nullptr;
+    cudaFree(ctx->ref_list);
+    ctx->ref_list = nullptr;
     ctx->A = ctx->norm = nullptr;
     ctx->Facc = nullptr;
     ctx->partials = nullptr;
@@ -168,6 +170,7 @@ int ensure_workspace(flr_ctx *ctx, int n)
     if (s == FLR_OK) s = dev_alloc(&ctx->Facc, N * 3, "workspace forces");
     if (s == FLR_OK) s = dev_alloc(&ctx->vir_atom, N * 9, "workspace virial");
     if (s == FLR_OK) s = dev_alloc(&ctx->scratch_out, N * 3, "workspace outputs");
+    if (s == FLR_OK) s = dev_alloc(&ctx->ref_list, N, "workspace variance queue");
     if (s == FLR_OK) s = dev_alloc(&ctx->partials, (size_t)kMaxPartials * 13 + 16, "workspace partials");
     if (s != FLR_OK) {
         free_workspace(ctx);
@@ -248,7 +251,12 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
     prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
     if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_QFORM, st);
+    if (ctx->var_mode == FLR_VAR_AUTO) {
+        e = cudaMemsetAsync(ctx->ref_count, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "clear variance queue");
+    }
     s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, out, st) : launch_qform_tc(ctx, nl, out, st);
+    if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) s = launch_variance_fp64(ctx, nl, out, st);
     prof_end(ctx, FLR_KERNEL_QFORM, st);
     if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_FORCE, st);
@@ -394,6 +402,8 @@ int flr_create(const flr_params *p, int device, flr_ctx **out)
         D.nrows_pad[r] = round_up(2 * D.K[r], 288);
     }
     int s = dev_alloc(&c->status, 4, "status word");
+    if (s == FLR_OK) s = dev_alloc(&c->ref_count, 1, "variance queue counter");
+    if (s == FLR_OK) s = cuda_fail(cudaMemset(c->ref_count, 0, sizeof(int)), "variance queue counter");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(c->status, 0, 4 * sizeof(int)), "status word");
     // index tables
     std::vector<int32_t> tf, ts;
@@ -431,6 +441,7 @@ int flr_destroy(flr_ctx *c)
         cudaFree(c->W32[g]);
         cudaFree(c->Whi[g]);
         cudaFree(c->Wlo[g]);
+        cudaFree(c->S64[g]);
     }
     for (int s = 0; s < kSpecies; ++s) {
         delete[] c->beta_h[s];
@@ -439,6 +450,7 @@ int flr_destroy(flr_ctx *c)
     cudaFree(c->tab_full);
     cudaFree(c->tab_single);
     cudaFree(c->status);
+    cudaFree(c->ref_count);
     delete c->maps;
     if (c->prof) {
         prof_drain(c->prof);
@@ -469,26 +481,59 @@ int flr_set_precision(flr_ctx *c, int32_t precision)
     return FLR_OK;
 }
 
-int flr_set_model(flr_ctx *c, int32_t species, const double *beta, const double *sigma)
+}  // extern "C"
+
+namespace flr {
+namespace {
+
+// Cholesky factor L (lower, row-major K x K) of a symmetric positive
+// semi-definite matrix, in FP64.  On a non-positive pivot the diagonal is
+// shifted by 1e-14, 1e-12, then 1e-10 of the trace and the factorization
+// restarted; false if it still fails.  pivot_ratio = max pivot / min pivot
+// (pivots lie inside the spectrum, so this bounds the condition number from
+// below).
+bool cholesky(const std::vector<double> &S, int K, std::vector<double> &L, double &pivot_ratio)
 {
-    if (!c || !beta || !sigma || species < 0 || species >= kSpecies) {
-        set_error("flr_set_model: invalid argument");
-        return FLR_EINVAL;
+    double tr = 0.0;
+    for (int i = 0; i < K; ++i) tr += S[(size_t)i * K + i];
+    for (double rel : {0.0, 1e-14, 1e-12, 1e-10}) {
+        const double tau = rel * tr;
+        L.assign((size_t)K * K, 0.0);
+        bool ok = true;
+        double pmin = 1e300, pmax = 0.0;
+        for (int j = 0; j < K && ok; ++j) {
+            double s = S[(size_t)j * K + j] + tau;
+            for (int k = 0; k < j; ++k) s -= L[(size_t)j * K + k] * L[(size_t)j * K + k];
+            if (!(s > 0.0)) {
+                ok = false;
+                break;
+            }
+            const double ljj = std::sqrt(s);
+            L[(size_t)j * K + j] = ljj;
+            pmin = std::min(pmin, s);
+            pmax = std::max(pmax, s);
+            for (int i = j + 1; i < K; ++i) {
+                double t = S[(size_t)i * K + j];
+                for (int k = 0; k < j; ++k) t -= L[(size_t)i * K + k] * L[(size_t)j * K + k];
+                L[(size_t)i * K + j] = t / ljj;
+            }
+        }
+        if (ok) {
+            pivot_ratio = pmax / pmin;
+            return true;
+        }
     }
-    cudaSetDevice(c->device);
+    return false;
+}
+
+// Build and upload the B operands of one species' three compaction groups:
+// rows [beta_c ; Sigma_c] (DIRECT) or [beta_c ; L_c^T] (FACTORED), restricted
+// to the class block c, as FP32 and as BF16 hi / lo parts.
+int upload_species(flr_ctx *c, int species)
+{
     const Dims &D = c->dims;
     const int d = D.d_full;
-    double *bh = new double[(size_t)d * d], *sh = new double[(size_t)d * d];
-    for (int r = 0; r < d; ++r)
-        for (int q = 0; q < d; ++q) {
-            bh[(size_t)r * d + q] = 0.5 * (beta[(size_t)r * d + q] + beta[(size_t)q * d + r]);
-            sh[(size_t)r * d + q] = 0.5 * (sigma[(size_t)r * d + q] + sigma[(size_t)q * d + r]);
-        }
-    delete[] c->beta_h[species];
-    delete[] c->sigma_h[species];
-    c->beta_h[species] = bh;
-    c->sigma_h[species] = sh;
-    // compact index maps of the three classes
+    const double *bh = c->beta_h[species], *sh = c->sigma_h[species];
     std::vector<int> idx_full(d), idx_single[kSpecies];
     for (int k = 0; k < d; ++k) idx_full[k] = k;
     for (int t = 0; t < kSpecies; ++t)
@@ -499,13 +544,60 @@ int flr_set_model(flr_ctx *c, int32_t species, const double *beta, const double 
         const int g = species * 3 + cls, r = group_region(g);
         const std::vector<int> &idx = cls == 0 ? idx_full : idx_single[cls - 1];
         const int K = D.K[r], rows = D.nrows_pad[r];
+        // the class block of Sigma and, when needed, its Cholesky factor
+        bool factored = c->var_mode == FLR_VAR_FACTORED;
+        std::vector<double> Lf;
+        if (c->var_mode != FLR_VAR_DIRECT) {
+            std::vector<double> Sc((size_t)K * K);
+            for (int i = 0; i < K; ++i)
+                for (int k = 0; k < K; ++k) Sc[(size_t)i * K + k] = sh[(size_t)idx[i] * d + idx[k]];
+            double ratio = 0.0;
+            if (!cholesky(Sc, K, Lf, ratio)) {
+                set_error("flr_set_model: Sigma of species " + std::to_string(species) +
+                          " is not positive semi-definite (Cholesky factorization failed)");
+                return FLR_EINVAL;
+            }
+            (void)ratio;
+        }
+        c->var_factored[g] = factored ? 1 : 0;
+        {
+            // FP64 copy of the class block of Sigma for the FP64 variance
+            std::vector<double> S64((size_t)K * K);
+            for (int i = 0; i < K; ++i)
+                for (int k = 0; k < K; ++k) S64[(size_t)i * K + k] = sh[(size_t)idx[i] * d + idx[k]];
+            int s = FLR_OK;
+            if (!c->S64[g]) s = dev_alloc(&c->S64[g], S64.size(), "model");
+            if (s == FLR_OK)
+                s = cuda_fail(cudaMemcpy(c->S64[g], S64.data(), S64.size() * 8, cudaMemcpyHostToDevice), "model upload");
+            if (s != FLR_OK) return s;
+            // largest eigenvalue of the block by power iteration (PSD: |Sigma|_2)
+            std::vector<double> x(K, 1.0), y(K);
+            double lam = 0.0;
+            for (int it = 0; it < 40; ++it) {
+                double ny = 0.0;
+                for (int i = 0; i < K; ++i) {
+                    double t = 0.0;
+                    for (int k = 0; k < K; ++k) t += S64[(size_t)i * K + k] * x[k];
+                    y[i] = t;
+                    ny += t * t;
+                }
+                ny = std::sqrt(ny);
+                double nx = 0.0;
+                for (int i = 0; i < K; ++i) nx += x[i] * x[i];
+                lam = ny / std::sqrt(nx);
+                if (!(ny > 0.0)) break;
+                for (int i = 0; i < K; ++i) x[i] = y[i] / ny;
+            }
+            c->sigma_norm[g] = (float)lam;
+        }
         std::vector<float> w32((size_t)rows * D.kp32[r], 0.f);
         std::vector<uint16_t> whi((size_t)rows * D.kp64[r], 0), wlo((size_t)rows * D.kp64[r], 0);
         for (int n = 0; n < 2 * K; ++n) {
-            const double *src = n < K ? bh : sh;
-            const int rn = idx[n % K];
             for (int k = 0; k < K; ++k) {
-                const double v = src[(size_t)rn * d + idx[k]];
+                double v;
+                if (n < K) v = bh[(size_t)idx[n] * d + idx[k]];
+                else if (!factored) v = sh[(size_t)idx[n - K] * d + idx[k]];
+                else v = Lf[(size_t)k * K + (n - K)];   // row n-K of L^T
                 w32[(size_t)n * D.kp32[r] + k] = (float)v;
                 const uint16_t h = f2bf((float)v);
                 whi[(size_t)n * D.kp64[r] + k] = h;
@@ -526,8 +618,57 @@ int flr_set_model(flr_ctx *c, int32_t species, const double *beta, const double 
             s = cuda_fail(cudaMemcpy(c->Wlo[g], wlo.data(), wlo.size() * 2, cudaMemcpyHostToDevice), "model upload");
         if (s != FLR_OK) return s;
     }
+    return FLR_OK;
+}
+
+}  // namespace
+}  // namespace flr
+
+extern "C" {
+
+int flr_set_model(flr_ctx *c, int32_t species, const double *beta, const double *sigma)
+{
+    if (!c || !beta || !sigma || species < 0 || species >= kSpecies) {
+        set_error("flr_set_model: invalid argument");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    const int d = c->dims.d_full;
+    double *bh = new double[(size_t)d * d], *sh = new double[(size_t)d * d];
+    for (int r = 0; r < d; ++r)
+        for (int q = 0; q < d; ++q) {
+            bh[(size_t)r * d + q] = 0.5 * (beta[(size_t)r * d + q] + beta[(size_t)q * d + r]);
+            sh[(size_t)r * d + q] = 0.5 * (sigma[(size_t)r * d + q] + sigma[(size_t)q * d + r]);
+        }
+    delete[] c->beta_h[species];
+    delete[] c->sigma_h[species];
+    c->beta_h[species] = bh;
+    c->sigma_h[species] = sh;
+    c->model_set[species] = false;
+    const int s = upload_species(c, species);
+    if (s != FLR_OK) return s;
     c->model_set[species] = true;
     c->maps_n = -1;   // B maps point at the (possibly new) buffers
+    return FLR_OK;
+}
+
+int flr_set_variance_mode(flr_ctx *c, int32_t mode)
+{
+    if (!c || mode < FLR_VAR_AUTO || mode > FLR_VAR_FACTORED) {
+        set_error("flr_set_variance_mode: invalid argument");
+        return FLR_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    c->var_mode = mode;
+    for (int sp = 0; sp < kSpecies; ++sp)
+        if (c->model_set[sp]) {
+            const int s = upload_species(c, sp);
+            if (s != FLR_OK) {
+                c->model_set[sp] = false;
+                return s;
+            }
+        }
+    c->maps_n = -1;
     return FLR_OK;
 }
 

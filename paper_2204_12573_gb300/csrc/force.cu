@@ -547,6 +547,7 @@ struct TotArgs {
     int n_part;
     double *totals;
     const int32_t *nl_flags;
+    const int *ref_count;    // atoms whose variance was re-evaluated in FP64 (or nullptr)
     int kick;
 };
 
@@ -593,6 +594,7 @@ __global__ void __launch_bounds__(1024) k_totals(TotArgs a)
         a.totals[FLR_TOT_MAX_SIGMA] = t[11];
         a.totals[FLR_TOT_N_ISOLATED] = I;
         if (a.kick) a.totals[FLR_TOT_KINETIC] = t[10];
+        a.totals[FLR_TOT_N_VAR_FP64] = a.ref_count ? (double)*a.ref_count : 0.0;
     }
 }
 
@@ -737,6 +739,7 @@ int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out
     t.n_part = nfin;
     t.totals = out->totals;
     t.nl_flags = nl ? nl->flags : nullptr;
+    t.ref_count = ctx->var_mode == FLR_VAR_AUTO ? ctx->ref_count : nullptr;
     t.kick = kick.enabled;
     if (out->totals) k_totals<<<1, 1024, 0, st>>>(t);
     count_launch(ctx, out->totals ? 2 : 1);

@@ -129,6 +129,12 @@ struct flr_ctx {
     bool model_set[flr::kSpecies];
     double *beta_h[flr::kSpecies];     // host copies (symmetrized), d_full^2
     double *sigma_h[flr::kSpecies];
+    int var_mode;                      // FLR_VAR_*
+    int var_factored[flr::kGroups];    // 1: the group's Sigma rows hold L^T (V = |L^T d|^2)
+    double *S64[flr::kGroups];         // FP64 Sigma block of each group (K x K), for the FP64 variance
+    float sigma_norm[flr::kGroups];    // largest eigenvalue of each group's Sigma block (power iteration)
+    int32_t *ref_list;                 // [ws_n] atoms queued for the FP64 variance
+    int *ref_count;                    // device counter of ref_list
     float *W32[flr::kGroups];          // [nrows_pad][kp32]  B operand rows (beta rows, then Sigma rows)
     __nv_bfloat16 *Whi[flr::kGroups];  // [nrows_pad][kp64]
     __nv_bfloat16 *Wlo[flr::kGroups];
@@ -219,6 +225,14 @@ struct KickArgs {
 int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick, float sign,
                     cudaStream_t st);
 int launch_dbeta(flr_ctx *ctx, const flr_nbrlist *nl, const float *u, float *grad_beta, cudaStream_t st);
+// FP64 re-evaluation of the variance of the atoms the epilogue queued (FLR_VAR_AUTO)
+int launch_variance_fp64(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
+constexpr float kVarCancel = 32.f;   // queue an atom when V < (sum_k |d_k (Sigma d)_k|) / kVarCancel
+// ... or when V < kVarSmall * |Sigma_c|_2: the FP32 GEMM's absolute error on V scales with
+// |Sigma_c|_2, so a variance this small relative to the prior's scale keeps too few digits
+// (the GEMM's own cancellation, which the final sum cannot see).  Per precision:
+constexpr float kVarSmallFP32 = 2e-3f;
+constexpr float kVarSmallBF16x3 = 2e-2f;
 int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, const float *forces,
                     const int *species, int n, const KickArgs &kick, float dt, float disp2_max,
                     cudaStream_t st);

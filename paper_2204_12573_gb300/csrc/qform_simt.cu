@@ -144,6 +144,12 @@ struct EpiArgs {
     const float *P[2];
     float *G[2];
     float *energy, *variance, *sigma;
+    int var_factored[kGroups];   // 1: P_Sigma holds L^T d, V = |L^T d|^2
+    int refine;                  // queue atoms whose V cancelled for the FP64 variance
+    float v_small[kGroups];      // ... or is below this (kVarSmallFP32 x |Sigma_c|_2)
+    int32_t *ref_list;
+    int *ref_count;
+    int ref_cap;
     int n;
 };
 
@@ -157,16 +163,21 @@ __global__ void __launch_bounds__(256) k_qform_epilogue(EpiArgs a)
         const int reg = group_region(g), K = a.K[reg], r = a.row[i];
         const float4 *d4 = reinterpret_cast<const float4 *>(a.D32[reg] + (size_t)r * a.kp32[reg]);
         const float4 *p4 = reinterpret_cast<const float4 *>(a.P[reg] + (size_t)r * (2 * K));
-        float E = 0.f, V = 0.f;
+        float E = 0.f, V = 0.f, Va = 0.f;
+        const bool fact = a.var_factored[g] != 0;
         for (int o = lane; 4 * o < K; o += 32) {
             const float4 d = d4[o], pb = p4[o], ps = p4[K / 4 + o];
             E += d.x * pb.x + d.y * pb.y + d.z * pb.z + d.w * pb.w;
-            V += d.x * ps.x + d.y * ps.y + d.z * ps.z + d.w * ps.w;
+            const float4 t = fact ? make_float4(ps.x * ps.x, ps.y * ps.y, ps.z * ps.z, ps.w * ps.w)
+                                  : make_float4(d.x * ps.x, d.y * ps.y, d.z * ps.z, d.w * ps.w);
+            V += t.x + t.y + t.z + t.w;
+            Va += fabsf(t.x) + fabsf(t.y) + fabsf(t.z) + fabsf(t.w);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             E += __shfl_xor_sync(0xffffffffu, E, o);
             V += __shfl_xor_sync(0xffffffffu, V, o);
+            Va += __shfl_xor_sync(0xffffffffu, Va, o);
         }
         const float nrm = a.norm[i];
         const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
@@ -180,6 +191,10 @@ __global__ void __launch_bounds__(256) k_qform_epilogue(EpiArgs a)
             a.energy[i] = E;
             if (a.variance) a.variance[i] = V;
             if (a.sigma) a.sigma[i] = sqrtf(fmaxf(V, 0.f));
+            if (a.refine && !fact && (V * kVarCancel < Va || V < a.v_small[g])) {
+                const int q = atomicAdd(a.ref_count, 1);
+                if (q < a.ref_cap) a.ref_list[q] = i;
+            }
         }
     }
 }
@@ -213,6 +228,12 @@ int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cud
     e.variance = out->variance;
     e.sigma = out->sigma;
     e.n = nl->n;
+    for (int g = 0; g < kGroups; ++g) e.var_factored[g] = ctx->var_factored[g];
+    e.refine = ctx->var_mode == FLR_VAR_AUTO;
+    for (int g = 0; g < kGroups; ++g) e.v_small[g] = kVarSmallFP32 * ctx->sigma_norm[g];
+    e.ref_list = ctx->ref_list;
+    e.ref_count = ctx->ref_count;
+    e.ref_cap = ctx->ws_n;
     k_qform_epilogue<<<persistent_grid(k_qform_epilogue, 256, ctx->num_sms, (nl->n + 7) / 8), 256, 0, st>>>(e);
     count_launch(ctx, 2);
     return cuda_fail(cudaGetLastError(), "FP32 quadratic-form GEMM");

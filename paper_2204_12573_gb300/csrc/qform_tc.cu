@@ -57,6 +57,12 @@ struct TcArgs {
     const float *norm;
     float *energy, *variance, *sigma;
     const GroupTab *gtab;
+    int var_factored[kGroups];   // 1: the Sigma columns hold L^T d, V = |L^T d|^2
+    int refine;                  // queue atoms whose V cancelled for the FP64 variance
+    float v_small[kGroups];      // ... or is below this (kVarSmall* x |Sigma_c|_2)
+    int32_t *ref_list;
+    int *ref_count;
+    int ref_cap;
     int *status;
 };
 
@@ -198,8 +204,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
     // bars: full[kStages], empty[kStages], tfull, tempty, drain, evx
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
-    // partial (E, V) of each row from the two column halves, double-buffered by tile
-    float2 *evx_buf = reinterpret_cast<float2 *>(base + kStages * kStageBytes + 128);
+    // partial (E, V, sum |d_k (Sigma d)_k|) of each row from the two column
+    // halves, double-buffered by tile
+    float4 *evx_buf = reinterpret_cast<float4 *>(base + kStages * kStageBytes + 128);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
@@ -349,7 +356,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             const float *d = a.D32[ti.reg] + (size_t)(valid ? row : 0) * a.kp32[ti.reg];
             float *grow = a.G[ti.reg] + (size_t)(valid ? row : 0) * K;
             const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
-            float E = 0.f, V = 0.f;
+            const bool fact = a.var_factored[ti.g] != 0;
+            float E = 0.f, V = 0.f, Va = 0.f;
             for (int ch = 0; ch < ti.nch; ++ch, ++it) {
                 // lane 0 waits and the warp follows its verdict, so the warp stays converged
                 int okw = 1;
@@ -377,7 +385,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
 #pragma unroll
                             for (int k = 0; k < 16; ++k) {
                                 E += dv[k] * vb[k];
-                                V += dv[k] * vs[k];
+                                const float t = (fact ? vs[k] : dv[k]) * vs[k];
+                                V += t;
+                                Va += fabsf(t);
                             }
 #pragma unroll
                             for (int k = 0; k < 16; k += 4)
@@ -403,7 +413,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                                     *reinterpret_cast<float4 *>(grow + cg + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
                             } else if (sigma_cols) {
 #pragma unroll
-                                for (int k = 0; k < 16; ++k) V += dv[k] * v[k];
+                                for (int k = 0; k < 16; ++k) {
+                                    const float t = (fact ? v[k] : dv[k]) * v[k];
+                                    V += t;
+                                    Va += fabsf(t);
+                                }
                             } else {                                  // a group straddling K or 2K
 #pragma unroll
                                 for (int k = 0; k < 16; ++k) {
@@ -412,7 +426,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                                         E += __ldg(d + cc) * v[k];
                                         grow[cc] = v[k];
                                     } else if (cc < 2 * K) {
-                                        V += __ldg(d + cc - K) * v[k];
+                                        const float t = (fact ? v[k] : __ldg(d + cc - K)) * v[k];
+                                        V += t;
+                                        Va += fabsf(t);
                                     }
                                 }
                             }
@@ -448,8 +464,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 }
             }
             // combine the two halves' partial sums (fixed order: half 0 + half 1)
-            float2 *xb = evx_buf + (tl & 1) * (2 * BM);
-            xb[sub * BM + rloc] = make_float2(E, V);
+            float4 *xb = evx_buf + (tl & 1) * (2 * BM);
+            xb[sub * BM + rloc] = make_float4(E, V, Va, 0.f);
             __syncwarp();
             int okx = 1;
             if (lane == 0) {
@@ -466,9 +482,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 alive = false;
                 break;
             }
-            const float2 p0 = xb[rloc], p1 = xb[BM + rloc];
+            const float4 p0 = xb[rloc], p1 = xb[BM + rloc];
             E = p0.x + p1.x;
             V = p0.y + p1.y;
+            Va = p0.z + p1.z;
             if (valid) {
                 // g = (2/||B||)(beta d - E d) over the 16-column groups this half parked
                 float4 *g4 = reinterpret_cast<float4 *>(grow);
@@ -493,6 +510,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     a.energy[atom] = E;
                     if (a.variance) a.variance[atom] = V;
                     if (a.sigma) a.sigma[atom] = sqrtf(fmaxf(V, 0.f));
+                    if (a.refine && !fact && (V * kVarCancel < Va || V < a.v_small[ti.g])) {
+                        const int q = atomicAdd(a.ref_count, 1);
+                        if (q < a.ref_cap) a.ref_list[q] = atom;
+                    }
                 }
             }
         }
@@ -603,10 +624,17 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaS
     a.variance = out->variance;
     a.sigma = out->sigma;
     a.gtab = nl->gtab;
+    for (int g = 0; g < kGroups; ++g) a.var_factored[g] = ctx->var_factored[g];
+    a.refine = ctx->var_mode == FLR_VAR_AUTO;
+    for (int g = 0; g < kGroups; ++g)   // TF32 is the low-precision option: only the cancellation test
+        a.v_small[g] = bf16 ? kVarSmallBF16x3 * ctx->sigma_norm[g] : 0.f;
+    a.ref_list = ctx->ref_list;
+    a.ref_count = ctx->ref_count;
+    a.ref_cap = ctx->ws_n;
     a.status = ctx->status;
-    // ring + barriers (128 B) + the E / V exchange (2 tiles x 2 halves x BM float2),
+    // ring + barriers (128 B) + the E / V exchange (2 tiles x 2 halves x BM float4),
     // and at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM
-    const size_t smem = std::max<size_t>(1024 + (size_t)kStages * kStageBytes + 128 + 2 * 2 * BM * sizeof(float2),
+    const size_t smem = std::max<size_t>(1024 + (size_t)kStages * kStageBytes + 128 + 2 * 2 * BM * sizeof(float4),
                                          116 * 1024);
     cudaError_t e;
     if (bf16) {

@@ -90,6 +90,11 @@ class FlareGB:
         N.check(self.lib.flr_set_precision(self.handle, N.PREC[precision]))
         self.precision = precision
 
+    def set_variance_mode(self, mode: str):
+        """"auto" (FP32 quadratic form, FP64 re-evaluation of cancelled
+        variances), "direct" (FP32 only) or "factored" (V = |L^T d|^2)."""
+        N.check(self.lib.flr_set_variance_mode(self.handle, N.VAR_MODE[mode]))
+
     def set_model(self, beta, sigma):
         """beta, sigma: [n_species, d_full, d_full] float64 (host)."""
         beta = np.ascontiguousarray(beta, np.float64)

@@ -305,11 +305,12 @@ def descriptor_dims(n_species: int, n_max: int, l_max: int):
     return c * (c + 1) // 2 * (l_max + 1), n_max * (n_max + 1) // 2 * (l_max + 1)
 
 
-def random_symmetric(d: int, seed: int, kind: str) -> np.ndarray:
+def random_symmetric(d: int, seed: int, kind: str, sigma_log10_min: float = -4.0) -> np.ndarray:
     """Seeded random symmetric d x d matrix (float64).
 
     kind == "beta":  eigenvalues U[-1, 1], rescaled so the spectral norm is 1.
-    kind == "sigma": eigenvalues log-uniform in [1e-4, 1] (positive definite).
+    kind == "sigma": eigenvalues log-uniform in [10^sigma_log10_min, 1]
+                     (positive definite; the default range is [1e-4, 1]).
     """
     rng = np.random.default_rng(seed)
     g = rng.normal(size=(d, d))
@@ -319,7 +320,7 @@ def random_symmetric(d: int, seed: int, kind: str) -> np.ndarray:
         lam = rng.uniform(-1.0, 1.0, size=d)
         lam = lam / np.abs(lam).max()
     elif kind == "sigma":
-        lam = 10.0 ** rng.uniform(-4.0, 0.0, size=d)
+        lam = 10.0 ** rng.uniform(sigma_log10_min, 0.0, size=d)
     else:
         raise ValueError(kind)
     m = (q * lam[None, :]) @ q.T
@@ -327,10 +328,11 @@ def random_symmetric(d: int, seed: int, kind: str) -> np.ndarray:
 
 
 def random_model(n_species: int = 2, n_max: int = 8, l_max: int = 3,
-                 beta_seed: int = 1001, sigma_seed: int = 2001):
+                 beta_seed: int = 1001, sigma_seed: int = 2001, sigma_log10_min: float = -4.0):
     """beta[s], Sigma[s] for each species s (float64, [S, d, d]); seeds are
-    beta_seed + s and sigma_seed + s."""
+    beta_seed + s and sigma_seed + s; Sigma's eigenvalues are log-uniform in
+    [10^sigma_log10_min, 1]."""
     d, _ = descriptor_dims(n_species, n_max, l_max)
     beta = np.stack([random_symmetric(d, beta_seed + s, "beta") for s in range(n_species)])
-    sigma = np.stack([random_symmetric(d, sigma_seed + s, "sigma") for s in range(n_species)])
+    sigma = np.stack([random_symmetric(d, sigma_seed + s, "sigma", sigma_log10_min) for s in range(n_species)])
     return beta, sigma
