@@ -81,7 +81,12 @@ typedef struct CUstream_st *flr_stream_t; /* == cudaStream_t; NULL = legacy defa
 #define FLR_TOT_KINETIC 12     /* sum_i m_i v_i^2 / 2 (eV), written by flr_md_step only */
 #define FLR_TOT_N_REBUILDS 13  /* neighbour-list rebuilds performed by the last flr_md_step call */
 #define FLR_TOT_N_VAR_FP64 14  /* atoms whose variance was re-evaluated in FP64 (FLR_VAR_AUTO) */
-#define FLR_NTOTALS 16
+#define FLR_TOT_N_UNCERTAIN 15 /* flr_md_step: atoms with sigma > sigma_stop at the last step run */
+#define FLR_TOT_N_CN 16        /* flr_md_step: atoms of species cn_species with a same-species
+                                  neighbour closer than cn_cutoff (2 per intact H2 molecule) */
+#define FLR_TOT_THERMOSTAT 17  /* flr_md_step (NVT): Q xi^2 / 2 + g kB T eta (eV); with the
+                                  potential and kinetic energies this sum is conserved */
+#define FLR_NTOTALS 24
 
 typedef struct flr_ctx flr_ctx;
 typedef struct flr_nbrlist flr_nbrlist;
@@ -153,6 +158,22 @@ typedef struct {
     int32_t rebuild_every;  /* forced rebuild cadence in steps (plus max displacement > skin/2) */
     int32_t forces_valid;   /* set to 1 by flr_md_step on return */
     int64_t step;           /* running step counter, advanced by flr_md_step */
+    /* Nose-Hoover thermostat (NVT; Sec. VI-A runs at fixed temperature):
+     * temperature > 0 turns it on, tau is its period (ps); xi (1/ps) and eta
+     * (its time integral) are the thermostat state, kept here between calls. */
+    double temperature;
+    double tau;
+    double xi, eta;
+    /* Uncertainty-triggered stop (the on-the-fly learning trigger of Sec. II):
+     * sigma_stop > 0 ends the call after the first step at which some atom's
+     * sigma exceeds it (halted = 1; FLR_TOT_N_UNCERTAIN counts the atoms). */
+    double sigma_stop;
+    int32_t halted;
+    /* Coordination count for reaction monitoring: atoms of species
+     * cn_species with a neighbour of the same species closer than cn_cutoff
+     * (A) at the last step (FLR_TOT_N_CN); cn_species < 0 turns it off. */
+    int32_t cn_species;
+    double cn_cutoff;
 } flr_md_state;
 
 /* Thread-local text of the last error on the calling thread. */
@@ -260,7 +281,12 @@ int flr_energy_forces_uncertainty(flr_ctx *ctx, const flr_system *sys, const flr
  * rebuild when due (every rebuild_every steps, or when an atom moved more
  * than skin/2 since the last build, decided on the device), forces, half
  * kick.  Positions are wrapped into the cell at each rebuild.  The list
- * must have been built once with flr_build_neighbors.  Asynchronous. */
+ * must have been built once with flr_build_neighbors.  With a thermostat
+ * (st->temperature > 0), Nose-Hoover half steps wrap each step: xi is
+ * advanced from the kinetic energy and the velocities are scaled by
+ * exp(-xi dt / 2).  Asynchronous, except that the call synchronizes the
+ * stream at its end when the thermostat is on (xi and eta return to *st)
+ * and after every step when sigma_stop > 0 (the stop test reads a count). */
 int flr_md_step(flr_ctx *ctx, flr_md_state *st, flr_nbrlist *nl, int32_t n_steps,
                 flr_outputs *out, flr_stream_t stream);
 

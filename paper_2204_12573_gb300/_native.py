@@ -32,7 +32,10 @@ TOT_N_ISOLATED = 11
 TOT_KINETIC = 12
 TOT_N_REBUILDS = 13
 TOT_N_VAR_FP64 = 14
-NTOTALS = 16
+NTOTALS = 24
+TOT_N_UNCERTAIN = 15
+TOT_N_CN = 16
+TOT_THERMOSTAT = 17
 
 EXPORTED = [
     "flr_last_error", "flr_version", "flr_create", "flr_destroy", "flr_descriptor_dims",
@@ -74,7 +77,10 @@ class MDState(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int32), ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p),
                 ("species", ctypes.c_void_p), ("cell", ctypes.c_double * 9), ("pbc", ctypes.c_int32 * 3),
                 ("masses", ctypes.c_double * 8), ("dt", ctypes.c_double), ("rebuild_every", ctypes.c_int32),
-                ("forces_valid", ctypes.c_int32), ("step", ctypes.c_int64)]
+                ("forces_valid", ctypes.c_int32), ("step", ctypes.c_int64), ("temperature", ctypes.c_double),
+                ("tau", ctypes.c_double), ("xi", ctypes.c_double), ("eta", ctypes.c_double),
+                ("sigma_stop", ctypes.c_double), ("halted", ctypes.c_int32), ("cn_species", ctypes.c_int32),
+                ("cn_cutoff", ctypes.c_double)]
 
 
 class ServerParams(ctypes.Structure):

@@ -403,6 +403,9 @@ int flr_create(const flr_params *p, int device, flr_ctx **out)
     }
     int s = dev_alloc(&c->status, 4, "status word");
     if (s == FLR_OK) s = dev_alloc(&c->ref_count, 1, "variance queue counter");
+    if (s == FLR_OK) s = dev_alloc(&c->md_sc, 8 + 256, "MD scalars");
+    if (s == FLR_OK) s = dev_alloc(&c->md_totals, FLR_NTOTALS, "MD totals");
+    if (s == FLR_OK) s = dev_alloc(&c->md_cnt, 2, "MD counters");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(c->ref_count, 0, sizeof(int)), "variance queue counter");
     if (s == FLR_OK) s = cuda_fail(cudaMemset(c->status, 0, 4 * sizeof(int)), "status word");
     // index tables
@@ -451,6 +454,9 @@ int flr_destroy(flr_ctx *c)
     cudaFree(c->tab_single);
     cudaFree(c->status);
     cudaFree(c->ref_count);
+    cudaFree(c->md_sc);
+    cudaFree(c->md_totals);
+    cudaFree(c->md_cnt);
     delete c->maps;
     if (c->prof) {
         prof_drain(c->prof);
@@ -923,12 +929,29 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
         set_error("flr_md_step: pos and vel must be 16-byte aligned float[n][4]");
         return FLR_EINVAL;
     }
+    const bool nvt = md->temperature > 0.0;
+    const bool stop = md->sigma_stop > 0.0;
+    const bool cn = md->cn_species >= 0;
+    if (nvt && !(md->tau > 0.0)) {
+        set_error("flr_md_step: the thermostat needs tau > 0");
+        return FLR_EINVAL;
+    }
+    if (stop && !out->sigma) {
+        set_error("flr_md_step: sigma_stop needs the sigma output");
+        return FLR_EINVAL;
+    }
+    if (cn && (md->cn_species >= kSpecies || !(md->cn_cutoff > 0.0) || md->cn_cutoff > c->p.r_cut)) {
+        set_error("flr_md_step: cn_species must be a species and 0 < cn_cutoff <= r_cut");
+        return FLR_EINVAL;
+    }
+    md->halted = 0;
     cudaSetDevice(c->device);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int n = md->n_atoms;
     s = ensure_workspace(c, n);
     if (s != FLR_OK || n == 0) return s;
     const double ftm2v = 1.0 / 1.0364269e-4;   // (eV/A)/amu -> A/ps^2
+    const double kB = 8.617333262e-5;           // eV/K
     KickArgs kick;
     std::memset(&kick, 0, sizeof(kick));
     kick.vel = reinterpret_cast<float4 *>(md->vel);
@@ -941,32 +964,76 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
         kick.half_dt_over_m[sp] = (float)(0.5 * md->dt * ftm2v / md->masses[sp]);
         kick.half_m[sp] = (float)(0.5 * md->masses[sp] / ftm2v);
     }
+    // the thermostat reads the kinetic energy from the totals: use the
+    // context's own totals when the caller passes none
+    flr_outputs o = *out;
+    if (!o.totals) o.totals = c->md_totals;
+    double *tot = o.totals;
     float4 *pos = reinterpret_cast<float4 *>(md->pos);
     const float skin = (float)c->p.skin;
     const float disp2 = 0.25f * skin * skin;
+    const double gkT = 3.0 * n * kB * md->temperature;          // g kB T, g = 3n degrees of freedom
+    const double Q = gkT * md->tau * md->tau;                     // thermostat mass (eV ps^2)
     s = launch_clear_rebuild_counter(c, nl, st);
     if (s != FLR_OK) return s;
     if (!md->forces_valid) {
         KickArgs none;
         std::memset(&none, 0, sizeof(none));
-        s = evaluate(c, nl, pos, md->species, n, out, none, st);
+        s = evaluate(c, nl, pos, md->species, n, &o, none, st);
         if (s != FLR_OK) return s;
         md->forces_valid = 1;
     }
+    if (nvt) {
+        const double init[2] = {md->xi, md->eta};
+        s = cuda_fail(cudaMemcpyAsync(c->md_sc, init, sizeof(init), cudaMemcpyHostToDevice, st), "thermostat state");
+        if (s == FLR_OK) s = launch_kinetic(c, kick.vel, md->species, n, md->masses, c->md_sc + 8, c->md_sc + 2, st);
+        if (s != FLR_OK) return s;
+        kick.scale = c->md_sc + 3;
+    }
     kick.enabled = 1;
     for (int k = 0; k < n_steps; ++k) {
+        if (nvt) s = launch_thermo_half(c, c->md_sc, nullptr, gkT, Q, md->dt, nullptr, st);
         prof_begin(c, FLR_KERNEL_DRIFT, st);
-        s = launch_md_drift(c, nl, pos, kick.vel, out->forces, md->species, n, kick, (float)md->dt, disp2, st);
+        if (s == FLR_OK)
+            s = launch_md_drift(c, nl, pos, kick.vel, o.forces, md->species, n, kick, (float)md->dt, disp2, st);
         prof_end(c, FLR_KERNEL_DRIFT, st);
         if (s == FLR_OK && (md->step + 1) % md->rebuild_every == 0) s = launch_set_rebuild(c, nl, st);
         prof_begin(c, FLR_KERNEL_REBUILD, st);
         if (s == FLR_OK) s = launch_rebuild(c, nl, pos, md->species, n, st, true, pos);
         prof_end(c, FLR_KERNEL_REBUILD, st);
-        if (s == FLR_OK) s = evaluate(c, nl, pos, md->species, n, out, kick, st);
+        if (s == FLR_OK) s = evaluate(c, nl, pos, md->species, n, &o, kick, st);
+        if (s == FLR_OK && nvt) {
+            // second half step from the kinetic energy after the final kick
+            s = launch_thermo_half(c, c->md_sc, tot + FLR_TOT_KINETIC, gkT, Q, md->dt, tot, st);
+            if (s == FLR_OK) s = launch_scale_vel(c, kick.vel, n, c->md_sc + 3, st);
+        }
+        if (s == FLR_OK && cn)
+            s = launch_cn_count(c, nl, md->species, n, md->cn_species, (float)md->cn_cutoff, c->md_cnt + 1, tot, st);
         if (s != FLR_OK) return s;
         md->step += 1;
+        if (stop) {
+            s = launch_count_above(c, o.sigma, n, (float)md->sigma_stop, c->md_cnt, tot, st);
+            int cnt = 0;
+            if (s == FLR_OK) s = cuda_fail(cudaMemcpyAsync(&cnt, c->md_cnt, sizeof(int), cudaMemcpyDeviceToHost, st),
+                                           "uncertainty count");
+            if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "uncertainty count");
+            if (s != FLR_OK) return s;
+            if (cnt > 0) {
+                md->halted = 1;
+                break;
+            }
+        }
     }
-    if (out->totals) s = launch_copy_rebuilds(c, nl, out->totals, st);
+    s = launch_copy_rebuilds(c, nl, tot, st);
+    if (s == FLR_OK && nvt) {
+        double fin[2];
+        s = cuda_fail(cudaMemcpyAsync(fin, c->md_sc, sizeof(fin), cudaMemcpyDeviceToHost, st), "thermostat state");
+        if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "thermostat state");
+        if (s == FLR_OK) {
+            md->xi = fin[0];
+            md->eta = fin[1];
+        }
+    }
     return s;
 }
 

@@ -135,6 +135,9 @@ struct flr_ctx {
     float sigma_norm[flr::kGroups];    // largest eigenvalue of each group's Sigma block (power iteration)
     int32_t *ref_list;                 // [ws_n] atoms queued for the FP64 variance
     int *ref_count;                    // device counter of ref_list
+    double *md_sc;                     // MD scalars: [0] xi, [1] eta, [2] KE, [3] scale, [8..8+256) KE partials
+    double *md_totals;                 // totals of flr_md_step when the caller passes none
+    int *md_cnt;                       // [2] uncertainty and coordination counts
     float *W32[flr::kGroups];          // [nrows_pad][kp32]  B operand rows (beta rows, then Sigma rows)
     __nv_bfloat16 *Whi[flr::kGroups];  // [nrows_pad][kp64]
     __nv_bfloat16 *Wlo[flr::kGroups];
@@ -221,10 +224,22 @@ struct KickArgs {
     float half_dt_over_m[kSpecies];   // (dt/2) * FTM2V / m_s
     float half_m[kSpecies];            // m_s / 2 / FTM2V  (kinetic energy in eV from A/ps)
     int enabled;
+    const double *scale;               // thermostat velocity scale before the first kick (drift), or nullptr
 };
 int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick, float sign,
                     cudaStream_t st);
 int launch_dbeta(flr_ctx *ctx, const flr_nbrlist *nl, const float *u, float *grad_beta, cudaStream_t st);
+// MD extras (md.cu): kinetic energy, Nose-Hoover half step, velocity scaling,
+// uncertainty and coordination counts
+int launch_kinetic(flr_ctx *ctx, const float4 *vel, const int32_t *species, int n, const double *masses,
+                   double *part, double *ke, cudaStream_t st);
+int launch_thermo_half(flr_ctx *ctx, double *sc, const double *ke_in, double gkT, double Q, double dt, double *totals,
+                       cudaStream_t st);
+int launch_scale_vel(flr_ctx *ctx, float4 *vel, int n, const double *scale, cudaStream_t st);
+int launch_count_above(flr_ctx *ctx, const float *sigma, int n, float thr, int *count, double *totals,
+                       cudaStream_t st);
+int launch_cn_count(flr_ctx *ctx, const flr_nbrlist *nl, const int32_t *species, int n, int cs, float rc,
+                    int *count, double *totals, cudaStream_t st);
 // FP64 re-evaluation of the variance of the atoms the epilogue queued (FLR_VAR_AUTO)
 int launch_variance_fp64(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
 constexpr float kVarCancel = 32.f;   // queue an atom when V < (sum_k |d_k (Sigma d)_k|) / kVarCancel

@@ -229,7 +229,11 @@ class MDState:
     """Velocity-Verlet state: pos, vel [n, 4] float32 device tensors updated in place."""
 
     def __init__(self, system: System, vel: torch.Tensor, masses=(195.084, 1.008), dt=0.0005,
-                 rebuild_every=10):
+                 rebuild_every=10, temperature=0.0, tau=0.1, sigma_stop=0.0, cn_species=-1, cn_cutoff=1.0):
+        """temperature > 0: Nose-Hoover NVT with period tau (ps); sigma_stop > 0:
+        stop after the first step with an atom's sigma above it; cn_species >= 0:
+        count atoms of that species with a same-species neighbour within
+        cn_cutoff (A) after every step."""
         self.system = system
         self.vel = vel
         self.c = N.MDState()
@@ -246,10 +250,26 @@ class MDState:
         c.rebuild_every = rebuild_every
         c.forces_valid = 0
         c.step = 0
+        c.temperature = temperature
+        c.tau = tau
+        c.xi = 0.0
+        c.eta = 0.0
+        c.sigma_stop = sigma_stop
+        c.halted = 0
+        c.cn_species = cn_species
+        c.cn_cutoff = cn_cutoff
 
     @property
     def step(self):
         return int(self.c.step)
+
+    @property
+    def halted(self):
+        return bool(self.c.halted)
+
+    @property
+    def xi(self):
+        return float(self.c.xi)
 
 
 def md_step(ff: FlareGB, state: MDState, nl: NbrList, n_steps: int, out, stream=None):
@@ -316,7 +336,7 @@ def build_neighbors_batch(ff: FlareGB, batch: Batch, nl: NbrList, stream=None):
 
 
 def energy_forces_uncertainty_batch(ff: FlareGB, batch: Batch, nl: NbrList, out=None, stream=None):
-    """Per-atom outputs over the whole batch; out["totals"] is [n_structs, 16]."""
+    """Per-atom outputs over the whole batch; out["totals"] is [n_structs, NTOTALS]."""
     if out is None:
         out = make_outputs(batch.n_atoms)
         out["totals"] = torch.zeros((batch.n_structs, N.NTOTALS), dtype=torch.float64, device="cuda")

@@ -77,7 +77,7 @@ def test_batch_equals_each_structure_alone(precision):
     ff = F.FlareGB(precision=precision, max_nbr=96)
     ff.set_model(BETA, SIGMA)
     g, b = _run_batch(ff, structs)
-    assert g["totals"].shape == (len(structs), 16)
+    assert g["totals"].shape == (len(structs), 24)
     for k, s in enumerate(structs):
         lo, hi = int(b.offsets[k]), int(b.offsets[k + 1])
         a = _run_single(ff, s)

@@ -91,3 +91,75 @@ def test_nve_energy_error_scales_as_dt_squared():
     ke = 1.5 * s.n_atoms * synth.KB_EV * 300.0
     assert d2 < 0.05 * ke, (d2, ke)
     assert 2.5 <= d2 / d1 <= 6.5, (d2, d1)
+
+
+def _temperature(ke, n):
+    return 2.0 * ke / (3.0 * n * synth.KB_EV)
+
+
+def test_nose_hoover_reaches_and_holds_the_target_temperature():
+    """NVT at 450 K from 300 K Maxwell velocities (64 Pt atoms, dt = 1 fs,
+    tau = 50 fs): the mean temperature of the second half of 1200 steps is
+    within 8 % of the target, and E_pot + KE + thermostat energy is conserved."""
+    from paper_2204_12573_gb300 import flare as F
+    s = _pt_slab()
+    ff, sysg, vel, nl, _ = _setup(s, 0.001)
+    st = F.MDState(sysg, vel, dt=0.001, rebuild_every=10, temperature=450.0, tau=0.05)
+    out = F.make_outputs(s.n_atoms)
+    temps, cons = [], []
+    for _ in range(120):
+        F.md_step(ff, st, nl, 10, out)
+        t = out["totals"].cpu().numpy()
+        temps.append(_temperature(t[12], s.n_atoms))
+        cons.append(t[0] + t[12] + t[17])
+    ff.sync()
+    assert st.step == 1200
+    t_mean = float(np.mean(temps[60:]))
+    assert abs(t_mean - 450.0) <= 0.08 * 450.0, t_mean
+    ke_scale = 1.5 * s.n_atoms * synth.KB_EV * 450.0
+    assert abs(cons[-1] - cons[0]) <= 0.02 * ke_scale, (cons[0], cons[-1])
+    assert st.xi != 0.0
+
+
+def test_uncertainty_stop():
+    """sigma_stop below the largest sigma halts after the first step; above it
+    every step runs."""
+    from paper_2204_12573_gb300 import flare as F
+    s = synth.tiny_system(0)
+    ff, sysg, vel, nl, _ = _setup(s, 0.0005)
+    sig = F.energy_forces_uncertainty(ff, sysg, nl)["sigma"].cpu().numpy()
+    st = F.MDState(sysg, vel, dt=0.0005, sigma_stop=0.5 * float(sig.max()))
+    out = F.make_outputs(s.n_atoms)
+    F.md_step(ff, st, nl, 5, out)
+    assert st.halted and st.step == 1
+    assert out["totals"][15].item() >= 1
+    st2 = F.MDState(sysg, vel, dt=0.0005, sigma_stop=10.0 * float(sig.max()))
+    F.md_step(ff, st2, nl, 5, out)
+    assert not st2.halted and st2.step == 5
+    assert out["totals"][15].item() == 0
+
+
+def test_coordination_count_of_h2():
+    """Same-species coordination of H within 1 A counts the atoms of intact H2
+    molecules, checked against a minimum-image count on the host."""
+    from paper_2204_12573_gb300 import flare as F
+    s = synth.tiny_system(0)
+    ff, sysg, vel, nl, _ = _setup(s, 0.0005)
+    for cut in (1.0, 0.5):
+        st = F.MDState(sysg, vel, dt=0.0005, cn_species=1, cn_cutoff=cut)
+        out = F.make_outputs(s.n_atoms)
+        F.md_step(ff, st, nl, 2, out)
+        ff.sync()
+        p = sysg.pos[:, :3].double().cpu().numpy()
+        h = np.nonzero(s.species == 1)[0]
+        inv = np.linalg.inv(s.cell)
+        cnt = 0
+        for a in h:
+            dr = p[h] - p[a]
+            f = dr @ inv
+            f[:, :2] -= np.round(f[:, :2])
+            dist = np.linalg.norm(f @ s.cell, axis=1)
+            dist[h == a] = 1e9
+            cnt += int((dist < cut).any())
+        assert out["totals"][16].item() == cnt
+    assert cnt == 0                      # no H pair closer than 0.5 A
