@@ -41,7 +41,10 @@ constexpr int kTileA = BM * 128;   // bytes (128-byte rows)
 constexpr int kTileB = NC * 128;
 constexpr int kStageBytes = kTileA + kTileB;
 constexpr int kTmemCols = 512;
-constexpr int kEpiWarps = 8;        // two per TMEM lane quarter, alternating 16-column groups
+constexpr int kSubs = 3;            // epilogue warps per TMEM lane quarter (each takes every 3rd 16-column group)
+constexpr int kParkCols = 144;      // widest one-species row parked in shared memory
+constexpr int kParkStride = kParkCols + 4;
+constexpr int kEpiWarps = 4 * kSubs;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr unsigned long long kDeadlineNs = 2000000000ull;
 
@@ -204,9 +207,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
     // bars: full[kStages], empty[kStages], tfull, tempty, drain, evx
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
-    // partial (E, V, sum |d_k (Sigma d)_k|) of each row from the two column
-    // halves, double-buffered by tile
+    // partial (E, V, sum |d_k (Sigma d)_k|) of each row from the kSubs column
+    // sets, double-buffered by tile
     float4 *evx_buf = reinterpret_cast<float4 *>(base + kStages * kStageBytes + 128);
+    // beta d of one-species tiles, parked until E is known (padded rows: conflict-free float4 access)
+    float *park = reinterpret_cast<float *>(base + kStages * kStageBytes + 128 + 2 * kSubs * BM * sizeof(float4));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
@@ -335,14 +340,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
         }
     } else {
         // ---------------- epilogue: TMEM -> E, V, sigma, g ----------------
-        // Warp (quarter qw, half sub) reads TMEM lanes 32 qw .. 32 qw + 31 (one
-        // row per thread) and the 16-column groups whose index has parity sub.
-        // The two halves of a row exchange their partial E and V through shared
+        // Warp (quarter qw, set sub) reads TMEM lanes 32 qw .. 32 qw + 31 (one
+        // row per thread) and every kSubs-th 16-column group starting at sub.
+        // The kSubs partial E and V of a row are combined through shared
         // memory (double-buffered by tile, guarded by a bounded mbarrier wait).
+        // One-species tiles park beta d in shared memory, so the accumulator is
+        // released as soon as it is read and g = s2 (beta d - E d) is formed
+        // without a round trip through global memory; two-species tiles (four
+        // column chunks) park beta d in the g row and fix it up afterwards.
         const int qw = warp & 3;                // TMEM lane quarter of this warp
-        const int sub = (warp - 2) >> 2;        // which alternate 16-column groups
+        const int sub = (warp - 2) >> 2;        // which column groups
         const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
         const int rloc = qw * 32 + lane;        // row within the tile
+        float *prow = park + (size_t)rloc * kParkStride;
         int it = 0;
         int tl = 0;                             // tiles done by this CTA
         bool alive = true;
@@ -357,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             float *grow = a.G[ti.reg] + (size_t)(valid ? row : 0) * K;
             const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
             const bool fact = a.var_factored[ti.g] != 0;
+            const bool in_smem = ti.nch == 1 && (K % 16) == 0 && 2 * K <= NC && K <= kParkCols;
             float E = 0.f, V = 0.f, Va = 0.f;
             for (int ch = 0; ch < ti.nch; ++ch, ++it) {
                 // lane 0 waits and the warp follows its verdict, so the warp stays converged
@@ -372,37 +383,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     break;
                 }
                 fence_after();
-                if (ti.nch == 1 && (K % 16) == 0 && 2 * K <= NC) {
-                    // one chunk holding [beta d | Sigma d]: read both halves together,
-                    // one load of d serves E and V; beta d is parked in the g row
+                if (in_smem) {
+                    // one chunk holding [beta d | Sigma d]
 #pragma unroll 1
-                    for (int c = 16 * sub; c < K; c += 32) {
+                    for (int c = 16 * sub; c < K; c += 16 * kSubs) {
                         float dv[16], vb[16], vs[16];
                         if (valid) load16(d + c, dv);
                         tmem_ld16(tbase + (uint32_t)c, vb);
                         tmem_ld16(tbase + (uint32_t)(K + c), vs);
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4)
+                            *reinterpret_cast<float4 *>(prow + c + k) = make_float4(vb[k], vb[k + 1], vb[k + 2], vb[k + 3]);
                         if (valid) {
 #pragma unroll
                             for (int k = 0; k < 16; ++k) {
                                 E += dv[k] * vb[k];
-                                const float t = (fact ? vs[k] : dv[k]) * vs[k];
-                                V += t;
-                                Va += fabsf(t);
+                                const float tq = (fact ? vs[k] : dv[k]) * vs[k];
+                                V += tq;
+                                Va += fabsf(tq);
                             }
-#pragma unroll
-                            for (int k = 0; k < 16; k += 4)
-                                *reinterpret_cast<float4 *>(grow + c + k) = make_float4(vb[k], vb[k + 1], vb[k + 2], vb[k + 3]);
                         }
                     }
                 } else {
                     const int c0 = ch * NC;
 #pragma unroll 1
-                    for (int c = 16 * sub; c < NC; c += 32) {
+                    for (int c = 16 * sub; c < NC; c += 16 * kSubs) {
                         const int cg = c0 + c;
                         float v[16], dv[16];
                         const bool beta_cols = cg + 16 <= K, sigma_cols = cg >= K && cg + 16 <= 2 * K;
                         if (valid && beta_cols) load16(d + cg, dv);
-                        else if (valid && sigma_cols) load16(d + cg - K, dv);
+                        else if (valid && sigma_cols && !fact) load16(d + cg - K, dv);
                         tmem_ld16(tbase + (uint32_t)c, v);
                         if (valid && cg < 2 * K) {
                             if (beta_cols) {
@@ -414,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                             } else if (sigma_cols) {
 #pragma unroll
                                 for (int k = 0; k < 16; ++k) {
-                                    const float t = (fact ? v[k] : dv[k]) * v[k];
-                                    V += t;
-                                    Va += fabsf(t);
+                                    const float tq = (fact ? v[k] : dv[k]) * v[k];
+                                    V += tq;
+                                    Va += fabsf(tq);
                                 }
                             } else {                                  // a group straddling K or 2K
 #pragma unroll
@@ -426,9 +436,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                                         E += __ldg(d + cc) * v[k];
                                         grow[cc] = v[k];
                                     } else if (cc < 2 * K) {
-                                        const float t = (fact ? v[k] : __ldg(d + cc - K)) * v[k];
-                                        V += t;
-                                        Va += fabsf(t);
+                                        const float tq = (fact ? v[k] : __ldg(d + cc - K)) * v[k];
+                                        V += tq;
+                                        Va += fabsf(tq);
                                     }
                                 }
                             }
@@ -442,9 +452,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             }
             if (!alive) break;
             // While the MMAs of the next tile run, pull this thread's descriptor
-            // row of that tile towards the SM (into L1 for one-species rows,
-            // which fit, into L2 for two-species rows), so the accumulator
-            // read-back of the next tile does not wait on memory.
+            // row of that tile into L2, so the accumulator read-back of the next
+            // tile does not wait on DRAM.
             {
                 const int tn = t + gridDim.x;
                 if (tn < total) {
@@ -453,18 +462,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     if (rown < tj.rend) {
                         const char *dn = reinterpret_cast<const char *>(a.D32[tj.reg] + (size_t)rown * a.kp32[tj.reg]);
                         const int bytes = 4 * a.K[tj.reg];
-                        if (tj.reg == 1) {
-                            for (int o = 128 * sub; o < bytes; o += 256)
-                                asm volatile("prefetch.global.L1 [%0];" ::"l"(dn + o));
-                        } else {
-                            for (int o = 128 * sub; o < bytes; o += 256)
-                                asm volatile("prefetch.global.L2 [%0];" ::"l"(dn + o));
-                        }
+                        for (int o = 128 * sub; o < bytes; o += 128 * kSubs)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(dn + o));
                     }
                 }
             }
-            // combine the two halves' partial sums (fixed order: half 0 + half 1)
-            float4 *xb = evx_buf + (tl & 1) * (2 * BM);
+            // combine the partial sums of the kSubs column sets (fixed order)
+            float4 *xb = evx_buf + (tl & 1) * (kSubs * BM);
             xb[sub * BM + rloc] = make_float4(E, V, Va, 0.f);
             __syncwarp();
             int okx = 1;
@@ -482,29 +486,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 alive = false;
                 break;
             }
-            const float4 p0 = xb[rloc], p1 = xb[BM + rloc];
-            E = p0.x + p1.x;
-            V = p0.y + p1.y;
-            Va = p0.z + p1.z;
+            E = 0.f;
+            V = 0.f;
+            Va = 0.f;
+#pragma unroll
+            for (int q = 0; q < kSubs; ++q) {
+                const float4 p = xb[q * BM + rloc];
+                E += p.x;
+                V += p.y;
+                Va += p.z;
+            }
             if (valid) {
-                // g = (2/||B||)(beta d - E d) over the 16-column groups this half parked
-                float4 *g4 = reinterpret_cast<float4 *>(grow);
-                const float4 *d4 = reinterpret_cast<const float4 *>(d);
-                const int nk = K / 4;
+                if (in_smem) {
+                    // g = (2/||B||)(beta d - E d) from the parked beta d
 #pragma unroll 1
-                for (int k0 = 4 * sub; k0 < nk; k0 += 8) {
-                    float4 p[4], q[4];
+                    for (int c = 16 * sub; c < K; c += 16 * kSubs) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (k0 + u < nk) {
-                            p[u] = g4[k0 + u];
-                            q[u] = __ldg(d4 + k0 + u);
+                        for (int k = 0; k < 16; k += 4) {
+                            const float4 p = *reinterpret_cast<const float4 *>(prow + c + k);
+                            const float4 q = __ldg(reinterpret_cast<const float4 *>(d + c + k));
+                            *reinterpret_cast<float4 *>(grow + c + k) =
+                                make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
+                                            s2 * (p.w - E * q.w));
                         }
+                    }
+                } else {
+                    // g = (2/||B||)(beta d - E d) over the 16-column groups this set parked
+                    float4 *g4 = reinterpret_cast<float4 *>(grow);
+                    const float4 *d4 = reinterpret_cast<const float4 *>(d);
+                    const int nk = K / 4;
+#pragma unroll 1
+                    for (int k0 = 4 * sub; k0 < nk; k0 += 4 * kSubs) {
+                        float4 p[4], q[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (k0 + u < nk)
-                            g4[k0 + u] = make_float4(s2 * (p[u].x - E * q[u].x), s2 * (p[u].y - E * q[u].y),
-                                                     s2 * (p[u].z - E * q[u].z), s2 * (p[u].w - E * q[u].w));
+                        for (int u = 0; u < 4; ++u)
+                            if (k0 + u < nk) {
+                                p[u] = g4[k0 + u];
+                                q[u] = __ldg(d4 + k0 + u);
+                            }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (k0 + u < nk)
+                                g4[k0 + u] = make_float4(s2 * (p[u].x - E * q[u].x), s2 * (p[u].y - E * q[u].y),
+                                                         s2 * (p[u].z - E * q[u].z), s2 * (p[u].w - E * q[u].w));
+                    }
                 }
                 if (sub == 0) {
                     a.energy[atom] = E;
@@ -632,10 +657,11 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaS
     a.ref_count = ctx->ref_count;
     a.ref_cap = ctx->ws_n;
     a.status = ctx->status;
-    // ring + barriers (128 B) + the E / V exchange (2 tiles x 2 halves x BM float4),
-    // and at least 116 KB so that one CTA (holding all 512 TMEM columns) runs per SM
-    const size_t smem = std::max<size_t>(1024 + (size_t)kStages * kStageBytes + 128 + 2 * 2 * BM * sizeof(float4),
-                                         116 * 1024);
+    // ring + barriers (128 B) + the E / V exchange (2 tiles x kSubs sets x BM float4)
+    // + the parked beta d rows; more than half of the SM's shared memory, so one CTA
+    // (holding all 512 TMEM columns) runs per SM
+    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 128 + 2 * kSubs * BM * sizeof(float4) +
+                        (size_t)BM * kParkStride * sizeof(float);
     cudaError_t e;
     if (bf16) {
         e = cudaFuncSetAttribute(k_qform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
