@@ -110,6 +110,14 @@ __device__ __forceinline__ void ylm_one(int lm, float x, float y, float z, float
     }
 }
 
+// Whether component c (x, y, z) of grad P_lm is not identically zero (lm and
+// c compile-time constants after unrolling, so the test folds away).
+__host__ __device__ constexpr bool grad_nz(int lm, int c)
+{
+    // bit lm of each mask: x: 3,4,6-15; y: 1,4,5,6,8-15; z: 2,5,6,7,10-14
+    return ((c == 0 ? 0xFFD8u : (c == 1 ? 0xFF72u : 0x7CE4u)) >> lm) & 1u;
+}
+
 // l of harmonic index lm
 __host__ __device__ constexpr int l_of(int lm) { return lm < 1 ? 0 : (lm < 4 ? 1 : (lm < 9 ? 2 : 3)); }
 

@@ -77,6 +77,8 @@ struct ForceSmem {
     int atom[kWarpsForce][kSlots];
     int qseq[kWarpsForce][64];                  // atom sequence number of each queued pair
     float vir[kWarpsForce][9];
+    int2 goff[(2 * N) * (2 * N + 1) / 2 + N * (N + 1) / 2];   // G~ offsets (b a, a b) of each compact pair:
+                                                             // two-species layout, then one-species
 };
 
 // |v| must stay below 2^15 eV/A (else the status word reports a non-finite
@@ -114,7 +116,8 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
         const float xx = ux * ux, yy = uy * uy, zz = uz * uz;
         // f = u (sum_lm c'_lm Y_lm - (1/r) sum_lm l c_lm Y_lm) + (1/r) sum_lm c_lm grad P_lm(u),
         // c_lm = sum_n w_{n,lm} R_n f_c,  c'_lm = sum_n w_{n,lm} (R_n f_c)'
-        float radial_part = 0.f, lsum = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        float radial_part = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        float ls[4] = {0.f, 0.f, 0.f, 0.f};   // sum of c Y per l
 #pragma unroll
         for (int lm = 0; lm < 16; ++lm) {
             const float4 w0 = *reinterpret_cast<const float4 *>(wp + lm * 8);
@@ -129,11 +132,13 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
             float Y, dx, dy, dz;
             ylm_one(lm, ux, uy, uz, xx, yy, zz, Y, dx, dy, dz);
             radial_part += cp * Y;
-            lsum += (float)l_of(lm) * c * Y;
-            gx += c * dx;
-            gy += c * dy;
-            gz += c * dz;
+            if (l_of(lm) > 0) ls[l_of(lm)] += c * Y;
+            // only the components of grad P_lm that are not identically zero
+            if (grad_nz(lm, 0)) gx += c * dx;
+            if (grad_nz(lm, 1)) gy += c * dy;
+            if (grad_nz(lm, 2)) gz += c * dz;
         }
+        const float lsum = ls[1] + 2.f * ls[2] + 3.f * ls[3];
         const float coef = radial_part - lsum * inv;
         const float fx = coef * ux + gx * inv;
         const float fy = coef * uy + gy * inv;
@@ -345,7 +350,19 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0;
     for (int k = lane; k < 9 * kSlots; k += 32) sm.V[w][k / 9][k % 9] = 0;
     const bool want_vatom = a.vir_atom != nullptr;
-    __syncwarp();
+    {
+        // where each compact channel pair (a, b) of g lands in the dense G~ of
+        // its class: offsets of (b, a) and (a, b); equal on the diagonal
+        constexpr int NPF = C * (C + 1) / 2, NPS = N * (N + 1) / 2;
+        for (int t = threadIdx.x; t < NPF + NPS; t += blockDim.x) {
+            const bool full = t < NPF;
+            const int e = __ldg(full ? a.tab[0] + 4 * t : a.tab[1] + 4 * (t - NPF));
+            const int ca = e & 255, cb = (e >> 8) & 255;
+            const int RS = full ? gd_row(C) : gd_row(N);
+            sm.goff[t] = make_int2(cb * RS + ca, ca * RS + cb);
+        }
+    }
+    __syncthreads();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
     // each CTA walks one contiguous block of atoms, its warps interleaved
@@ -390,21 +407,19 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         // dense symmetric G~[l][b][a] with the diagonal doubled
         {
             const float4 *g4 = reinterpret_cast<const float4 *>(sm.gr[w]);
-            const int32_t *tab = a.tab[reg];
+            const int2 *goff = sm.goff + (reg == 0 ? 0 : C * (C + 1) / 2);
             const float u = a.weight ? __ldg(a.weight + i) : 1.f;
-            const int RS = cls == 0 ? gd_row(C) : gd_row(N);
             const int LS = cls == 0 ? gd_plane(C) : gd_plane(N);
             float *sGd = sm.Gd[w];
             for (int t = lane; 4 * t < K; t += 32) {
-                const int e = __ldg(tab + 4 * t);
-                const int ca = e & 255, cb = (e >> 8) & 255;
+                const int2 of = goff[t];
+                const int o1 = of.x, o2 = of.y;
                 float4 v = g4[t];
-                const float sc = ca == cb ? 2.f * u : u;
+                const float sc = o1 == o2 ? 2.f * u : u;   // the diagonal of G~ is doubled
                 v.x *= sc;
                 v.y *= sc;
                 v.z *= sc;
                 v.w *= sc;
-                const int o1 = cb * RS + ca, o2 = ca * RS + cb;
                 sGd[o1] = v.x;
                 sGd[o2] = v.x;
                 sGd[LS + o1] = v.y;
