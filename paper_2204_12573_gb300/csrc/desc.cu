@@ -38,22 +38,47 @@ struct DescArgs {
     int32_t *pair_cnt;         // [n] out: their number
 };
 
+constexpr int kYStride = 20;   // padded row of staged harmonics (conflict-free float4 stores)
+
+// Per warp, the staged basis of a batch of pairs and, once the pairs are
+// done, the rows of A and the unnormalized B2 (kept here between the norm
+// reduction and the scaled stores instead of in registers) share one region.
+template <int N>
+union __align__(16) DescStage {
+    struct {
+        float Y[32][kYStride];           // harmonics of up to 32 staged pairs
+        float Rf[N][33];                 // their radial values, pair index fastest
+    } p;
+    struct {
+        float A[2 * N * kAStride];
+        float4 B[(2 * N) * (2 * N + 1) / 2];   // unnormalized B2 of the class's channel pairs
+    } b;
+};
+
 template <int N>
 struct DescSmem {
     float4 rec[kWarpsDesc][64];          // compacted pairs inside r_cut: r_ij, species of j
-    float Rf[kWarpsDesc][32][N];         // staged radial values of up to 32 pairs
-    float Y[kWarpsDesc][32][16];         // staged harmonics
-    float A[kWarpsDesc][2 * N * kAStride];
+    DescStage<N> st[kWarpsDesc];
 };
 
 // Basis of up to 32 staged pairs (lane p evaluates pair p), then the lanes
-// that own A coefficients accumulate over them.
+// that own A coefficients accumulate over them.  The basis is stored with the
+// pairs of a species-0 neighbour first (each species keeps list order, so
+// every accumulator sums in the same order as an unsorted pass), so the
+// accumulation picks the accumulator by a warp-uniform index test instead of
+// loading each pair's species.
 template <int N>
 __device__ __forceinline__ void desc_batch(DescSmem<N> &sm, int w, int lane, int m, float rc, float acc0[4],
                                            float acc1[4])
 {
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < m) r = sm.rec[w][lane];
+    const bool s1 = lane < m && __float_as_int(r.w) != 0;
+    const unsigned b1 = __ballot_sync(0xffffffffu, s1);
+    const int n0 = m - __popc(b1);
     if (lane < m) {
-        const float4 r = sm.rec[w][lane];
+        const int below1 = __popc(b1 & ((1u << lane) - 1u));
+        const int slot = s1 ? n0 + below1 : lane - below1;
         const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
         const float rr = sqrtf(d2), inv = 1.f / rr;
         float Rf[N], dummy[N];
@@ -61,19 +86,19 @@ __device__ __forceinline__ void desc_batch(DescSmem<N> &sm, int w, int lane, int
         float Y[16];
         real_ylm(r.x * inv, r.y * inv, r.z * inv, Y);
 #pragma unroll
-        for (int n = 0; n < N; ++n) sm.Rf[w][lane][n] = Rf[n];
+        for (int n = 0; n < N; ++n) sm.st[w].p.Rf[n][slot] = Rf[n];
 #pragma unroll
         for (int k = 0; k < 16; k += 4)
-            *reinterpret_cast<float4 *>(&sm.Y[w][lane][k]) = make_float4(Y[k], Y[k + 1], Y[k + 2], Y[k + 3]);
+            *reinterpret_cast<float4 *>(&sm.st[w].p.Y[slot][k]) = make_float4(Y[k], Y[k + 1], Y[k + 2], Y[k + 3]);
     }
     __syncwarp();
     const int my_n = lane >> 2, quad = lane & 3;
     if (my_n < N) {
 #pragma unroll 4
         for (int p = 0; p < m; ++p) {
-            const float rf = sm.Rf[w][p][my_n];
-            const float4 y = *reinterpret_cast<const float4 *>(&sm.Y[w][p][4 * quad]);
-            if (__float_as_int(sm.rec[w][p].w) == 0) {
+            const float rf = sm.st[w].p.Rf[my_n][p];
+            const float4 y = *reinterpret_cast<const float4 *>(&sm.st[w].p.Y[p][4 * quad]);
+            if (p < n0) {   // warp-uniform
                 acc0[0] += rf * y.x; acc0[1] += rf * y.y; acc0[2] += rf * y.z; acc0[3] += rf * y.w;
             } else {
                 acc1[0] += rf * y.x; acc1[1] += rf * y.y; acc1[2] += rf * y.z; acc1[3] += rf * y.w;
@@ -201,7 +226,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         if (lane == 0) a.pair_cnt[i] = np;
 
         // A to shared memory (padded rows) and to global memory (blocks in use only)
-        float *sA = sm.A[w];
+        float *sA = sm.st[w].b.A;   // the staging area is free once the pairs are done
         const int my_n = lane >> 2, quad = lane & 3;
         if (my_n < N) {
             *reinterpret_cast<float4 *>(sA + my_n * kAStride + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
@@ -220,16 +245,16 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         const int npairs = cls == 0 ? NPF : NPS;
         const int choff = cls == 0 ? 0 : (cls - 1) * N;
         const int32_t *tab = a.tab[reg];
-        float4 b[MAXP];
+        float4 *sB = sm.st[w].b.B;
         float ss = 0.f;
 #pragma unroll
         for (int k = 0; k < MAXP; ++k) {
             const int t = lane + 32 * k;
-            b[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (t < npairs) {
                 const int e = __ldg(tab + 4 * t);
-                b[k] = b2_pair(sA, choff + (e & 255), choff + ((e >> 8) & 255));
-                ss += b[k].x * b[k].x + b[k].y * b[k].y + b[k].z * b[k].z + b[k].w * b[k].w;
+                const float4 bb = b2_pair(sA, choff + (e & 255), choff + ((e >> 8) & 255));
+                sB[t] = bb;
+                ss += bb.x * bb.x + bb.y * bb.y + bb.z * bb.z + bb.w * bb.w;
             }
         }
 #pragma unroll
@@ -247,20 +272,19 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         for (int k = 0; k < MAXP; ++k) {
             const int t = lane + 32 * k;
             if (t < npairs) {
-                const float4 v = make_float4(b[k].x * inv, b[k].y * inv, b[k].z * inv, b[k].w * inv);
+                const float4 bb = sB[t];
+                const float4 v = make_float4(bb.x * inv, bb.y * inv, bb.z * inv, bb.w * inv);
                 *reinterpret_cast<float4 *>(d32 + 4 * t) = v;
                 if (dh) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
-                    const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
-                    __nv_bfloat162 hi01, hi23, lo01, lo23;
-                    hi01.x = h0; hi01.y = h1; hi23.x = h2; hi23.y = h3;
-                    lo01.x = __float2bfloat16_rn(v.x - __bfloat162float(h0));
-                    lo01.y = __float2bfloat16_rn(v.y - __bfloat162float(h1));
-                    lo23.x = __float2bfloat16_rn(v.z - __bfloat162float(h2));
-                    lo23.y = __float2bfloat16_rn(v.w - __bfloat162float(h3));
+                    // hi = RN(v), lo = RN(v - hi), two values per conversion
+                    const __nv_bfloat162 hi01 = __floats2bfloat162_rn(v.x, v.y);
+                    const __nv_bfloat162 hi23 = __floats2bfloat162_rn(v.z, v.w);
+                    const float2 f01 = __bfloat1622float2(hi01), f23 = __bfloat1622float2(hi23);
+                    const __nv_bfloat162 lo01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+                    const __nv_bfloat162 lo23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
                     uint2 hv, lv;
-                    hv.x = *reinterpret_cast<uint32_t *>(&hi01); hv.y = *reinterpret_cast<uint32_t *>(&hi23);
-                    lv.x = *reinterpret_cast<uint32_t *>(&lo01); lv.y = *reinterpret_cast<uint32_t *>(&lo23);
+                    hv.x = *reinterpret_cast<const uint32_t *>(&hi01); hv.y = *reinterpret_cast<const uint32_t *>(&hi23);
+                    lv.x = *reinterpret_cast<const uint32_t *>(&lo01); lv.y = *reinterpret_cast<const uint32_t *>(&lo23);
                     *reinterpret_cast<uint2 *>(dh + 4 * t) = hv;
                     *reinterpret_cast<uint2 *>(dl + 4 * t) = lv;
                 }
