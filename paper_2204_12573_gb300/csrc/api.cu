@@ -743,7 +743,7 @@ int flr_nbrlist_destroy(flr_nbrlist *nl)
     cudaFree(nl->pair_rec);
     cudaFree(nl->pair_cnt);
     cudaFree(nl->offsets_d);
-    cudaFree(nl->cells_d);
+    cudaFree(nl->shift_d);
     cudaFree(nl->plans_d);
     delete[] nl->plans_h;
     delete[] nl->offsets_h;

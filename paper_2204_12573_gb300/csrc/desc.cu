@@ -25,7 +25,7 @@ struct DescArgs {
     const int32_t *species;
     const int32_t *entries, *count, *group, *row;
     int max_nbr, n;
-    Cells cells;               // per-structure lattice vectors
+    Cells cells;               // per-structure image shifts
     float rcut;
     const int32_t *tab[2];     // compact index -> (a, b, l)
     int K[2], kp32[2], kp64[2];
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         const int cls = group_cls(g);
         const int reg = group_region(g);
         const float4 pi = cur.pi;
-        const double *cl = a.cells.of(i);
+        const float4 *shift = a.cells.of(i);
         const int cnt = cur.cnt;
         const int32_t *rowp = a.entries + (size_t)i * a.max_nbr;
 
@@ -197,12 +197,11 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
             float3 r = make_float3(0.f, 0.f, 0.f);
             int sj = 0, j = 0;
             if (q < cnt) {
-                int sx, sy, sz;
                 const int e = base == 0 ? cur.e0 : (base == 32 ? cur.e1 : __ldg(rowp + q));
-                decode_entry(e, j, sx, sy, sz);
+                j = entry_atom(e);
                 const float4 pj = __ldg(a.pos + j);
                 sj = entry_species(e);   // the list carries the neighbour's species: no gather
-                r = pair_vector(pi, pj, sx, sy, sz, cl);
+                r = pair_vector(pi, pj, entry_code(e), shift);
                 ok = r.x * r.x + r.y * r.y + r.z * r.z < rc2;
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -342,7 +341,7 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.row = nl->row;
     a.max_nbr = nl->max_nbr;
     a.n = n;
-    a.cells.cells = nl->cells_d;
+    a.cells.shift = nl->shift_d;
     a.cells.struct_of = nl->n_structs > 1 ? nl->struct_of : nullptr;
     a.rcut = (float)ctx->p.r_cut;
     a.tab[0] = ctx->tab_full;

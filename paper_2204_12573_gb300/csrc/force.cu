@@ -42,7 +42,6 @@ struct ForceArgs {
     const int32_t *species;
     const int32_t *entries, *count, *group, *row;
     int max_nbr, n;
-    Cells cells;               // per-structure lattice vectors
     float rcut;
     int K[2];
     const float *G[2];         // g = dE/dB rows from the quadratic-form epilogue
@@ -503,9 +502,11 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
     int iso = 0;
     for (int i = blockIdx.x * 256 + threadIdx.x; i < a.n; i += gridDim.x * 256) {
         float f[3];
+        // RN(x) * 2^-32 is exact scaling of the correctly rounded integer, so
+        // this equals RN(x * 2^-32) without FP64 arithmetic
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            f[c] = a.sign * (float)((double)(long long)a.Facc[3 * (size_t)i + c] * (1.0 / 4294967296.0));
+            f[c] = a.sign * (__ll2float_rn((long long)a.Facc[3 * (size_t)i + c]) * 0x1p-32f);
         a.forces[3 * (size_t)i + 0] = f[0];
         a.forces[3 * (size_t)i + 1] = f[1];
         a.forces[3 * (size_t)i + 2] = f[2];
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a)
             v.y += h * f[1];
             v.z += h * f[2];
             a.kick.vel[i] = v;
-            ke += (double)a.kick.half_m[s] * (double)(v.x * v.x + v.y * v.y + v.z * v.z);
+            ke += (double)(a.kick.half_m[s] * (v.x * v.x + v.y * v.y + v.z * v.z));
         }
     }
     for (int o = 16; o; o >>= 1) {
@@ -695,8 +696,6 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.row = nl->row;
     a.max_nbr = nl->max_nbr;
     a.n = n;
-    a.cells.cells = nl->cells_d;
-    a.cells.struct_of = nl->n_structs > 1 ? nl->struct_of : nullptr;
     a.rcut = (float)ctx->p.r_cut;
     for (int r = 0; r < 2; ++r) {
         a.K[r] = ctx->dims.K[r];

@@ -63,6 +63,7 @@ struct Plan {
     float fspan[3];     // fractional span of the bin grid (1 along periodic dirs)
     double cell[9];
     double inv[9];      // inverse of the cell matrix (frac = pos . inv)
+    float invf[9];      // inv rounded to FP32 (the in-bin offsets used to prune the stencil)
     int pbc[3];
     long long nbins;
     long long bin_base; // first global bin of this structure in a batch
@@ -104,7 +105,7 @@ struct flr_nbrlist {
     int structs_cap;
     int32_t *struct_of;    // device [n_cap] structure of each atom (nullptr when n_structs == 1)
     int32_t *offsets_d;    // device [structs_cap + 1]
-    double *cells_d;       // device [structs_cap][9]
+    float4 *shift_d;       // device [structs_cap][125][2] image shifts S.cell, FP32 hi and lo
     flr::Plan *plans_d;    // device [structs_cap]
     flr::Plan *plans_h;    // host  [structs_cap]
     int32_t *offsets_h;    // host  [structs_cap + 1]
@@ -271,50 +272,49 @@ constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
 // Decode a neighbour entry: (j << 8) | (s_j << 7) | code,
 // code = (sx+2)*25 + (sy+2)*5 + (sz+2); s_j is the species of j (0 or 1).
 __device__ __forceinline__ int entry_species(int e) { return (e >> 7) & 1; }
-__device__ __forceinline__ void decode_entry(int e, int &j, int &sx, int &sy, int &sz)
-{
-    j = (int)((unsigned)e >> 8);
-    int code = e & 127;
-    sx = code / 25 - 2;
-    sy = (code / 5) % 5 - 2;
-    sz = code % 5 - 2;
-}
+__device__ __forceinline__ int entry_atom(int e) { return (int)((unsigned)e >> 8); }
+__device__ __forceinline__ int entry_code(int e) { return e & 127; }
 constexpr int kCenterCode = 62;   // (0, 0, 0)
 
-// Cell passed by value to kernels (rows = lattice vectors).
-struct CellArg {
-    double c[9];
-};
+constexpr int kShiftCodes = 125;  // image codes (sx, sy, sz) in [-2, 2]^3
 
-// Lattice vectors of the structure atom i belongs to: per-structure cells
-// live in device memory (rows = lattice vectors, 9 doubles each).
+// Image shifts S.cell of the structure atom i belongs to: per structure and
+// code, the FP64 shift split into FP32 hi and lo parts (two float4, .w unused),
+// formed on the host from the cell rows (the lattice vectors).
 struct Cells {
-    const double *cells;       // [n_structs][9]
+    const float4 *shift;       // [n_structs][kShiftCodes][2]
     const int32_t *struct_of;  // [n] or nullptr (one structure)
-    __device__ __forceinline__ const double *of(int i) const
+    __device__ __forceinline__ const float4 *of(int i) const
     {
-        return cells + 9 * (struct_of ? __ldg(struct_of + i) : 0);
+        return shift + 2 * kShiftCodes * (struct_of ? __ldg(struct_of + i) : 0);
     }
 };
 
-// Pair vector r_ij = r_j + S.cell - r_i in FP32.  Without an image shift the
-// FP32 difference is correctly rounded; with one, the sum is formed in FP64
-// from the exact FP32 inputs so large coordinates lose no accuracy.
-__device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, int sx, int sy,
-                                              int sz, const double *c)
+// x_j - x_i + (th + tl) for one coordinate, in FP32 only: TwoSum (Knuth)
+// gives x_j - x_i = s + e and s + th = u + f exactly, then the small terms
+// are summed and added last.  The result is the FP32 rounding of the exact
+// sum up to terms of relative size 2^-37, so a shift by a large lattice
+// vector loses nothing to cancellation.
+__device__ __forceinline__ float shifted_diff(float xj, float xi, float th, float tl)
 {
-    if ((sx | sy | sz) == 0) return make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z);
-    double tx = sx * __ldg(c + 0) + sy * __ldg(c + 3) + sz * __ldg(c + 6);
-    double ty = sx * __ldg(c + 1) + sy * __ldg(c + 4) + sz * __ldg(c + 7);
-    double tz = sx * __ldg(c + 2) + sy * __ldg(c + 5) + sz * __ldg(c + 8);
-    return make_float3((float)(((double)pj.x - (double)pi.x) + tx),
-                       (float)(((double)pj.y - (double)pi.y) + ty),
-                       (float)(((double)pj.z - (double)pi.z) + tz));
+    const float s = __fsub_rn(xj, xi);
+    const float bs = __fsub_rn(s, xj);
+    const float e = __fadd_rn(__fsub_rn(xj, __fsub_rn(s, bs)), __fsub_rn(-xi, bs));
+    const float u = __fadd_rn(s, th);
+    const float bu = __fsub_rn(u, s);
+    const float f = __fadd_rn(__fsub_rn(s, __fsub_rn(u, bu)), __fsub_rn(th, bu));
+    return __fadd_rn(u, __fadd_rn(__fadd_rn(e, f), tl));
 }
-__device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, int sx, int sy,
-                                              int sz, const CellArg &cell)
+
+// Pair vector r_ij = r_j + S.cell - r_i in FP32 for the image code of a list
+// entry.  Without an image shift the FP32 difference is correctly rounded;
+// with one, see shifted_diff.
+__device__ __forceinline__ float3 pair_vector(const float4 &pi, const float4 &pj, int code, const float4 *shift)
 {
-    return pair_vector(pi, pj, sx, sy, sz, cell.c);
+    if (code == kCenterCode) return make_float3(pj.x - pi.x, pj.y - pi.y, pj.z - pi.z);
+    const float4 hi = __ldg(shift + 2 * code), lo = __ldg(shift + 2 * code + 1);
+    return make_float3(shifted_diff(pj.x, pi.x, hi.x, lo.x), shifted_diff(pj.y, pi.y, hi.y, lo.y),
+                       shifted_diff(pj.z, pi.z, hi.z, lo.z));
 }
 
 }  // namespace flr

@@ -299,6 +299,7 @@ struct RowArgs {
     int n, max_nbr, compaction;
     const Plan *plans;
     const int32_t *struct_of;
+    const float4 *shift;       // [n_structs][kShiftCodes][2] image shifts, FP32 hi and lo
     float rc2;
     double rc2d;
     int32_t *entries, *count, *group;
@@ -324,7 +325,9 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
     const int k_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * blk);
     for (int kq = blockIdx.x * blk + wl; kq < k_end; kq += 8) {
         const int i = a.bin_atoms[kq];
-        const Plan &P = a.plans[structure_of(a.struct_of, i)];
+        const int sidx = structure_of(a.struct_of, i);
+        const Plan &P = a.plans[sidx];
+        const float4 *img_shift = a.shift + 2 * kShiftCodes * sidx;
         const int span[3] = {2 * P.R[0] + 1, 2 * P.R[1] + 1, 2 * P.R[2] + 1};
         const int n_stencil = span[0] * span[1] * span[2];
         const float4 pib = a.pos_bin[kq];
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
         float u[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            float f = pi.x * (float)P.inv[d] + pi.y * (float)P.inv[3 + d] + pi.z * (float)P.inv[6 + d];
+            float f = pi.x * P.invf[d] + pi.y * P.invf[3 + d] + pi.z * P.invf[6 + d];
             if (P.pbc[d]) f -= floorf(f);
             u[d] = (f - P.flo[d]) / P.fspan[d] * (float)P.nb[d] - (float)bi[d];
         }
@@ -418,9 +421,10 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                     const bool in_range = S[0] >= -2 && S[0] <= 2 && S[1] >= -2 && S[1] <= 2 && S[2] >= -2 &&
                                           S[2] <= 2;
                     if (!in_range) atomicOr(a.status, kErrShift);
-                    if (in_range && !(j == i && S[0] == 0 && S[1] == 0 && S[2] == 0)) {
+                    const int code = (S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2);
+                    if (in_range && !(j == i && code == kCenterCode)) {
                         const float4 pj = pjb;
-                        const float3 r = pair_vector(pi, pj, S[0], S[1], S[2], P.cell);
+                        const float3 r = pair_vector(pi, pj, code, img_shift);
                         const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
                         if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
                             ok = d2 < a.rc2;
@@ -436,7 +440,7 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                             ok = x * x + y * y + z * z < a.rc2d;
                         }
                         sj = (int)((unsigned)__float_as_int(pjb.w) >> 24);
-                        entry = (j << 8) | ((sj & 1) << 7) | ((S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2));
+                        entry = (j << 8) | ((sj & 1) << 7) | code;
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -632,6 +636,7 @@ bool plan_cell(Plan &P, const double *cell, const int *pbc)
     for (int d = 0; d < 3; ++d) P.pbc[d] = pbc[d] ? 1 : 0;
     for (int k = 0; k < 9; ++k)
         if (!std::isfinite(P.inv[k])) return false;
+    for (int k = 0; k < 9; ++k) P.invf[k] = (float)P.inv[k];
     return true;
 }
 
@@ -713,6 +718,23 @@ void host_frac_bbox(const double *cell, const float *pos4, int n, float bb[8])
     bb[6] = bb[7] = 0.f;
 }
 
+// Image shifts S.cell of the 125 codes of one cell (rows = lattice vectors):
+// FP64 sums, each split into FP32 hi and lo = RN(t - hi).
+void fill_shifts(const double *cl, float4 *out)
+{
+    for (int code = 0; code < kShiftCodes; ++code) {
+        const int S[3] = {code / 25 - 2, (code / 5) % 5 - 2, code % 5 - 2};
+        float h[3], l[3];
+        for (int d = 0; d < 3; ++d) {
+            const double t = S[0] * cl[d] + S[1] * cl[3 + d] + S[2] * cl[6 + d];
+            h[d] = (float)t;
+            l[d] = (float)(t - (double)h[d]);
+        }
+        out[2 * code] = make_float4(h[0], h[1], h[2], 0.f);
+        out[2 * code + 1] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
 int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
                const int32_t *pbc, const float4 *pos, int n, cudaStream_t st, const float *host_bb)
 {
@@ -727,18 +749,18 @@ int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offs
         }
     if (n_structs > nl->structs_cap) {
         cudaFree(nl->offsets_d);
-        cudaFree(nl->cells_d);
+        cudaFree(nl->shift_d);
         cudaFree(nl->plans_d);
         cudaFree(nl->bbox);
         delete[] nl->plans_h;
         delete[] nl->offsets_h;
         const int cap = std::max(n_structs, 2 * nl->structs_cap);
         nl->offsets_d = nullptr;
-        nl->cells_d = nullptr;
+        nl->shift_d = nullptr;
         nl->plans_d = nullptr;
         nl->bbox = nullptr;
         cudaError_t e = cudaMalloc(&nl->offsets_d, sizeof(int32_t) * (cap + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&nl->cells_d, sizeof(double) * 9 * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&nl->shift_d, sizeof(float4) * 2 * kShiftCodes * cap);
         if (e == cudaSuccess) e = cudaMalloc(&nl->plans_d, sizeof(Plan) * cap);
         if (e == cudaSuccess) e = cudaMalloc(&nl->bbox, sizeof(float) * 8 * cap);
         nl->plans_h = new Plan[cap];
@@ -763,11 +785,11 @@ int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offs
                                       st),
                       "offsets");
     if (r != FLR_OK) return r;
-    std::vector<double> cl(9 * (size_t)n_structs);
-    for (int s = 0; s < n_structs; ++s)
-        for (int k = 0; k < 9; ++k) cl[9 * s + k] = nl->plans_h[s].cell[k];
-    r = cuda_fail(cudaMemcpyAsync(nl->cells_d, cl.data(), sizeof(double) * cl.size(), cudaMemcpyHostToDevice, st),
-                  "cells");
+    // image shifts S.cell of every code: FP64 sums split into FP32 hi + lo
+    std::vector<float4> sh(2 * kShiftCodes * (size_t)n_structs);
+    for (int s = 0; s < n_structs; ++s) fill_shifts(nl->plans_h[s].cell, sh.data() + 2 * kShiftCodes * (size_t)s);
+    r = cuda_fail(cudaMemcpyAsync(nl->shift_d, sh.data(), sizeof(float4) * sh.size(), cudaMemcpyHostToDevice, st),
+                  "image shifts");
     if (r != FLR_OK) return r;
     if (n_structs > 1) {
         k_struct_of<<<std::min(n_structs, 65535), 256, 0, st>>>(nl->offsets_d, n_structs, nl->struct_of);
@@ -874,6 +896,7 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.max_nbr = nl->max_nbr;
     r.compaction = ctx->p.compaction;
     r.plans = nl->plans_d;
+    r.shift = nl->shift_d;
     r.struct_of = sof;
     const double rc = ctx->p.r_cut + ctx->p.skin;
     r.rc2 = (float)(rc * rc);
@@ -935,6 +958,7 @@ constexpr size_t kNoAllocBytes =
                                                                             // pos_ref, positions in bin order
     (size_t)2 * (kNoAllocMaxBins + 2) * sizeof(int32_t) +                  // bin starts, bin fill
     (size_t)(kNoAllocMaxBins / kScanBlock + 2) * sizeof(int32_t) +         // scan block sums
+    (size_t)2 * kShiftCodes * sizeof(float4) + 256 +                        // image shifts
     4096;                                                                   // flags, status, bbox, plan, group table
 
 std::mutex g_noalloc_mu;
@@ -1015,6 +1039,7 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     float *bbox = reinterpret_cast<float *>(take(sizeof(float) * 8));
     Plan *plan_d = reinterpret_cast<Plan *>(take(sizeof(Plan)));
     GroupTab *gtab = reinterpret_cast<GroupTab *>(take(sizeof(GroupTab)));
+    float4 *shift_d = reinterpret_cast<float4 *>(take(sizeof(float4) * 2 * kShiftCodes));
     if (q > static_cast<unsigned char *>(base) + kNoAllocBytes) {
         set_error("flr_build_neighbors_noalloc: scratch layout exceeds the array");
         return FLR_EINVAL;
@@ -1028,6 +1053,10 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
         return FLR_EINVAL;
     }
     s = cuda_fail(cudaMemcpyAsync(plan_d, &P, sizeof(Plan), cudaMemcpyHostToDevice, st), "plan");
+    if (s != FLR_OK) return s;
+    float4 sh[2 * kShiftCodes];
+    fill_shifts(P.cell, sh);
+    s = cuda_fail(cudaMemcpyAsync(shift_d, sh, sizeof(sh), cudaMemcpyHostToDevice, st), "image shifts");
     if (s != FLR_OK) return s;
     const float4 *pos = reinterpret_cast<const float4 *>(sys->pos);
     k_bbox_init<<<1, 32, 0, st>>>(reinterpret_cast<int *>(bbox), 1);
@@ -1092,6 +1121,7 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     r.max_nbr = max_nbr;
     r.compaction = 1;
     r.plans = plan_d;
+    r.shift = shift_d;
     r.struct_of = nullptr;
     r.rc2 = (float)(r_list * r_list);
     r.rc2d = r_list * r_list;
