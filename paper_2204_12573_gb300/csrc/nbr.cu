@@ -300,6 +300,7 @@ struct RowArgs {
     const Plan *plans;
     const int32_t *struct_of;
     const float4 *shift;       // [n_structs][kShiftCodes][2] image shifts, FP32 hi and lo
+    long long nbins;           // bins of all structures
     float rc2;
     double rc2d;
     int32_t *entries, *count, *group;
@@ -310,45 +311,212 @@ struct RowArgs {
 
 __device__ __forceinline__ int img_comp(int v, int d) { return (int)(int8_t)((v >> (8 * d)) & 0xFF); }
 
-// One warp per atom.  The candidates of all stencil bins are treated as one
-// sequence (bins in stencil order, atoms inside a bin by index), and lanes
-// take 32 consecutive candidates at a time, so the lanes stay full however
-// few atoms each bin holds.
-__global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
+// |r_j + S.cell - r_i|^2 < rc2 decided in FP64 from the exact FP32 inputs
+// (used for candidates whose FP32 distance lies close to the cutoff).
+__device__ __noinline__ bool within_fp64(const float4 pi, const float4 pj, const int *S, const Plan &P, double rc2)
+{
+    double tv[3];
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) tv[cc] = S[0] * P.cell[cc] + S[1] * P.cell[3 + cc] + S[2] * P.cell[6 + cc];
+    const double x = ((double)pj.x - (double)pi.x) + tv[0];
+    const double y = ((double)pj.y - (double)pi.y) + tv[1];
+    const double z = ((double)pj.z - (double)pi.z) + tv[2];
+    return x * x + y * y + z * z < rc2;
+}
+
+// Count, overflow flag and compaction group of a finished row; smask holds
+// the species bits of the accepted neighbours, per lane.
+__device__ __forceinline__ void finish_row(const RowArgs &a, int i, int cnt, unsigned smask, int lane)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) smask |= __shfl_xor_sync(0xffffffffu, smask, o);
+    if (lane == 0) {
+        if (cnt > a.max_nbr) atomicOr(a.status, kErrOverflow);
+        atomicMax(&a.gtab->max_count, cnt);
+        a.count[i] = min(cnt, a.max_nbr);
+        int g = -1;
+        if (cnt > 0) {
+            const int si = a.species[i];
+            if (si < 0 || si >= kSpecies || (smask >> kSpecies) != 0) atomicOr(a.status, kErrSpecies);
+            int cls = 0;
+            if (a.compaction) cls = (smask == 1u) ? 1 : (smask == 2u ? 2 : 0);
+            g = min(max(si, 0), kSpecies - 1) * 3 + cls;
+        }
+        a.group[i] = g;
+    }
+    __syncwarp();
+}
+
+// Row of one atom (bin-order index kq), general form: any image of the atoms,
+// any stencil, per-atom stencil pruning for orthogonal cells.  The
+// candidates of all stencil bins are treated as one sequence (bins in stencil
+// order, atoms inside a bin by index), and lanes take 32 consecutive
+// candidates at a time, so the lanes stay full however few atoms each bin
+// holds.  s_start, s_excl and s_shift are the warp's 32-entry scratch rows.
+__device__ __forceinline__ void row_general(const RowArgs &a, int kq, int lane, int *s_start, int *s_excl,
+                                            int *s_shift)
+{
+    const int i = a.bin_atoms[kq];
+    const int sidx = structure_of(a.struct_of, i);
+    const Plan &P = a.plans[sidx];
+    const float4 *img_shift = a.shift + 2 * kShiftCodes * sidx;
+    const int span[3] = {2 * P.R[0] + 1, 2 * P.R[1] + 1, 2 * P.R[2] + 1};
+    const int n_stencil = span[0] * span[1] * span[2];
+    const float4 pib = a.pos_bin[kq];
+    const float4 pi = pib;
+    const int bin = a.atom_bin[i] - (int)P.bin_base;
+    const int bi[3] = {bin / (P.nb[1] * P.nb[2]), (bin / P.nb[2]) % P.nb[1], bin % P.nb[2]};
+    const int imi = __float_as_int(pib.w) & 0xFFFFFF;
+    // the atom's offset inside its bin (bin units), for skipping stencil
+    // bins whose box lies farther than the list cutoff (orthogonal cells)
+    float u[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float f = pi.x * P.invf[d] + pi.y * P.invf[3 + d] + pi.z * P.invf[6 + d];
+        if (P.pbc[d]) f -= floorf(f);
+        u[d] = (f - P.flo[d]) / P.fspan[d] * (float)P.nb[d] - (float)bi[d];
+    }
+    int32_t *row = a.entries + (size_t)i * a.max_nbr;
+    int cnt = 0;
+    unsigned smask = 0;
+    for (int sbase = 0; sbase < n_stencil; sbase += 32) {
+        // this lane's stencil bin: range of candidates and lattice shift
+        const int k = sbase + lane;
+        int c = 0, start = 0, shift = 0;
+        if (k < n_stencil) {
+            const int dd[3] = {k / (span[1] * span[2]) - P.R[0], (k / span[2]) % span[1] - P.R[1],
+                               k % span[2] - P.R[2]};
+            int bj[3], sb[3];
+            bool skip = false;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int kk = bi[d] + dd[d];
+                if (P.pbc[d]) {
+                    const int q = (kk >= 0) ? kk / P.nb[d] : -((-kk + P.nb[d] - 1) / P.nb[d]);
+                    sb[d] = q;
+                    bj[d] = kk - q * P.nb[d];
+                } else {
+                    skip |= (kk < 0 || kk >= P.nb[d]);
+                    sb[d] = 0;
+                    bj[d] = kk;
+                }
+            }
+            if (!skip && P.orth) {
+                // lower bound of the distance from the atom to the bin's box
+                float d2 = 0.f;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float gap = dd[d] > 0 ? (float)dd[d] - u[d] : (dd[d] < 0 ? u[d] - (float)dd[d] - 1.f : 0.f);
+                    const float gm = fmaxf(gap, 0.f) * P.bw[d];
+                    d2 += gm * gm;
+                }
+                skip = d2 > a.rc2 * 1.0001f + 1e-3f;
+            }
+            if (!skip) {
+                const int b = (int)P.bin_base + (bj[0] * P.nb[1] + bj[1]) * P.nb[2] + bj[2];
+                start = a.bin_start[b];
+                c = a.bin_start[b + 1] - start;
+                shift = (sb[0] & 0xFF) | ((sb[1] & 0xFF) << 8) | ((sb[2] & 0xFF) << 16);
+            }
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_start[lane] = start;
+        s_excl[lane] = incl - c;
+        s_shift[lane] = shift;
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int t = base + lane;
+            bool ok = false;
+            int entry = 0, sj = 0;
+            if (t < total) {
+                // last stencil slot whose first candidate index is <= t
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_excl[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int slot = s_start[lo] + (t - s_excl[lo]);
+                const int j = a.bin_atoms[slot];
+                const float4 pjb = a.pos_bin[slot];   // independent of j: no load chain
+                const int sh = s_shift[lo];
+                const int imj = __float_as_int(pjb.w) & 0xFFFFFF;
+                int S[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) S[d] = img_comp(sh, d) + img_comp(imi, d) - img_comp(imj, d);
+                const bool in_range = S[0] >= -2 && S[0] <= 2 && S[1] >= -2 && S[1] <= 2 && S[2] >= -2 &&
+                                      S[2] <= 2;
+                if (!in_range) atomicOr(a.status, kErrShift);
+                const int code = (S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2);
+                if (in_range && !(j == i && code == kCenterCode)) {
+                    const float4 pj = pjb;
+                    const float3 r = pair_vector(pi, pj, code, img_shift);
+                    const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                    if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
+                        ok = d2 < a.rc2;
+                    } else {
+                        // near the cutoff: decide in FP64 from the exact inputs
+                        ok = within_fp64(pi, pj, S, P, a.rc2d);
+                    }
+                    sj = (int)((unsigned)__float_as_int(pjb.w) >> 24);
+                    entry = (j << 8) | ((sj & 1) << 7) | code;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+            if (ok) {
+                if (slot < a.max_nbr) row[slot] = entry;
+                smask |= 1u << (sj & 31);
+            }
+            cnt += __popc(m);
+        }
+        __syncwarp();
+    }
+    finish_row(a, i, cnt, smask, lane);
+}
+
+constexpr int kBuildWarps = 8;
+constexpr int kTile = 320;   // stencil candidates a warp stages for one bin
+
+// One warp per bin (bins in order, spread over the warps of the grid).  For a
+// bin whose stencil candidates all carry image 0, image shifts inside
+// [-2, 2]^3 and a valid species (always the case for positions wrapped into
+// the cell, as in MD), the warp stages the candidate set once: each
+// candidate's position relative to the bin's first atom, shifted by its
+// image (shifted_diff: within a few 1e-6 A of exact over the stencil's
+// extent), and its finished list entry.  Every atom of the bin then scans the
+// staged set with one distance test per candidate, decided again in FP64
+// from the exact inputs within a relative 4e-5 of the cutoff, so the accepted
+// set and its order (stencil order, then atom index) are those of the general
+// per-atom path, which the other bins take.
+__global__ void __launch_bounds__(kBuildWarps * 32) k_build_bins(RowArgs a)
 {
     if (a.flags[0] == 0) return;
-    __shared__ int s_start[8][32], s_excl[8][32], s_shift[8][32];
+    __shared__ int s_start[kBuildWarps][32], s_excl[kBuildWarps][32], s_shift[kBuildWarps][32];
+    __shared__ __align__(16) float4 s_cand[kBuildWarps][kTile];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    // atoms are taken in bin order, each CTA a contiguous block of it, so the
-    // warps of a CTA scan overlapping stencils and share candidates in L1
-    const int blk = (int)(((long long)a.n + gridDim.x - 1) / gridDim.x);
-    const int k_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * blk);
-    for (int kq = blockIdx.x * blk + wl; kq < k_end; kq += 8) {
-        const int i = a.bin_atoms[kq];
-        const int sidx = structure_of(a.struct_of, i);
+    const long long nwarps = (long long)gridDim.x * kBuildWarps;
+    for (long long b = (long long)blockIdx.x * kBuildWarps + wl; b < a.nbins; b += nwarps) {
+        const int k0 = a.bin_start[b], k1 = a.bin_start[b + 1];
+        if (k1 <= k0) continue;
+        const int sidx = structure_of(a.struct_of, a.bin_atoms[k0]);
         const Plan &P = a.plans[sidx];
         const float4 *img_shift = a.shift + 2 * kShiftCodes * sidx;
         const int span[3] = {2 * P.R[0] + 1, 2 * P.R[1] + 1, 2 * P.R[2] + 1};
         const int n_stencil = span[0] * span[1] * span[2];
-        const float4 pib = a.pos_bin[kq];
-        const float4 pi = pib;
-        const int bin = a.atom_bin[i] - (int)P.bin_base;
+        const int bin = (int)(b - P.bin_base);
         const int bi[3] = {bin / (P.nb[1] * P.nb[2]), (bin / P.nb[2]) % P.nb[1], bin % P.nb[2]};
-        const int imi = __float_as_int(pib.w) & 0xFFFFFF;
-        // the atom's offset inside its bin (bin units), for skipping stencil
-        // bins whose box lies farther than the list cutoff (orthogonal cells)
-        float u[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            float f = pi.x * P.invf[d] + pi.y * P.invf[3 + d] + pi.z * P.invf[6 + d];
-            if (P.pbc[d]) f -= floorf(f);
-            u[d] = (f - P.flo[d]) / P.fspan[d] * (float)P.nb[d] - (float)bi[d];
-        }
-        int32_t *row = a.entries + (size_t)i * a.max_nbr;
-        int cnt = 0;
-        unsigned smask = 0;
-        for (int sbase = 0; sbase < n_stencil; sbase += 32) {
-            // this lane's stencil bin: range of candidates and lattice shift
+        const float4 o4 = a.pos_bin[k0];   // reference point of the staged coordinates
+        float4 *cand = s_cand[wl];
+        bool fast = true;
+        int nc = 0;
+        for (int sbase = 0; sbase < n_stencil && fast; sbase += 32) {
             const int k = sbase + lane;
             int c = 0, start = 0, shift = 0;
             if (k < n_stencil) {
@@ -369,21 +537,10 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
                         bj[d] = kk;
                     }
                 }
-                if (!skip && P.orth) {
-                    // lower bound of the distance from the atom to the bin's box
-                    float d2 = 0.f;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const float gap = dd[d] > 0 ? (float)dd[d] - u[d] : (dd[d] < 0 ? u[d] - (float)dd[d] - 1.f : 0.f);
-                        const float gm = fmaxf(gap, 0.f) * P.bw[d];
-                        d2 += gm * gm;
-                    }
-                    skip = d2 > a.rc2 * 1.0001f + 1e-3f;
-                }
                 if (!skip) {
-                    const int b = (int)P.bin_base + (bj[0] * P.nb[1] + bj[1]) * P.nb[2] + bj[2];
-                    start = a.bin_start[b];
-                    c = a.bin_start[b + 1] - start;
+                    const int gb = (int)P.bin_base + (bj[0] * P.nb[1] + bj[1]) * P.nb[2] + bj[2];
+                    start = a.bin_start[gb];
+                    c = a.bin_start[gb + 1] - start;
                     shift = (sb[0] & 0xFF) | ((sb[1] & 0xFF) << 8) | ((sb[2] & 0xFF) << 16);
                 }
             }
@@ -398,79 +555,93 @@ __global__ void __launch_bounds__(256) k_build_rows(RowArgs a)
             s_excl[wl][lane] = incl - c;
             s_shift[wl][lane] = shift;
             __syncwarp();
-            for (int base = 0; base < total; base += 32) {
+            if (nc + total > kTile) {
+                fast = false;
+            } else {
+                for (int base = 0; base < total; base += 32) {
+                    const int t = base + lane;
+                    bool bad = false;
+                    if (t < total) {
+                        int lo = 0, hi = 31;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_excl[wl][mid] <= t) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const int slot = s_start[wl][lo] + (t - s_excl[wl][lo]);
+                        const int j = a.bin_atoms[slot];
+                        const float4 pj = a.pos_bin[slot];
+                        const int sh = s_shift[wl][lo];
+                        const int wj = __float_as_int(pj.w);
+                        const int sj = (int)((unsigned)wj >> 24);
+                        int S[3];
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) S[d] = img_comp(sh, d);
+                        bad = (wj & 0xFFFFFF) != 0 || sj >= kSpecies || S[0] < -2 || S[0] > 2 || S[1] < -2 ||
+                              S[1] > 2 || S[2] < -2 || S[2] > 2;
+                        if (!bad) {
+                            const int code = (S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2);
+                            float3 d;
+                            if (code == kCenterCode) {
+                                d = make_float3(__fsub_rn(pj.x, o4.x), __fsub_rn(pj.y, o4.y), __fsub_rn(pj.z, o4.z));
+                            } else {
+                                const float4 th = __ldg(img_shift + 2 * code), tl = __ldg(img_shift + 2 * code + 1);
+                                d = make_float3(shifted_diff(pj.x, o4.x, th.x, tl.x), shifted_diff(pj.y, o4.y, th.y, tl.y),
+                                                shifted_diff(pj.z, o4.z, th.z, tl.z));
+                            }
+                            // keep the staged coordinates small, so their rounding stays far below the FP64 band
+                            bad = fmaxf(fabsf(d.x), fmaxf(fabsf(d.y), fabsf(d.z))) > 96.f;
+                            cand[nc + t] = make_float4(d.x, d.y, d.z, __int_as_float((j << 8) | (sj << 7) | code));
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, bad)) fast = false;
+                }
+                nc += total;
+            }
+            __syncwarp();
+        }
+        if (!fast) {
+            for (int kq = k0; kq < k1; ++kq) row_general(a, kq, lane, s_start[wl], s_excl[wl], s_shift[wl]);
+            continue;
+        }
+        for (int kq = k0; kq < k1; ++kq) {
+            const int i = a.bin_atoms[kq];
+            const float4 pi = a.pos_bin[kq];
+            const float dix = __fsub_rn(pi.x, o4.x), diy = __fsub_rn(pi.y, o4.y), diz = __fsub_rn(pi.z, o4.z);
+            const int self = (i << 8) | ((int)((unsigned)__float_as_int(pi.w) >> 24) << 7) | kCenterCode;
+            int32_t *row = a.entries + (size_t)i * a.max_nbr;
+            int cnt = 0;
+            unsigned smask = 0;
+            for (int base = 0; base < nc; base += 32) {
                 const int t = base + lane;
                 bool ok = false;
-                int entry = 0, sj = 0;
-                if (t < total) {
-                    // last stencil slot whose first candidate index is <= t
-                    int lo = 0, hi = 31;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_excl[wl][mid] <= t) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    const int slot = s_start[wl][lo] + (t - s_excl[wl][lo]);
-                    const int j = a.bin_atoms[slot];
-                    const float4 pjb = a.pos_bin[slot];   // independent of j: no load chain
-                    const int sh = s_shift[wl][lo];
-                    const int imj = __float_as_int(pjb.w) & 0xFFFFFF;
-                    int S[3];
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) S[d] = img_comp(sh, d) + img_comp(imi, d) - img_comp(imj, d);
-                    const bool in_range = S[0] >= -2 && S[0] <= 2 && S[1] >= -2 && S[1] <= 2 && S[2] >= -2 &&
-                                          S[2] <= 2;
-                    if (!in_range) atomicOr(a.status, kErrShift);
-                    const int code = (S[0] + 2) * 25 + (S[1] + 2) * 5 + (S[2] + 2);
-                    if (in_range && !(j == i && code == kCenterCode)) {
-                        const float4 pj = pjb;
-                        const float3 r = pair_vector(pi, pj, code, img_shift);
-                        const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
-                        if (fabsf(d2 - a.rc2) > 1e-5f * a.rc2) {
+                int e = 0;
+                if (t < nc) {
+                    const float4 cd = cand[t];
+                    e = __float_as_int(cd.w);
+                    if (e != self) {
+                        const float rx = cd.x - dix, ry = cd.y - diy, rz = cd.z - diz;
+                        const float d2 = rx * rx + ry * ry + rz * rz;
+                        if (fabsf(d2 - a.rc2) > 4e-5f * a.rc2) {
                             ok = d2 < a.rc2;
                         } else {
-                            // near the cutoff: decide in FP64 from the exact inputs
-                            double tv[3];
-#pragma unroll
-                            for (int cc = 0; cc < 3; ++cc)
-                                tv[cc] = S[0] * P.cell[cc] + S[1] * P.cell[3 + cc] + S[2] * P.cell[6 + cc];
-                            const double x = ((double)pj.x - (double)pi.x) + tv[0];
-                            const double y = ((double)pj.y - (double)pi.y) + tv[1];
-                            const double z = ((double)pj.z - (double)pi.z) + tv[2];
-                            ok = x * x + y * y + z * z < a.rc2d;
+                            const int code = e & 127;
+                            const int S[3] = {code / 25 - 2, (code / 5) % 5 - 2, code % 5 - 2};
+                            ok = within_fp64(pi, __ldg(a.pos + ((unsigned)e >> 8)), S, P, a.rc2d);
                         }
-                        sj = (int)((unsigned)__float_as_int(pjb.w) >> 24);
-                        entry = (j << 8) | ((sj & 1) << 7) | code;
                     }
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, ok);
                 const int slot = cnt + __popc(m & ((1u << lane) - 1u));
                 if (ok) {
-                    if (slot < a.max_nbr) row[slot] = entry;
-                    smask |= 1u << (sj & 31);
+                    if (slot < a.max_nbr) row[slot] = e;
+                    smask |= 1u << ((e >> 7) & 1);
                 }
                 cnt += __popc(m);
             }
-            __syncwarp();
+            finish_row(a, i, cnt, smask, lane);
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) smask |= __shfl_xor_sync(0xffffffffu, smask, o);
-        if (lane == 0) {
-            if (cnt > a.max_nbr) atomicOr(a.status, kErrOverflow);
-            atomicMax(&a.gtab->max_count, cnt);
-            a.count[i] = min(cnt, a.max_nbr);
-            int g = -1;
-            if (cnt > 0) {
-                const int si = a.species[i];
-                if (si < 0 || si >= kSpecies || (smask >> kSpecies) != 0) atomicOr(a.status, kErrSpecies);
-                int cls = 0;
-                if (a.compaction) cls = (smask == 1u) ? 1 : (smask == 2u ? 2 : 0);
-                g = min(max(si, 0), kSpecies - 1) * 3 + cls;
-            }
-            a.group[i] = g;
-        }
-        __syncwarp();
-    }  // atoms
+    }
 }
 
 // ---- stable partition of atoms into compaction groups ----
@@ -907,7 +1078,9 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.gtab = nl->gtab;
     r.flags = nl->flags;
     r.status = ctx->status;
-    k_build_rows<<<persistent_grid(k_build_rows, 256, ctx->num_sms, (n + 7) / 8), 256, 0, st>>>(r);
+    r.nbins = nbins;
+    k_build_bins<<<persistent_grid(k_build_bins, kBuildWarps * 32, ctx->num_sms, (nbins + kBuildWarps - 1) / kBuildWarps),
+                   kBuildWarps * 32, 0, st>>>(r);
 
     const int nblk = (n + kGroupBlock - 1) / kGroupBlock;
     k_group_count<<<nblk, kGroupBlock, 0, st>>>(nl->group, n, nl->blk_group, nl->flags);
@@ -1131,7 +1304,9 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     r.gtab = gtab;
     r.flags = flags;
     r.status = status;
-    k_build_rows<<<std::max(1, std::min((n + 7) / 8, num_sms * 8)), 256, 0, st>>>(r);
+    r.nbins = nbins;
+    k_build_bins<<<persistent_grid(k_build_bins, kBuildWarps * 32, num_sms, (nbins + kBuildWarps - 1) / kBuildWarps),
+                   kBuildWarps * 32, 0, st>>>(r);
     s = cuda_fail(cudaGetLastError(), "neighbour build (no allocation)");
     if (s != FLR_OK) return s;
     int stv = 0, maxc = 0;

@@ -66,6 +66,41 @@ def test_neighbor_sets_bit_exact(which):
         assert np.array_equal((v >> 7) & 1, s.species[v >> 8])
 
 
+def _boundary_cluster():
+    """A 13-atom Pt cuboctahedron (nearest neighbours 2.77 A) and an H2
+    molecule, centred on a corner of a 2000 A triclinic cell periodic in x
+    and y and wrapped into it: most pairs cross the periodic boundary, with
+    coordinates near 0 and near 2000 A.  Forming r_j - r_i + S.cell plainly
+    in FP32 loses about 6e-5 A there, far outside the descriptor tolerance."""
+    a = 3.92
+    pts = [np.zeros(3)]
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        for si in (-1, 1):
+            for sj in (-1, 1):
+                v = np.zeros(3)
+                v[i], v[j] = si * a / 2, sj * a / 2
+                pts.append(v)
+    pt = np.array(pts)
+    h2 = np.array([[0.37, 0.0, 4.6], [-0.37, 0.0, 4.6]])
+    cell = np.array([[2000.0, 0.0, 0.0], [1000.0, 1732.0508075688772, 0.0], [0.0, 0.0, 60.0]])
+    pos = np.concatenate([pt, h2]) + np.array([0.35, 0.2, 25.0])
+    pos = synth._wrap(pos, cell, (1, 1, 0))
+    sp = np.array([0] * 13 + [1, 1], np.int32)
+    return synth.Structure(pos, sp, cell, (1, 1, 0), "boundary-cluster")
+
+
+def test_large_cell_boundary_pairs():
+    s = _boundary_cluster()
+    assert s.pos[:, 0].max() > 1990.0          # wrapped to the far side of the cell
+    g, *_ = gpu_run(s, BETA, SIGMA, want_desc=True)
+    pos = synth.f32_exact_f64(synth.as_f32_positions(s.pos))
+    ref = O.neighbors(pos, s.cell, s.pbc, 5.0, method="brute")
+    assert np.array_equal(decode_entries(g["entries"], g["count"]), ref.astype(np.int64))
+    o = oracle_run(s, BETA, SIGMA)
+    assert np.abs(g["dhat"] - o["dhat"]).max() <= 2e-6
+    compare_efv(g, o)
+
+
 def test_rows_are_deterministic():
     s = _slabs()[0]
     g1, *_ = gpu_run(s, BETA, SIGMA)
