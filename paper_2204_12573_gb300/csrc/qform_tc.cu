@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 const TileInfo ti = decode_tile(T, a.nch, t);
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
+                const int K = a.K[ti.reg];
                 for (int ch = 0; ch < ti.nch && ok; ++ch, ++it) {
                     if (!mbar_wait(tempty, (uint32_t)((it & 1) ^ 1), abort_flag)) { ok = false; break; }
                     fence_after();
@@ -313,8 +314,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                         const uint32_t db = smem_u32(sB + stage * kTileB);
                         const uint64_t ad = sw128_desc(da);
                         const uint64_t bd0 = sw128_desc(db), bd1 = sw128_desc(db + NH * 128);
+                        // K steps past K (the zero padding of the last block) are skipped
+                        const int kk = BF16 ? kb % nkb : kb;
+                        const int kleft = K - kk * (BF16 ? 64 : 32);
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
+                            if (ks * (BF16 ? 16 : 8) >= kleft) break;
                             const uint32_t accum = (kb | ks) != 0;
                             mma<BF16>(tmem, ad + 2 * ks, bd0 + 2 * ks, idesc, accum);
                             mma<BF16>(tmem + NH, ad + 2 * ks, bd1 + 2 * ks, idesc, accum);
