@@ -44,6 +44,7 @@ constexpr int kTmemCols = 512;
 constexpr int kSubs = 3;            // epilogue warps per TMEM lane quarter (each takes every 3rd 16-column group)
 constexpr int kParkCols = 144;      // widest one-species row parked in shared memory
 constexpr int kParkStride = kParkCols + 4;
+constexpr int kParkGroups = (kParkCols / 16 + kSubs - 1) / kSubs;   // 16-column groups per epilogue thread
 constexpr int kEpiWarps = 4 * kSubs;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr unsigned long long kDeadlineNs = 2000000000ull;
@@ -194,6 +195,70 @@ __device__ __forceinline__ void load16(const float *p, float v[16])
         v[4 * k + 2] = q.z;
         v[4 * k + 3] = q.w;
     }
+}
+
+// Epilogue: wait for a full accumulator (lane 0 waits, the warp follows its
+// verdict, so the warp stays converged); false on timeout or abort.
+__device__ __forceinline__ bool acc_wait(uint32_t tfull, int it, int lane, volatile int *abort_flag, int *status)
+{
+    int okw = 1;
+    if (lane == 0) okw = mbar_wait(tfull, (uint32_t)(it & 1), abort_flag) ? 1 : 0;
+    okw = __shfl_sync(0xffffffffu, okw, 0);
+    if (!okw && lane == 0) {
+        atomicOr(status, kErrTimeout);
+        *abort_flag = 1;
+    }
+    if (okw) fence_after();
+    return okw != 0;
+}
+
+// While the MMAs of the next tile run, pull this thread's descriptor row of
+// tile tn into L2, so that tile's reads of it do not wait on DRAM.
+__device__ __forceinline__ void prefetch_next_rows(const TcArgs &a, const GroupTab &T, int tn, int total, int rloc,
+                                                   int sub)
+{
+    if (tn >= total) return;
+    const TileInfo tj = decode_tile(T, a.nch, tn);
+    const int rown = tj.row0 + rloc;
+    if (rown >= tj.rend) return;
+    const char *dn = reinterpret_cast<const char *>(a.D32[tj.reg] + (size_t)rown * a.kp32[tj.reg]);
+    const int bytes = 4 * a.K[tj.reg];
+    for (int o = 128 * sub; o < bytes; o += 128 * kSubs) asm volatile("prefetch.global.L2 [%0];" ::"l"(dn + o));
+}
+
+// Combine the partial E, V, sum|.| of the kSubs column sets of a row through
+// shared memory (double-buffered by tile, bounded mbarrier wait, fixed order).
+__device__ __forceinline__ bool exchange(float4 *evx_buf, uint32_t evx, int tl, int sub, int rloc, int lane,
+                                         volatile int *abort_flag, int *status, float &E, float &V, float &Va)
+{
+    float4 *xb = evx_buf + (tl & 1) * (kSubs * BM);
+    xb[sub * BM + rloc] = make_float4(E, V, Va, 0.f);
+    __syncwarp();
+    int okx = 1;
+    if (lane == 0) {
+        mbar_arrive(evx);
+        okx = mbar_wait(evx, (uint32_t)(tl & 1), abort_flag) ? 1 : 0;
+    }
+    okx = __shfl_sync(0xffffffffu, okx, 0);
+    __syncwarp();
+    if (!okx) {
+        if (lane == 0) {
+            atomicOr(status, kErrTimeout);
+            *abort_flag = 1;
+        }
+        return false;
+    }
+    E = 0.f;
+    V = 0.f;
+    Va = 0.f;
+#pragma unroll
+    for (int q = 0; q < kSubs; ++q) {
+        const float4 p = xb[q * BM + rloc];
+        E += p.x;
+        V += p.y;
+        Va += p.z;
+    }
+    return true;
 }
 
 template <bool BF16>
@@ -374,42 +439,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             const bool fact = a.var_factored[ti.g] != 0;
             const bool in_smem = ti.nch == 1 && (K % 16) == 0 && 2 * K <= NC && K <= kParkCols;
             float E = 0.f, V = 0.f, Va = 0.f;
-            for (int ch = 0; ch < ti.nch; ++ch, ++it) {
-                // lane 0 waits and the warp follows its verdict, so the warp stays converged
-                int okw = 1;
-                if (lane == 0) okw = mbar_wait(tfull, (uint32_t)(it & 1), abort_flag) ? 1 : 0;
-                okw = __shfl_sync(0xffffffffu, okw, 0);
-                if (!okw) {
-                    if (lane == 0) {
-                        atomicOr(a.status, kErrTimeout);
-                        *abort_flag = 1;
-                    }
+            if (in_smem) {
+                // one-species tile: one chunk holding [beta d | Sigma d]; this
+                // thread takes at most kParkGroups groups of 16 columns
+                if (!acc_wait(tfull, it, lane, abort_flag, a.status)) {
                     alive = false;
                     break;
                 }
-                fence_after();
-                if (in_smem) {
-                    // one chunk holding [beta d | Sigma d]
-#pragma unroll 1
-                    for (int c = 16 * sub; c < K; c += 16 * kSubs) {
-                        float dv[16], vb[16], vs[16];
-                        if (valid) load16(d + c, dv);
-                        tmem_ld16(tbase + (uint32_t)c, vb);
-                        tmem_ld16(tbase + (uint32_t)(K + c), vs);
+                ++it;
 #pragma unroll
-                        for (int k = 0; k < 16; k += 4)
-                            *reinterpret_cast<float4 *>(prow + c + k) = make_float4(vb[k], vb[k + 1], vb[k + 2], vb[k + 3]);
-                        if (valid) {
+                for (int j = 0; j < kParkGroups; ++j) {
+                    const int c = 16 * (sub + kSubs * j);
+                    if (c >= K) break;
+                    float dv[16];
+                    if (valid) {
+                        load16(d + c, dv);
+                    } else {
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                E += dv[k] * vb[k];
-                                const float tq = (fact ? vs[k] : dv[k]) * vs[k];
-                                V += tq;
-                                Va += fabsf(tq);
-                            }
+                        for (int k = 0; k < 16; ++k) dv[k] = 0.f;
+                    }
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)c, v);
+#pragma unroll
+                    for (int k = 0; k < 16; k += 4)
+                        *reinterpret_cast<float4 *>(prow + c + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
+                    tmem_ld16(tbase + (uint32_t)(K + c), v);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float tq = (fact ? v[k] : dv[k]) * v[k];
+                        V += tq;
+                        Va += fabsf(tq);
+                    }
+                }
+                // the accumulator is free again: the next MMAs overlap the rest below
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty);
+                prefetch_next_rows(a, T, t + gridDim.x, total, rloc, sub);
+                if (!exchange(evx_buf, evx, tl, sub, rloc, lane, abort_flag, a.status, E, V, Va)) {
+                    alive = false;
+                    break;
+                }
+                if (valid) {
+                    // g = (2/||B||)(beta d - E d) from the parked beta d (d read again)
+#pragma unroll
+                    for (int j = 0; j < kParkGroups; ++j) {
+                        const int c = 16 * (sub + kSubs * j);
+                        if (c >= K) break;
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4) {
+                            const float4 p = *reinterpret_cast<const float4 *>(prow + c + k);
+                            const float4 q = __ldg(reinterpret_cast<const float4 *>(d + c + k));
+                            *reinterpret_cast<float4 *>(grow + c + k) =
+                                make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
+                                            s2 * (p.w - E * q.w));
                         }
                     }
-                } else {
+                }
+            } else {
+                // two-species tile: column chunks of NC, beta d parked in the g row
+                for (int ch = 0; ch < ti.nch; ++ch, ++it) {
+                    if (!acc_wait(tfull, it, lane, abort_flag, a.status)) {
+                        alive = false;
+                        break;
+                    }
                     const int c0 = ch * NC;
 #pragma unroll 1
                     for (int c = 16 * sub; c < NC; c += 16 * kSubs) {
@@ -449,73 +544,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                             }
                         }
                     }
+                    // the accumulator is free again: the next MMAs overlap the rest below
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty);
                 }
-                // the accumulator is free again: the next MMAs overlap the rest below
-                fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty);
-            }
-            if (!alive) break;
-            // While the MMAs of the next tile run, pull this thread's descriptor
-            // row of that tile into L2, so the accumulator read-back of the next
-            // tile does not wait on DRAM.
-            {
-                const int tn = t + gridDim.x;
-                if (tn < total) {
-                    const TileInfo tj = decode_tile(T, a.nch, tn);
-                    const int rown = tj.row0 + rloc;
-                    if (rown < tj.rend) {
-                        const char *dn = reinterpret_cast<const char *>(a.D32[tj.reg] + (size_t)rown * a.kp32[tj.reg]);
-                        const int bytes = 4 * a.K[tj.reg];
-                        for (int o = 128 * sub; o < bytes; o += 128 * kSubs)
-                            asm volatile("prefetch.global.L2 [%0];" ::"l"(dn + o));
-                    }
+                if (!alive) break;
+                prefetch_next_rows(a, T, t + gridDim.x, total, rloc, sub);
+                if (!exchange(evx_buf, evx, tl, sub, rloc, lane, abort_flag, a.status, E, V, Va)) {
+                    alive = false;
+                    break;
                 }
-            }
-            // combine the partial sums of the kSubs column sets (fixed order)
-            float4 *xb = evx_buf + (tl & 1) * (kSubs * BM);
-            xb[sub * BM + rloc] = make_float4(E, V, Va, 0.f);
-            __syncwarp();
-            int okx = 1;
-            if (lane == 0) {
-                mbar_arrive(evx);
-                okx = mbar_wait(evx, (uint32_t)(tl & 1), abort_flag) ? 1 : 0;
-            }
-            okx = __shfl_sync(0xffffffffu, okx, 0);
-            __syncwarp();
-            if (!okx) {
-                if (lane == 0) {
-                    atomicOr(a.status, kErrTimeout);
-                    *abort_flag = 1;
-                }
-                alive = false;
-                break;
-            }
-            E = 0.f;
-            V = 0.f;
-            Va = 0.f;
-#pragma unroll
-            for (int q = 0; q < kSubs; ++q) {
-                const float4 p = xb[q * BM + rloc];
-                E += p.x;
-                V += p.y;
-                Va += p.z;
-            }
-            if (valid) {
-                if (in_smem) {
-                    // g = (2/||B||)(beta d - E d) from the parked beta d
-#pragma unroll 1
-                    for (int c = 16 * sub; c < K; c += 16 * kSubs) {
-#pragma unroll
-                        for (int k = 0; k < 16; k += 4) {
-                            const float4 p = *reinterpret_cast<const float4 *>(prow + c + k);
-                            const float4 q = __ldg(reinterpret_cast<const float4 *>(d + c + k));
-                            *reinterpret_cast<float4 *>(grow + c + k) =
-                                make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
-                                            s2 * (p.w - E * q.w));
-                        }
-                    }
-                } else {
+                if (valid) {
                     // g = (2/||B||)(beta d - E d) over the 16-column groups this set parked
                     float4 *g4 = reinterpret_cast<float4 *>(grow);
                     const float4 *d4 = reinterpret_cast<const float4 *>(d);
@@ -536,14 +576,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                                                          s2 * (p[u].z - E * q[u].z), s2 * (p[u].w - E * q[u].w));
                     }
                 }
-                if (sub == 0) {
-                    a.energy[atom] = E;
-                    if (a.variance) a.variance[atom] = V;
-                    if (a.sigma) a.sigma[atom] = sqrtf(fmaxf(V, 0.f));
-                    if (a.refine && !fact && (V * kVarCancel < Va || V < a.v_small[ti.g])) {
-                        const int q = atomicAdd(a.ref_count, 1);
-                        if (q < a.ref_cap) a.ref_list[q] = atom;
-                    }
+            }
+            if (valid && sub == 0) {
+                a.energy[atom] = E;
+                if (a.variance) a.variance[atom] = V;
+                if (a.sigma) a.sigma[atom] = sqrtf(fmaxf(V, 0.f));
+                if (a.refine && !fact && (V * kVarCancel < Va || V < a.v_small[ti.g])) {
+                    const int q = atomicAdd(a.ref_count, 1);
+                    if (q < a.ref_cap) a.ref_list[q] = atom;
                 }
             }
         }
