@@ -20,10 +20,10 @@
 // FIFO queue; whenever 32 pairs are queued they are evaluated with one pair
 // per lane, whatever atoms they belong to, so the expensive per-pair path
 // always runs with full lanes.  Forces are accumulated as 64-bit fixed point
-// (2^-32 eV/A): F_j through global atomics, F_i by warp reductions over the
-// lanes of each atom; integer sums do not depend on order or on how an
-// atom's pairs were split over batches, so forces are bitwise reproducible
-// and independent of what else is evaluated alongside.
+// (2^-32 eV/A) through global atomics, +f_ij on F_i and -f_ij on F_j; integer
+// sums do not depend on order or on how an atom's pairs were split over
+// batches, so forces are bitwise reproducible and independent of what else is
+// evaluated alongside.
 #include "basis.cuh"
 #include "internal.cuh"
 
@@ -71,7 +71,6 @@ struct ForceSmem {
     float gr[kWarpsForce][(2 * N) * (2 * N + 1) / 2 * 4];   // raw g row of the next atom (cp.async)
     float W[kWarpsForce][kSlots * kWSlot];
     float4 q[kWarpsForce][64];                  // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
-    long long F[kWarpsForce][kSlots][3];         // F_i of each slot's atom, fixed point
     long long V[kWarpsForce][kSlots][9];         // virial of each slot's atom (when requested), fixed point
     int atom[kWarpsForce][kSlots];
     int qseq[kWarpsForce][64];                  // atom sequence number of each queued pair
@@ -98,7 +97,6 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
                                             unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     int my_slot = -1;
-    long long f3[3] = {0, 0, 0};   // f_ij in fixed point: F_i gets exactly what F_j loses
     float dv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (lane < m) {
         const float4 rec = sm.q[w][lane];
@@ -147,44 +145,38 @@ __device__ __forceinline__ void force_batch(ForceSmem<N> &sm, int w, int lane, i
         atomicAdd(dj + 0, (unsigned long long)(-ix));
         atomicAdd(dj + 1, (unsigned long long)(-iy));
         atomicAdd(dj + 2, (unsigned long long)(-iz));
+        unsigned long long *di = Facc + 3 * (size_t)sm.atom[w][slot];
+        atomicAdd(di + 0, (unsigned long long)ix);
+        atomicAdd(di + 1, (unsigned long long)iy);
+        atomicAdd(di + 2, (unsigned long long)iz);
         dv[0] = -rec.x * fx; dv[1] = -rec.x * fy; dv[2] = -rec.x * fz;
         dv[3] = -rec.y * fx; dv[4] = -rec.y * fy; dv[5] = -rec.y * fz;
         dv[6] = -rec.z * fx; dv[7] = -rec.z * fy; dv[8] = -rec.z * fz;
 #pragma unroll
         for (int k = 0; k < 9; ++k) vir[k] += dv[k];
         my_slot = slot;
-        f3[0] = ix;
-        f3[1] = iy;
-        f3[2] = iz;
     }
-    // F_i (and the atom's virial): the queue is filled atom by atom, so each
-    // slot's pairs occupy consecutive lanes.  Every lane finds the mask of
-    // its segment and the segment is summed with warp reductions on 32-bit
-    // halves of the fixed-point values (|v| < 2^47, so the high parts of 32
-    // lanes cannot overflow); integer sums do not depend on how an atom's
-    // pairs were split over batches.
-    const int prev_slot = __shfl_up_sync(0xffffffffu, my_slot, 1);
-    const unsigned heads = __ballot_sync(0xffffffffu, lane < m && (lane == 0 || my_slot != prev_slot));
-    const unsigned valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
-    unsigned seg;
-    if (lane < m) {
-        const unsigned below = heads & (0xffffffffu >> (31 - lane));          // heads at or below this lane
-        const unsigned start = 1u << (31 - __clz(below));
-        const unsigned above = heads & ~(0xffffffffu >> (31 - lane));         // heads above this lane
-        const unsigned stop = above ? (above & (0u - above)) : 0u;            // lowest of them, or none
-        seg = (stop ? (stop - start) : (valid & ~(start - 1u)));
-    } else {
-        seg = ~valid;   // idle lanes form one group of their own
-    }
-    const bool leader = (seg & (0u - seg)) == (1u << lane);                    // lowest lane of the segment
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long x = f3[c];
-        const unsigned lo = __reduce_add_sync(seg, (unsigned)(x & 0x3FFFFF));
-        const int hi = __reduce_add_sync(seg, (int)(x >> 22));
-        if (leader && lane < m) sm.F[w][my_slot][c] += (long long)hi * 4194304ll + (long long)lo;
-    }
+    // The per-atom virial (when requested): the queue is filled atom by atom,
+    // so each slot's pairs occupy consecutive lanes.  Every lane finds the
+    // mask of its segment and the segment is summed with warp reductions on
+    // 32-bit halves of the fixed-point values (|v| < 2^47, so the high parts
+    // of 32 lanes cannot overflow); integer sums do not depend on how an
+    // atom's pairs were split over batches.
     if (want_vatom) {
+        const int prev_slot = __shfl_up_sync(0xffffffffu, my_slot, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane < m && (lane == 0 || my_slot != prev_slot));
+        const unsigned valid = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
+        unsigned seg;
+        if (lane < m) {
+            const unsigned below = heads & (0xffffffffu >> (31 - lane));          // heads at or below this lane
+            const unsigned start = 1u << (31 - __clz(below));
+            const unsigned above = heads & ~(0xffffffffu >> (31 - lane));         // heads above this lane
+            const unsigned stop = above ? (above & (0u - above)) : 0u;            // lowest of them, or none
+            seg = (stop ? (stop - start) : (valid & ~(start - 1u)));
+        } else {
+            seg = ~valid;   // idle lanes form one group of their own
+        }
+        const bool leader = (seg & (0u - seg)) == (1u << lane);                    // lowest lane of the segment
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
             const long long x = lane < m ? to_fix(dv[c], status) : 0;
@@ -221,16 +213,11 @@ __device__ __forceinline__ void drain(ForceSmem<N> &sm, int w, int lane, int &nq
     }
 }
 
-// Move a slot's accumulated F_i to the global accumulator and clear it.
+// Release a slot: write its atom's virial (when requested) and clear it.
 template <int N>
-__device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, int slot,
-                                           unsigned long long *Facc, int *status, float *vir_atom)
+__device__ __forceinline__ void flush_slot(ForceSmem<N> &sm, int w, int lane, int slot, float *vir_atom)
 {
     const int i = sm.atom[w][slot];
-    if (lane < 3 && i >= 0) {
-        atomicAdd(Facc + 3 * (size_t)i + lane, (unsigned long long)sm.F[w][slot][lane]);
-        sm.F[w][slot][lane] = 0;
-    }
     if (lane < 9) {
         if (vir_atom && i >= 0) vir_atom[9 * (size_t)i + lane] = (float)((double)sm.V[w][slot][lane] * kFixInv);
         sm.V[w][slot][lane] = 0;
@@ -346,7 +333,6 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
     if (lane < kSlots) sm.atom[w][lane] = -1;
-    if (lane < 3 * kSlots) sm.F[w][lane / 3][lane % 3] = 0;
     for (int k = lane; k < 9 * kSlots; k += 32) sm.V[w][k / 9][k % 9] = 0;
     const bool want_vatom = a.vir_atom != nullptr;
     {
@@ -394,7 +380,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
         const int slot = seq & (kSlots - 1);
         if (nq > 0 && sm.qseq[w][0] <= seq - kSlots) drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
-        flush_slot<N>(sm, w, lane, slot, a.Facc, a.status, a.vir_atom);
+        flush_slot<N>(sm, w, lane, slot, a.vir_atom);
         if (lane == 0) sm.atom[w][slot] = i;
 
         // this atom's g row and A rows were copied into shared memory while the
@@ -463,7 +449,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         cur = nxt;
     }  // atoms
     drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
-    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.Facc, a.status, a.vir_atom);
+    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.vir_atom);
 
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
