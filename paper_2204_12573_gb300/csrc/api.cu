@@ -172,6 +172,13 @@ int ensure_workspace(flr_ctx *ctx, int n)
     if (s == FLR_OK) s = dev_alloc(&ctx->scratch_out, N * 3, "workspace outputs");
     if (s == FLR_OK) s = dev_alloc(&ctx->ref_list, N, "workspace variance queue");
     if (s == FLR_OK) s = dev_alloc(&ctx->partials, (size_t)kMaxPartials * 13 + 16, "workspace partials");
+    // descriptor rows are written up to K only: their padding columns stay zero from here on
+    for (int r = 0; r < 2 && s == FLR_OK; ++r) {
+        s = cuda_fail(cudaMemset(ctx->D32[r], 0, sizeof(float) * N * D.kp32[r]), "workspace D32");
+        if (s == FLR_OK) s = cuda_fail(cudaMemset(ctx->Dhi[r], 0, sizeof(__nv_bfloat16) * N * D.kp64[r]), "workspace Dhi");
+        if (s == FLR_OK) s = cuda_fail(cudaMemset(ctx->Dlo[r], 0, sizeof(__nv_bfloat16) * N * D.kp64[r]), "workspace Dlo");
+    }
+    if (s == FLR_OK) s = cuda_fail(cudaDeviceSynchronize(), "workspace");
     if (s != FLR_OK) {
         free_workspace(ctx);
         return s;

@@ -263,7 +263,6 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         if (lane == 0) a.norm[i] = nrm;
 
         const int r = cur.row;
-        const int K = 4 * npairs;
         float *d32 = a.D32[reg] + (size_t)r * a.kp32[reg];
         __nv_bfloat16 *dh = a.bf16 ? a.Dhi[reg] + (size_t)r * a.kp64[reg] : nullptr;
         __nv_bfloat16 *dl = a.bf16 ? a.Dlo[reg] + (size_t)r * a.kp64[reg] : nullptr;
@@ -289,12 +288,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
                 }
             }
         }
-        for (int o = K + lane; o < a.kp32[reg]; o += 32) d32[o] = 0.f;
-        if (dh)
-            for (int o = K + lane; o < a.kp64[reg]; o += 32) {
-                dh[o] = __float2bfloat16_rn(0.f);
-                dl[o] = __float2bfloat16_rn(0.f);
-            }
+        // columns K.. of the rows are zero from allocation on and never written
         __syncwarp();
         cur = nxt;
     }  // atoms
