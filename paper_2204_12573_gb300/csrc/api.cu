@@ -410,6 +410,7 @@ int flr_create(const flr_params *p, int device, flr_ctx **out)
     }
     int s = dev_alloc(&c->status, 4, "status word");
     if (s == FLR_OK) s = dev_alloc(&c->ref_count, 1, "variance queue counter");
+    if (s == FLR_OK) s = dev_alloc(&c->sched, 4, "work counters");
     if (s == FLR_OK) s = dev_alloc(&c->md_sc, 8 + 256, "MD scalars");
     if (s == FLR_OK) s = dev_alloc(&c->md_totals, FLR_NTOTALS, "MD totals");
     if (s == FLR_OK) s = dev_alloc(&c->md_cnt, 2, "MD counters");
@@ -461,6 +462,7 @@ int flr_destroy(flr_ctx *c)
     cudaFree(c->tab_single);
     cudaFree(c->status);
     cudaFree(c->ref_count);
+    cudaFree(c->sched);
     cudaFree(c->md_sc);
     cudaFree(c->md_totals);
     cudaFree(c->md_cnt);

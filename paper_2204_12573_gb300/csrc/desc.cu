@@ -36,6 +36,8 @@ struct DescArgs {
     int bf16;                  // also write BF16 hi/lo rows
     float4 *pair_rec;          // [n][max_nbr] out: pairs inside r_cut (r_ij, j | s_j << 25)
     int32_t *pair_cnt;         // [n] out: their number
+    const int32_t *order;      // order in which atoms are taken (nullptr: by index)
+    int *sched;                // work counter, zero at launch
 };
 
 constexpr int kYStride = 20;   // padded row of staged harmonics (conflict-free float4 stores)
@@ -163,21 +165,22 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
     __shared__ __align__(16) DescSmem<N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float rc = a.rcut, rc2 = rc * rc;
-    // persistent warps: each CTA walks one contiguous block of atoms with its
-    // warps interleaved, so atoms in flight together are spatial neighbours
-    // and share most of their neighbours' positions in L1; each atom's
-    // scalars and first 64 list entries are loaded one iteration ahead
-    const int span = (int)(((long long)a.n + gridDim.x - 1) / gridDim.x);
-    const int i_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * span);
-    const int stride = kWarpsDesc;
-    int i = blockIdx.x * span + w;
-    DescPre cur = desc_preload(a, i, i_end, lane);
-    for (; i < i_end; i += stride) {
-        const DescPre nxt = desc_preload(a, i + stride, i_end, lane);
+    // persistent warps taking chunks of the atom sequence dynamically; each
+    // atom's scalars and first 64 list entries are loaded one atom ahead
+    WarpChunks wc;
+    wc.init(a.sched, a.n, lane);
+    int p = wc.pos();
+    int i = p < a.n ? (a.order ? __ldg(a.order + p) : p) : a.n;
+    DescPre cur = desc_preload(a, i, a.n, lane);
+    int p2 = a.n, i2 = a.n;
+    DescPre nxt;
+    for (; p < a.n; p = p2, i = i2, cur = nxt, wc.advance(lane)) {
+        p2 = wc.peek();
+        i2 = p2 < a.n ? (a.order ? __ldg(a.order + p2) : p2) : a.n;
+        nxt = desc_preload(a, i2, a.n, lane);
         const int g = cur.g;
         if (g < 0) {
             if (lane == 0) a.norm[i] = 0.f;
-            cur = nxt;
             continue;
         }
         const int cls = group_cls(g);
@@ -290,7 +293,6 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         }
         // columns K.. of the rows are zero from allocation on and never written
         __syncwarp();
-        cur = nxt;
     }  // atoms
 }
 
@@ -353,6 +355,13 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.bf16 = ctx->p.precision == FLR_PREC_BF16X3;
     a.pair_rec = nl->pair_rec;
     a.pair_cnt = nl->pair_cnt;
+    a.order = nullptr;
+    a.sched = ctx->sched;
+    if (n <= 0) return FLR_OK;
+    {
+        const cudaError_t e = cudaMemsetAsync(ctx->sched, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "descriptor work counter");
+    }
     if (ctx->dims.N == 8) {
         const int grid = persistent_grid(k_desc<8>, kWarpsDesc * 32, ctx->num_sms, (n + kWarpsDesc - 1) / kWarpsDesc);
         k_desc<8><<<grid, kWarpsDesc * 32, 0, st>>>(a);

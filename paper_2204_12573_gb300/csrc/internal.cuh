@@ -136,6 +136,7 @@ struct flr_ctx {
     float sigma_norm[flr::kGroups];    // largest eigenvalue of each group's Sigma block (power iteration)
     int32_t *ref_list;                 // [ws_n] atoms queued for the FP64 variance
     int *ref_count;                    // device counter of ref_list
+    int *sched;                        // device work counters of the per-atom kernels [4]
     double *md_sc;                     // MD scalars: [0] xi, [1] eta, [2] KE, [3] scale, [8..8+256) KE partials
     double *md_totals;                 // totals of flr_md_step when the caller passes none
     int *md_cnt;                       // [2] uncertainty and coordination counts
@@ -266,6 +267,57 @@ inline int persistent_grid(K kernel, int threads, int num_sms, long long work_bl
     return (int)(g < 1 ? 1 : g);
 }
 constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
+
+// Dynamic work distribution for the per-atom kernels: a warp takes
+// kWarpChunk consecutive positions of the atom sequence at a time from a
+// global counter (zeroed before the launch) and claims its next chunk one
+// chunk ahead, so the atom after the current one is always known and can be
+// prefetched.  Warps that run into expensive atoms (two-species
+// environments, surface layers) take fewer chunks, so the kernel ends when
+// the work does instead of when the slowest fixed block does.
+constexpr int kWarpChunk = 16;
+struct WarpChunks {
+    int n, nchunks, cur, nxt, k;
+    int *counter;
+    __device__ __forceinline__ void init(int *ctr, int n_, int lane)
+    {
+        counter = ctr;
+        n = n_;
+        nchunks = (n_ + kWarpChunk - 1) / kWarpChunk;
+        k = 0;
+        int c0 = 0, c1 = 0;
+        if (lane == 0) {
+            c0 = atomicAdd(ctr, 1);
+            c1 = atomicAdd(ctr, 1);
+        }
+        cur = __shfl_sync(0xffffffffu, c0, 0);
+        nxt = __shfl_sync(0xffffffffu, c1, 0);
+    }
+    // sequence position of the current atom (n when the warp is done)
+    __device__ __forceinline__ int pos() const { return cur < nchunks ? cur * kWarpChunk + k : n; }
+    // the position after the current one
+    __device__ __forceinline__ int peek() const
+    {
+        if (cur >= nchunks) return n;
+        const int p = cur * kWarpChunk + k + 1;
+        if (k + 1 < kWarpChunk && p < n) return p;
+        return nxt < nchunks ? nxt * kWarpChunk : n;
+    }
+    // move to peek(); the whole warp calls it
+    __device__ __forceinline__ void advance(int lane)
+    {
+        const int p = cur * kWarpChunk + k + 1;
+        if (cur < nchunks && k + 1 < kWarpChunk && p < n) {
+            ++k;
+            return;
+        }
+        cur = nxt;
+        k = 0;
+        int c = nchunks;
+        if (lane == 0 && cur < nchunks) c = atomicAdd(counter, 1);
+        nxt = __shfl_sync(0xffffffffu, c, 0);
+    }
+};
 
 // ---- shared device helpers ----
 
