@@ -54,6 +54,7 @@ struct ForceArgs {
     const float4 *pair_rec;    // [n][max_nbr] pairs inside r_cut from the descriptor kernel
     const int32_t *pair_cnt;   // [n]
     const int32_t *tab[2];     // compact index -> channel pair (a | b << 8), per region
+    int *sched;                // work counter, zero at launch
     int *status;
 };
 
@@ -350,16 +351,18 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     __syncthreads();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
-    // each CTA walks one contiguous block of atoms, its warps interleaved
-    const int span = (int)(((long long)a.n + gridDim.x - 1) / gridDim.x);
-    const int i_end = (int)min((long long)a.n, (long long)(blockIdx.x + 1) * span);
-    const int stride = kWarpsForce;
-    int i = blockIdx.x * span + w;
-    AtomPre cur = preload(a, i, i_end, lane);
-    rows_async<N>(a, cur, i, i_end, sm.gr[w], sm.A[w], lane);
-
-    for (; i < i_end; i += stride) {
-        const AtomPre nxt = preload(a, i + stride, i_end, lane);
+    // warps take chunks of consecutive atoms dynamically; the next atom's
+    // scalars are loaded, and its g and A rows copied, one atom ahead
+    WarpChunks wc;
+    wc.init(a.sched, a.n, lane);
+    int i = wc.pos();
+    AtomPre cur = preload(a, i, a.n, lane);
+    rows_async<N>(a, cur, i, a.n, sm.gr[w], sm.A[w], lane);
+    int i2 = a.n;
+    AtomPre nxt;
+    for (; i < a.n; i = i2, cur = nxt, wc.advance(lane)) {
+        i2 = wc.peek();
+        nxt = preload(a, i2, a.n, lane);
         const int g = cur.g;
         if (g < 0 || !(cur.nrm > 0.f)) {
             // no environment inside r_cut: no forces from this centre
@@ -369,8 +372,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
                 if (a.sigma) a.sigma[i] = 0.f;
             }
             if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
-            cur = nxt;
-            rows_async<N>(a, cur, i + stride, i_end, sm.gr[w], sm.A[w], lane);
+            rows_async<N>(a, nxt, i2, a.n, sm.gr[w], sm.A[w], lane);
             continue;
         }
         const int cls = group_cls(g), reg = group_region(g);
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         }
         __syncwarp();
         // the g and A buffers are free: start copying the next atom's rows
-        rows_async<N>(a, nxt, i + stride, i_end, sm.gr[w], sm.A[w], lane);
+        rows_async<N>(a, nxt, i2, a.n, sm.gr[w], sm.A[w], lane);
 
         // queue the atom's pairs inside r_cut (recorded by the descriptor kernel)
         const int np = cur.np;
@@ -446,7 +448,6 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
             drain<N>(sm, w, lane, nq, false, rc, a.Facc, a.status, vir, want_vatom);
         }
         ++seq;
-        cur = nxt;
     }  // atoms
     drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
     for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.vir_atom);
@@ -701,6 +702,11 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.tab[0] = ctx->tab_full;
     a.tab[1] = ctx->tab_single;
     a.status = ctx->status;
+    a.sched = ctx->sched + 1;
+    {
+        const cudaError_t e = cudaMemsetAsync(a.sched, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "force work counter");
+    }
     const long long work = (n + kWarpsForce - 1) / kWarpsForce;
     int grid;
     if (ctx->dims.N == 8) {
