@@ -282,14 +282,15 @@ __device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int i_end,
     p.nrm = 0.f;
     p.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < i_end) {
-        // read-only loads (ld.global.nc): free to move across the force atomics
+        // read-only loads (ld.global.nc): free to move across the force atomics.
+        // All five are issued at once, none waits for another: the pair count
+        // and record row exist for every atom (lane < 32 <= max_nbr) and are
+        // used only when the atom has pairs, and only below the count.
         p.g = __ldg(a.group + i);
         p.row = __ldg(a.row + i);
         p.nrm = __ldg(a.norm + i);
-        if (p.g >= 0 && p.nrm > 0.f) {
-            p.np = __ldg(a.pair_cnt + i);
-            if (lane < p.np) p.r0 = __ldg(a.pair_rec + (size_t)i * a.max_nbr + lane);
-        }
+        p.np = __ldg(a.pair_cnt + i);
+        p.r0 = __ldg(a.pair_rec + (size_t)i * a.max_nbr + lane);
     }
     return p;
 }
@@ -419,7 +420,8 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         }
         float *sA = sm.A[w];   // A rows of the class's channels (already copied)
         float *ws = sm.W[w] + slot * kWSlot;
-        for (int k = lane; k < 256; k += 32) ws[k] = 0.f;   // both species blocks of the slot
+        // w_dense writes every channel of the atom's class; pairs only read
+        // the species blocks of that class, so the slot needs no clearing
         __syncwarp();
         {
             const int lm = lane & 15, half = lane >> 4;
