@@ -301,6 +301,7 @@ struct RowArgs {
     const int32_t *struct_of;
     const float4 *shift;       // [n_structs][kShiftCodes][2] image shifts, FP32 hi and lo
     long long nbins;           // bins of all structures
+    int *sched;                // work counter, zero at launch
     float rc2;
     double rc2d;
     int32_t *entries, *count, *group;
@@ -484,7 +485,7 @@ __device__ __forceinline__ void row_general(const RowArgs &a, int kq, int lane, 
 constexpr int kBuildWarps = 8;
 constexpr int kTile = 320;   // stencil candidates a warp stages for one bin
 
-// One warp per bin (bins in order, spread over the warps of the grid).  For a
+// One warp per bin (warps take runs of consecutive bins from a counter).  For a
 // bin whose stencil candidates all carry image 0, image shifts inside
 // [-2, 2]^3 and a valid species (always the case for positions wrapped into
 // the cell, as in MD), the warp stages the candidate set once: each
@@ -501,8 +502,11 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_bins(RowArgs a)
     __shared__ int s_start[kBuildWarps][32], s_excl[kBuildWarps][32], s_shift[kBuildWarps][32];
     __shared__ __align__(16) float4 s_cand[kBuildWarps][kTile];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const long long nwarps = (long long)gridDim.x * kBuildWarps;
-    for (long long b = (long long)blockIdx.x * kBuildWarps + wl; b < a.nbins; b += nwarps) {
+    // dynamic runs of bins: occupied bins cluster in z (the innermost bin
+    // index), so a fixed stride would give some warps only empty bins
+    WarpChunks wc;
+    wc.init(a.sched, (int)a.nbins, lane);
+    for (int b = wc.pos(); b < (int)a.nbins; wc.advance(lane), b = wc.pos()) {
         const int k0 = a.bin_start[b], k1 = a.bin_start[b + 1];
         if (k1 <= k0) continue;
         const int sidx = structure_of(a.struct_of, a.bin_atoms[k0]);
@@ -510,7 +514,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_bins(RowArgs a)
         const float4 *img_shift = a.shift + 2 * kShiftCodes * sidx;
         const int span[3] = {2 * P.R[0] + 1, 2 * P.R[1] + 1, 2 * P.R[2] + 1};
         const int n_stencil = span[0] * span[1] * span[2];
-        const int bin = (int)(b - P.bin_base);
+        const int bin = b - (int)P.bin_base;
         const int bi[3] = {bin / (P.nb[1] * P.nb[2]), (bin / P.nb[2]) % P.nb[1], bin % P.nb[2]};
         const float4 o4 = a.pos_bin[k0];   // reference point of the staged coordinates
         float4 *cand = s_cand[wl];
@@ -1079,6 +1083,11 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.flags = nl->flags;
     r.status = ctx->status;
     r.nbins = nbins;
+    r.sched = ctx->sched + 2;
+    {
+        const cudaError_t e = cudaMemsetAsync(r.sched, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "list build work counter");
+    }
     k_build_bins<<<persistent_grid(k_build_bins, kBuildWarps * 32, ctx->num_sms, (nbins + kBuildWarps - 1) / kBuildWarps),
                    kBuildWarps * 32, 0, st>>>(r);
 
@@ -1213,6 +1222,7 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     Plan *plan_d = reinterpret_cast<Plan *>(take(sizeof(Plan)));
     GroupTab *gtab = reinterpret_cast<GroupTab *>(take(sizeof(GroupTab)));
     float4 *shift_d = reinterpret_cast<float4 *>(take(sizeof(float4) * 2 * kShiftCodes));
+    int *sched = reinterpret_cast<int *>(take(sizeof(int)));
     if (q > static_cast<unsigned char *>(base) + kNoAllocBytes) {
         set_error("flr_build_neighbors_noalloc: scratch layout exceeds the array");
         return FLR_EINVAL;
@@ -1305,6 +1315,9 @@ extern "C" int flr_build_neighbors_noalloc(const flr_system *sys, double r_list,
     r.flags = flags;
     r.status = status;
     r.nbins = nbins;
+    r.sched = sched;
+    s = cuda_fail(cudaMemsetAsync(sched, 0, sizeof(int), st), "list build work counter");
+    if (s != FLR_OK) return s;
     k_build_bins<<<persistent_grid(k_build_bins, kBuildWarps * 32, num_sms, (nbins + kBuildWarps - 1) / kBuildWarps),
                    kBuildWarps * 32, 0, st>>>(r);
     s = cuda_fail(cudaGetLastError(), "neighbour build (no allocation)");
