@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
         const int slot = seq & (kSlots - 1);
         if (nq > 0 && sm.qseq[w][0] <= seq - kSlots) drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
-        flush_slot<N>(sm, w, lane, slot, a.vir_atom);
+        if (want_vatom) flush_slot<N>(sm, w, lane, slot, a.vir_atom);   // otherwise the slot holds nothing to write
         if (lane == 0) sm.atom[w][slot] = i;
 
         // this atom's g row and A rows were copied into shared memory while the
@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
         ++seq;
     }  // atoms
     drain<N>(sm, w, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
-    for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.vir_atom);
+    if (want_vatom)
+        for (int s = 0; s < kSlots; ++s) flush_slot<N>(sm, w, lane, s, a.vir_atom);
 
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
