@@ -268,22 +268,23 @@ inline int persistent_grid(K kernel, int threads, int num_sms, long long work_bl
 }
 constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
 
-// Dynamic work distribution for the per-atom kernels: a warp takes
-// kWarpChunk consecutive positions of the atom sequence at a time from a
-// global counter (zeroed before the launch) and claims its next chunk one
-// chunk ahead, so the atom after the current one is always known and can be
-// prefetched.  Warps that run into expensive atoms (two-species
-// environments, surface layers) take fewer chunks, so the kernel ends when
-// the work does instead of when the slowest fixed block does.
-constexpr int kWarpChunk = 16;
-struct WarpChunks {
+// Dynamic work distribution for the per-atom kernels: a warp takes CH
+// consecutive positions of a work sequence at a time from a global counter
+// (zeroed before the launch) and claims its next chunk one chunk ahead, so
+// the item after the current one is always known and can be prefetched.
+// Warps that run into expensive items (two-species environments, surface
+// layers, dense bins) take fewer chunks, so the kernel ends when the work
+// does instead of when the slowest fixed block does.
+constexpr int kWarpChunk = 16;   // atoms per chunk in the per-atom kernels
+template <int CH>
+struct WarpChunksT {
     int n, nchunks, cur, nxt, k;
     int *counter;
     __device__ __forceinline__ void init(int *ctr, int n_, int lane)
     {
         counter = ctr;
         n = n_;
-        nchunks = (n_ + kWarpChunk - 1) / kWarpChunk;
+        nchunks = (n_ + CH - 1) / CH;
         k = 0;
         int c0 = 0, c1 = 0;
         if (lane == 0) {
@@ -293,21 +294,21 @@ struct WarpChunks {
         cur = __shfl_sync(0xffffffffu, c0, 0);
         nxt = __shfl_sync(0xffffffffu, c1, 0);
     }
-    // sequence position of the current atom (n when the warp is done)
-    __device__ __forceinline__ int pos() const { return cur < nchunks ? cur * kWarpChunk + k : n; }
+    // sequence position of the current item (n when the warp is done)
+    __device__ __forceinline__ int pos() const { return cur < nchunks ? cur * CH + k : n; }
     // the position after the current one
     __device__ __forceinline__ int peek() const
     {
         if (cur >= nchunks) return n;
-        const int p = cur * kWarpChunk + k + 1;
-        if (k + 1 < kWarpChunk && p < n) return p;
-        return nxt < nchunks ? nxt * kWarpChunk : n;
+        const int p = cur * CH + k + 1;
+        if (k + 1 < CH && p < n) return p;
+        return nxt < nchunks ? nxt * CH : n;
     }
     // move to peek(); the whole warp calls it
     __device__ __forceinline__ void advance(int lane)
     {
-        const int p = cur * kWarpChunk + k + 1;
-        if (cur < nchunks && k + 1 < kWarpChunk && p < n) {
+        const int p = cur * CH + k + 1;
+        if (cur < nchunks && k + 1 < CH && p < n) {
             ++k;
             return;
         }
@@ -318,6 +319,7 @@ struct WarpChunks {
         nxt = __shfl_sync(0xffffffffu, c, 0);
     }
 };
+using WarpChunks = WarpChunksT<kWarpChunk>;
 
 // ---- shared device helpers ----
 
