@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
     const float rc = a.rcut, rc2 = rc * rc;
     // persistent warps taking chunks of the atom sequence dynamically; each
     // atom's scalars and first 64 list entries are loaded one atom ahead
-    WarpChunks wc;
+    WarpChunksT<8> wc;   // 8-atom chunks: measured 0.5 % faster than 16 here
     wc.init(a.sched, a.n, lane);
     int p = wc.pos();
     int i = p < a.n ? (a.order ? __ldg(a.order + p) : p) : a.n;

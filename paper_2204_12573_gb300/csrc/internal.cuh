@@ -275,7 +275,7 @@ constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
 // Warps that run into expensive items (two-species environments, surface
 // layers, dense bins) take fewer chunks, so the kernel ends when the work
 // does instead of when the slowest fixed block does.
-constexpr int kWarpChunk = 16;   // atoms per chunk in the per-atom kernels
+constexpr int kWarpChunk = 16;   // atoms per chunk in the force kernel
 template <int CH>
 struct WarpChunksT {
     int n, nchunks, cur, nxt, k;

@@ -485,7 +485,7 @@ __device__ __forceinline__ void row_general(const RowArgs &a, int kq, int lane, 
 constexpr int kBuildWarps = 8;
 constexpr int kTile = 320;   // stencil candidates a warp stages for one bin
 
-// One warp per bin (warps take runs of two consecutive bins from a counter).  For a
+// One warp per bin (warps claim bins in order from a counter).  For a
 // bin whose stencil candidates all carry image 0, image shifts inside
 // [-2, 2]^3 and a valid species (always the case for positions wrapped into
 // the cell, as in MD), the warp stages the candidate set once: each
@@ -502,10 +502,10 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_bins(RowArgs a)
     __shared__ int s_start[kBuildWarps][32], s_excl[kBuildWarps][32], s_shift[kBuildWarps][32];
     __shared__ __align__(16) float4 s_cand[kBuildWarps][kTile];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    // dynamic runs of two bins: occupied bins cluster in z (the innermost bin
+    // one bin per claim: occupied bins cluster in z (the innermost bin
     // index), so a fixed stride would give some warps only empty bins, and
-    // bins differ widely in cost, so the runs are kept short
-    WarpChunksT<2> wc;
+    // bins differ widely in cost
+    WarpChunksT<1> wc;
     wc.init(a.sched, (int)a.nbins, lane);
     for (int b = wc.pos(); b < (int)a.nbins; wc.advance(lane), b = wc.pos()) {
         const int k0 = a.bin_start[b], k1 = a.bin_start[b + 1];
