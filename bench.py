@@ -9,8 +9,10 @@ plus a device-side displacement trigger).  One step = half kick + drift +
 
 Headline `value`: M atom-steps/s with the quadratic forms on the tensor
 cores in 3xBF16 (FP32 accumulate); `plain_fp32` gives the same run with the
-FP32 SIMT quadratic forms, and `force_err_ev_per_A` the force error of each
-against the FP64 oracle on sampled atoms.  Inputs are larger than L2 (the
+FP32 SIMT quadratic forms, `compaction_off` the 3xBF16 run with every atom
+at the two-species descriptor size (no species-block compaction), and
+`force_err_ev_per_A` the force error of each precision against the FP64
+oracle on sampled atoms.  Inputs are larger than L2 (the
 neighbour list alone is 545 MB), so no L2 flush is needed between steps.
 
 `--impl reference` times the FP64 CPU oracle on bounded samples of the same
@@ -366,6 +368,34 @@ def run_ours(args):
     value = job_throughput(world, n, args.steps, ms_mix)
     value_fp32 = job_throughput(world, n, args.steps, ms_fp32)
 
+    # compaction off: every atom takes the two-species (d = 544) descriptor,
+    # the paper's method without its species-block compaction (own context)
+    def timed_no_compaction(steps):
+        ffn = F.FlareGB(precision="bf16x3", max_nbr=64, compaction=False)
+        ffn.set_model(beta, sigma)
+        nln = ffn.nbrlist(n)
+        sysg.pos.copy_(torch.as_tensor(pos0, device="cuda"))
+        vel.copy_(torch.as_tensor(vel0, device="cuda"))
+        F.build_neighbors(ffn, sysg, nln)
+        stn = F.MDState(sysg, vel)
+        F.md_step(ffn, stn, nln, args.warmup, out)
+        ffn.sync()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        F.md_step(ffn, stn, nln, steps, out)
+        e1.record(stream)
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist)
+        ffn.sync()
+        del nln, ffn
+        torch.cuda.synchronize()
+        return ms
+
+    nc_steps = max(1, min(args.steps, 10))
+    ms_nc = timed_no_compaction(nc_steps)
+    value_nc = job_throughput(world, n, nc_steps, ms_nc)
+
     # force error of each precision against the FP64 oracle on sampled atoms (same positions)
     ff.set_precision("bf16x3")
     F.build_neighbors(ff, sysg, nl)
@@ -470,6 +500,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16x3", "data": "synthetic",
                 "config": _config(n, "3xBF16 tcgen05 quadratic forms, FP32 elsewhere, FP64 totals"),
                 "plain_fp32": {"value": round(value_fp32, 3), "ms_per_step": round(ms_fp32 / args.steps, 4)},
+                "compaction_off": {"value": round(value_nc, 3), "ms_per_step": round(ms_nc / nc_steps, 4),
+                                   "steps": nc_steps, "note": "3xBF16, every atom at d = 544"},
                 "force_err_ev_per_A": ferr,
                 "errors_vs_oracle": {"sample": err_sample, **errs},
                 "rebuilds_in_timed_steps": rebuild_count,
