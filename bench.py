@@ -396,6 +396,28 @@ def run_ours(args):
     ms_nc = timed_no_compaction(nc_steps)
     value_nc = job_throughput(world, n, nc_steps, ms_nc)
 
+    # sparse-GP -> (beta, Sigma) mapping on the device (once per model, not per step)
+    def timed_sgp_mapping(n_s=2048, reps=3):
+        ffm = F.FlareGB(precision="fp32")
+        g = torch.Generator(device="cuda").manual_seed(5)
+        D = torch.randn((n_s, ffm.d_full), dtype=torch.float64, device="cuda", generator=g)
+        D /= D.norm(dim=1, keepdim=True)
+        alpha = torch.randn(n_s, dtype=torch.float64, device="cuda", generator=g)
+        K = 0.7 * D @ D.T + 1e-3 * torch.eye(n_s, dtype=torch.float64, device="cuda")
+        ffm.map_sgp(0, D, alpha, K, 0.7)          # warm-up
+        times = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ffm.map_sgp(0, D, alpha, K, 0.7)
+            times.append((time.perf_counter() - t0) * 1e3)
+        d_full = ffm.d_full
+        del ffm
+        return {"n_sparse": n_s, "d": d_full, "ms": round(float(np.median(times)), 2),
+                "note": "flr_map_sgp: FP64 Cholesky of K_SS, X = L^-1 D_S, beta and Sigma products, "
+                        "copy to host and model upload; wall clock, median of 3"}
+    sgp_map = timed_sgp_mapping() if rank == 0 else None
+
     # force error of each precision against the FP64 oracle on sampled atoms (same positions)
     ff.set_precision("bf16x3")
     F.build_neighbors(ff, sysg, nl)
@@ -502,6 +524,7 @@ def run_ours(args):
                 "plain_fp32": {"value": round(value_fp32, 3), "ms_per_step": round(ms_fp32 / args.steps, 4)},
                 "compaction_off": {"value": round(value_nc, 3), "ms_per_step": round(ms_nc / nc_steps, 4),
                                    "steps": nc_steps, "note": "3xBF16, every atom at d = 544"},
+                "sgp_mapping": sgp_map,
                 "force_err_ev_per_A": ferr,
                 "errors_vs_oracle": {"sample": err_sample, **errs},
                 "rebuilds_in_timed_steps": rebuild_count,

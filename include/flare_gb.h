@@ -205,6 +205,31 @@ int flr_set_precision(flr_ctx *ctx, int32_t precision);
  * and the FP32 / BF16-hi/lo copies on the device.  Synchronous. */
 int flr_set_model(flr_ctx *ctx, int32_t species, const double *beta, const double *sigma);
 
+/* Map a sparse GP of central species `species` onto the quadratic forms and
+ * install it (Sec. V-B, "Mapped Sparse GP"; Eq. 1 and Eq. 2 reordered):
+ *   beta  = sig2 * D_S^T diag(alpha) D_S,
+ *   Sigma = sig2 * I - sig2^2 * D_S^T K_SS^{-1} D_S,
+ * so that d^T beta d equals the Eq. 1 sum over the sparse set
+ * sig2 * sum_s alpha_s (d . d_s)^2 and d^T Sigma d the Eq. 2 variance
+ * sig2 - sig2^2 k^T K_SS^{-1} k with k_s = d . d_s (unit d).  All in FP64 on
+ * the device: Cholesky K_SS = L L^T, X = L^{-1} D_S, Sigma from X^T X.
+ *   d_sparse: DEVICE double[n_sparse][d_full], the sparse set's normalized
+ *             descriptor rows in the ABI component order (as returned by
+ *             flr_compute_descriptors);
+ *   alpha:    DEVICE double[n_sparse], the mean weights;
+ *   k_ss:     DEVICE double[n_sparse][n_sparse], symmetric positive
+ *             definite (only its lower triangle is read);
+ *   sig2:     the signal variance sigma^2 > 0;
+ *   beta_out, sigma_out: optional DEVICE double[d_full][d_full] copies of
+ *             the mapped matrices (NULL to skip).
+ * The inputs are not modified; temporary device memory of
+ * 8 (n_sparse^2 + n_sparse d_full + 2 d_full^2) bytes is allocated and freed.
+ * Then behaves as flr_set_model with the mapped matrices (its checks apply).
+ * FLR_EINVAL if K_SS is not positive definite (a Cholesky pivot <= 0).
+ * Synchronous on `stream`. */
+int flr_map_sgp(flr_ctx *ctx, int32_t species, int32_t n_sparse, const double *d_sparse, const double *alpha,
+                const double *k_ss, double sig2, double *beta_out, double *sigma_out, flr_stream_t stream);
+
 /* Choose the variance evaluation (FLR_VAR_*) for models set afterwards and
  * re-upload the models already set.  FLR_EINVAL if a Sigma block is not
  * positive semi-definite (its Cholesky factorization fails even after a

@@ -45,7 +45,7 @@ EXPORTED = [
     "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
     "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
     "flr_bytes_per_atom", "flr_server_create", "flr_server_submit", "flr_server_poll", "flr_server_stats_read",
-    "flr_server_destroy", "flr_set_variance_mode",
+    "flr_server_destroy", "flr_set_variance_mode", "flr_map_sgp",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
@@ -134,6 +134,7 @@ def lib():
             "flr_set_precision": (ctypes.c_int, [P, ctypes.c_int32]),
             "flr_set_variance_mode": (ctypes.c_int, [P, ctypes.c_int32]),
             "flr_set_model": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
+            "flr_map_sgp": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_double, P, P, P]),
             "flr_nbrlist_create": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(P)]),
             "flr_nbrlist_destroy": (ctypes.c_int, [P]),
             "flr_nbrlist_view": (ctypes.c_int, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),

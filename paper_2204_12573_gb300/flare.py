@@ -103,6 +103,24 @@ class FlareGB:
             N.check(self.lib.flr_set_model(self.handle, s, beta[s].ctypes.data_as(ctypes.c_void_p),
                                            sigma[s].ctypes.data_as(ctypes.c_void_p)))
 
+    def map_sgp(self, species, d_sparse, alpha, k_ss, sig2, stream=None):
+        """Install the mapped sparse GP of one central species (Sec. V-B,
+        Eq. 1 and Eq. 2): d_sparse [n_S, d_full], alpha [n_S], k_ss [n_S, n_S],
+        float64 CUDA tensors.  Returns the mapped (beta, Sigma) as float64
+        CUDA tensors [d_full, d_full]."""
+        import torch
+        d_sparse = d_sparse.to(device="cuda", dtype=torch.float64).contiguous()
+        alpha = alpha.to(device="cuda", dtype=torch.float64).contiguous()
+        k_ss = k_ss.to(device="cuda", dtype=torch.float64).contiguous()
+        n_s = int(d_sparse.shape[0])
+        if d_sparse.shape != (n_s, self.d_full) or alpha.shape != (n_s,) or k_ss.shape != (n_s, n_s):
+            raise ValueError("map_sgp: shapes must be d_sparse [n_S, d_full], alpha [n_S], k_ss [n_S, n_S]")
+        beta = torch.empty((self.d_full, self.d_full), dtype=torch.float64, device="cuda")
+        sigma = torch.empty_like(beta)
+        N.check(self.lib.flr_map_sgp(self.handle, int(species), n_s, _ptr(d_sparse), _ptr(alpha), _ptr(k_ss),
+                                     float(sig2), _ptr(beta), _ptr(sigma), _stream(stream)))
+        return beta, sigma
+
     def nbrlist(self, n_atoms):
         return NbrList(self, n_atoms)
 
