@@ -53,7 +53,7 @@ struct GroupTab {
     int tiles_simt[kGroups + 1];  // prefix of SIMT tiles (M-tiles x N-tiles)
     int tiles_tc[kGroups + 1];    // prefix of tensor-core M-tiles (each covers all its column chunks)
     int n_isolated;         // atoms with an empty list
-    int max_count;          // longest neighbour row seen (before clipping)
+    int max_count;          // longest overflowing neighbour row (before clipping); 0 without overflow
 };
 
 struct Plan {

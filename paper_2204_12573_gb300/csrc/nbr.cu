@@ -332,8 +332,12 @@ __device__ __forceinline__ void finish_row(const RowArgs &a, int i, int cnt, uns
 #pragma unroll
     for (int o = 16; o; o >>= 1) smask |= __shfl_xor_sync(0xffffffffu, smask, o);
     if (lane == 0) {
-        if (cnt > a.max_nbr) atomicOr(a.status, kErrOverflow);
-        atomicMax(&a.gtab->max_count, cnt);
+        if (cnt > a.max_nbr) {
+            // the longest row is only reported with the overflow; one atomic on
+            // a single address per atom would serialize every row in one L2 slice
+            atomicOr(a.status, kErrOverflow);
+            atomicMax(&a.gtab->max_count, cnt);
+        }
         a.count[i] = min(cnt, a.max_nbr);
         int g = -1;
         if (cnt > 0) {
