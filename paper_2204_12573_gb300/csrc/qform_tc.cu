@@ -7,18 +7,19 @@
 //   * 3xBF16: both operands split into BF16 hi + lo parts; the K loop runs
 //     three times (hi.hi, hi.lo, lo.hi), the lo.lo term is dropped, so the
 //     product keeps about 16 significant bits (kind::f16, FP32 accumulate).
-// Operand tiles arrive by TMA (128-byte swizzle) into a 4-stage shared
+// Operand tiles arrive by TMA (128-byte swizzle) into a 3-stage shared
 // memory ring guarded by mbarriers; one thread issues the MMAs, which
-// accumulate in tensor memory (288 of 512 columns).  Eight epilogue warps
-// (two per TMEM lane quarter, each taking alternate 16-column groups) read
-// the accumulator back with tcgen05.ld, one atom (row) per thread:
+// accumulate in tensor memory (288 of 512 columns).  Twelve epilogue warps
+// (three per TMEM lane quarter, each taking every third 16-column group)
+// read the accumulator back with tcgen05.ld, one atom (row) per thread:
 //   E = d . (beta d),  V = d . (Sigma d),  sigma = sqrt(V),
 //   g = dE/dB = (2/||B||)(beta d - E d)
 // and store E, V, sigma per atom and g as the row the force kernel needs,
 // so P itself never goes to memory.  A one-species tile (d = 144) is a
-// single 288-column chunk; a two-species tile (d = 544) takes four chunks
-// of the same CTA, the partial E and V living in the epilogue registers
-// and the beta d columns parked in the g row until E is final.
+// single 288-column chunk whose beta d columns are parked in the free TMEM
+// columns 288..431 until E is final; a two-species tile (d = 544) takes
+// four chunks of the same CTA, the partial E and V living in the epilogue
+// registers and the beta d columns parked in the g row.
 //
 // Every wait on an mbarrier has a deadline (about 2 s of %globaltimer); on
 // expiry the kernel records FLR_ETIMEOUT in the status word, stops issuing
@@ -36,14 +37,15 @@ namespace {
 constexpr int BM = 128;
 constexpr int NH = 144;            // N of one MMA
 constexpr int NC = 2 * NH;         // columns per chunk (one accumulator)
-constexpr int kStages = 2;          // two stages keep the MMAs fed and leave L1 room for prefetched rows
+constexpr int kStages = 3;          // three 52 KB stages in flight (measured: 2 and 4 are slower; 4 leaves the epilogue little L1)
 constexpr int kTileA = BM * 128;   // bytes (128-byte rows)
 constexpr int kTileB = NC * 128;
 constexpr int kStageBytes = kTileA + kTileB;
 constexpr int kTmemCols = 512;
 constexpr int kSubs = 3;            // epilogue warps per TMEM lane quarter (each takes every 3rd 16-column group)
-constexpr int kParkCols = 144;      // widest one-species row parked in shared memory
-constexpr int kParkStride = kParkCols + 4;
+constexpr int kParkCols = 144;      // widest one-species row parked in tensor memory
+constexpr int kParkCol0 = NC;       // first TMEM column of the park (after the accumulator)
+static_assert(kParkCol0 + kParkCols <= 512, "accumulator and park must fit in 512 TMEM columns");
 constexpr int kParkGroups = (kParkCols / 16 + kSubs - 1) / kSubs;   // 16-column groups per epilogue thread
 constexpr int kEpiWarps = 4 * kSubs;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -153,6 +155,22 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// store 16 columns of this warp's TMEM lane quarter (one row per thread);
+// tmem_wait_st makes them visible to later tcgen05.ld of the same thread
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+          "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 {
@@ -276,7 +294,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
     // sets, double-buffered by tile
     float4 *evx_buf = reinterpret_cast<float4 *>(base + kStages * kStageBytes + 128);
     // beta d of one-species tiles, parked until E is known (padded rows: conflict-free float4 access)
-    float *park = reinterpret_cast<float *>(base + kStages * kStageBytes + 128 + 2 * kSubs * BM * sizeof(float4));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
@@ -414,15 +431,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
         // row per thread) and every kSubs-th 16-column group starting at sub.
         // The kSubs partial E and V of a row are combined through shared
         // memory (double-buffered by tile, guarded by a bounded mbarrier wait).
-        // One-species tiles park beta d in shared memory, so the accumulator is
-        // released as soon as it is read and g = s2 (beta d - E d) is formed
-        // without a round trip through global memory; two-species tiles (four
-        // column chunks) park beta d in the g row and fix it up afterwards.
+        // One-species tiles park beta d in tensor memory beside the accumulator
+        // (columns kParkCol0..), so the accumulator is released as soon as it
+        // is read and g = s2 (beta d - E d) is formed without a round trip
+        // through global memory; two-species tiles (four column chunks) park
+        // beta d in the g row and fix it up afterwards.
         const int qw = warp & 3;                // TMEM lane quarter of this warp
         const int sub = (warp - 2) >> 2;        // which column groups
         const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
         const int rloc = qw * 32 + lane;        // row within the tile
-        float *prow = park + (size_t)rloc * kParkStride;
         int it = 0;
         int tl = 0;                             // tiles done by this CTA
         bool alive = true;
@@ -460,9 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     }
                     float v[16];
                     tmem_ld16(tbase + (uint32_t)c, v);
-#pragma unroll
-                    for (int k = 0; k < 16; k += 4)
-                        *reinterpret_cast<float4 *>(prow + c + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    tmem_st16(tbase + (uint32_t)(kParkCol0 + c), v);   // park beta d beside the accumulator
 #pragma unroll
                     for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
                     tmem_ld16(tbase + (uint32_t)(K + c), v);
@@ -482,19 +497,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     alive = false;
                     break;
                 }
-                if (valid) {
-                    // g = (2/||B||)(beta d - E d) from the parked beta d (d read again)
+                tmem_wait_st();
+                // g = (2/||B||)(beta d - E d) from the parked beta d (d read again);
+                // the tensor-memory reads are warp-collective, so every lane takes part
 #pragma unroll
-                    for (int j = 0; j < kParkGroups; ++j) {
-                        const int c = 16 * (sub + kSubs * j);
-                        if (c >= K) break;
+                for (int j = 0; j < kParkGroups; ++j) {
+                    const int c = 16 * (sub + kSubs * j);
+                    if (c >= K) break;
+                    float pv[16];
+                    tmem_ld16(tbase + (uint32_t)(kParkCol0 + c), pv);
+                    if (valid) {
 #pragma unroll
                         for (int k = 0; k < 16; k += 4) {
-                            const float4 p = *reinterpret_cast<const float4 *>(prow + c + k);
                             const float4 q = __ldg(reinterpret_cast<const float4 *>(d + c + k));
                             *reinterpret_cast<float4 *>(grow + c + k) =
-                                make_float4(s2 * (p.x - E * q.x), s2 * (p.y - E * q.y), s2 * (p.z - E * q.z),
-                                            s2 * (p.w - E * q.w));
+                                make_float4(s2 * (pv[k] - E * q.x), s2 * (pv[k + 1] - E * q.y),
+                                            s2 * (pv[k + 2] - E * q.z), s2 * (pv[k + 3] - E * q.w));
                         }
                     }
                 }
@@ -702,11 +720,10 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaS
     a.ref_count = ctx->ref_count;
     a.ref_cap = ctx->ws_n;
     a.status = ctx->status;
-    // ring + barriers (128 B) + the E / V exchange (2 tiles x kSubs sets x BM float4)
-    // + the parked beta d rows; more than half of the SM's shared memory, so one CTA
-    // (holding all 512 TMEM columns) runs per SM
-    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 128 + 2 * kSubs * BM * sizeof(float4) +
-                        (size_t)BM * kParkStride * sizeof(float);
+    // ring + barriers (128 B) + the E / V exchange (2 tiles x kSubs sets x BM float4);
+    // more than half of the SM's shared memory, so one CTA (holding all 512 TMEM
+    // columns) runs per SM
+    const size_t smem = 1024 + (size_t)kStages * kStageBytes + 128 + 2 * kSubs * BM * sizeof(float4);
     cudaError_t e;
     if (bf16) {
         e = cudaFuncSetAttribute(k_qform_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
