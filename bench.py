@@ -467,6 +467,25 @@ def run_ours(args):
     else:
         peak = _fp32_peak_tflops(peaks)
         peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock (derived)"
+    # whole step against the sum of per-kernel bounds (kernels run one after another)
+    step_bound = {}
+    gcount = np.bincount(groups + 1, minlength=7)[1:]
+    for k in ("descriptor", "qform", "force"):
+        amt, _, bnd = _algorithmic(k, groups, n, ff.d_full, ff.d_single, pairs_per_atom)
+        pk = peaks.get("bf16_tflops_sustained", 1700.0) if bnd == "tensor" else _fp32_peak_tflops(peaks)
+        step_bound[k + "_ms"] = round(amt / (pk * 1e12) * 1e3, 4)
+    # HBM: positions, the list read twice, forces and E/V/sigma written (the unavoidable bytes)
+    hbm_bytes = n * (16 + 2 * 64 * 4 + 12 + 12)
+    step_bound["hbm_ms"] = round(hbm_bytes / (peaks.get("hbm_gbs", 6800.0) * 1e9) * 1e3, 4)
+    step_bound["sum_ms"] = round(sum(step_bound[k + "_ms"] for k in ("descriptor", "qform", "force")) +
+                                 step_bound["hbm_ms"], 4)
+    step_bound["measured_ms"] = round(ms_mix / args.steps, 4)
+    step_bound["frac"] = round(step_bound["sum_ms"] / step_bound["measured_ms"], 4)
+    step_bound["atoms_mixed_class"] = int(gcount[0] + gcount[3])
+    step_bound["atoms_one_species_class"] = int(gcount[1] + gcount[2] + gcount[4] + gcount[5])
+    step_bound["note"] = ("algorithmic FLOPs of each kernel over its peak (FP32 FMA for the descriptor and force "
+                          "kernels, BF16 dense sustained for the quadratic forms, whose 3xBF16 split executes 3x "
+                          "these FLOPs) plus the step's unavoidable HBM bytes; frac = bound / measured")
     tpa = _traffic_per_atom(dom)
     roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1),
                 "unit": unit, "frac": round(achieved / peak, 4), "peak_source": peak_note,
@@ -525,6 +544,7 @@ def run_ours(args):
                 "compaction_off": {"value": round(value_nc, 3), "ms_per_step": round(ms_nc / nc_steps, 4),
                                    "steps": nc_steps, "note": "3xBF16, every atom at d = 544"},
                 "sgp_mapping": sgp_map,
+                "step_bound": step_bound,
                 "force_err_ev_per_A": ferr,
                 "errors_vs_oracle": {"sample": err_sample, **errs},
                 "rebuilds_in_timed_steps": rebuild_count,

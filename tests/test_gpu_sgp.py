@@ -116,3 +116,25 @@ def test_not_positive_definite_is_rejected(sparse_sets):
     with pytest.raises(N.FlareError) as e:
         ff.map_sgp(0, torch.as_tensor(D_S), torch.as_tensor(alpha), torch.as_tensor(bad), SIG2)
     assert e.value.code == N.FLR_EINVAL
+
+
+@pytest.mark.parametrize("n_s", [1, 33, 300])
+def test_mapping_sizes_against_oracle(n_s):
+    """A single sparse point, one past a 32-column Cholesky panel, and many
+    panels: random unit descriptor rows, K_SS = sig2 D D^T + jitter I."""
+    import torch
+    from paper_2204_12573_gb300 import flare as F
+    rng = np.random.default_rng(100 + n_s)
+    ff = F.FlareGB(precision="fp32")
+    d = ff.d_full
+    D = rng.normal(size=(n_s, d))
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    alpha = rng.normal(size=n_s)
+    K = SIG2 * (D @ D.T) + JITTER * np.eye(n_s)
+    b, g = ff.map_sgp(1, torch.as_tensor(D), torch.as_tensor(alpha), torch.as_tensor(K), SIG2)
+    b, g = b.cpu().numpy(), g.cpu().numpy()
+    b_ref = sgp.mapped_beta(D, alpha, SIG2)
+    g_ref = sgp.mapped_gamma(D, K, SIG2)
+    assert np.abs(b - b_ref).max() <= 1e-11 * max(1.0, np.abs(b_ref).max())
+    assert np.abs(g - g_ref).max() <= 1e-9 * max(1.0, np.abs(g_ref).max())
+
