@@ -211,6 +211,7 @@ class OracleSample:
         self.struct, self.beta, self.sigma = struct, beta, sigma
         self.pos = synth.f32_exact_f64(synth.as_f32_positions(struct.pos))
         self.h = O.Hyper()
+        self.cores = O.max_threads()   # all host cores (OpenMP default), before any 1-thread run
         # two pilots give the fixed cost (neighbour search over the whole slab) and the cost per atom
         self.t_fixed, self.t_atom = 0.0, 1e-3
         pts = []
@@ -226,9 +227,10 @@ class OracleSample:
     def _block(self, side):
         return np.nonzero((self.pos[:, 0] < side) & (self.pos[:, 1] < side))[0]
 
-    def _run(self, atoms):
+    def _run(self, atoms, n_threads=0):
         s = self.struct
-        self.O.forces_subset(self.h, self.pos, s.species, s.cell, s.pbc, self.beta, self.sigma, atoms, skin=0.5)
+        self.O.forces_subset(self.h, self.pos, s.species, s.cell, s.pbc, self.beta, self.sigma, atoms, skin=0.5,
+                             n_threads=n_threads or self.cores)
 
     def step(self, target_s):
         n25 = len(self._block(25.0))
@@ -238,14 +240,31 @@ class OracleSample:
         t0 = time.time()
         self._run(blk)
         dt = time.time() - t0
-        return {"value": len(blk) / dt / 1e6, "unit": UNIT, "cores": self.O.max_threads(), "kind": "oracle",
+        return {"value": len(blk) / dt / 1e6, "unit": UNIT, "cores": self.cores, "kind": "oracle",
                 "seconds": round(dt, 2),
                 "sample": f"{len(blk)} atoms (x,y < {side:.1f} A column of the slab, Pt and H): cell-list "
                           f"neighbours over all atoms + FP64 E/F/sigma of the column, one step"}
 
 
+    def one_core(self, target_s):
+        """The same kind of step on one thread, on a column sized for about target_s."""
+        n25 = len(self._block(25.0))
+        want = target_s / (self.t_atom * self.cores)
+        side = float(np.clip(25.0 * np.sqrt(want / max(n25, 1)), 10.0, 300.0))
+        blk = self._block(side)
+        t0 = time.time()
+        self._run(blk, n_threads=1)
+        dt = time.time() - t0
+        return len(blk) / dt / 1e6, f"{len(blk)} atoms (x,y < {side:.1f} A column), 1 thread, {dt:.2f} s"
+
+
 def cpu_baseline_sample(struct, beta, sigma, target_s=12.0):
-    return OracleSample(struct, beta, sigma).step(target_s)
+    samp = OracleSample(struct, beta, sigma)
+    r = samp.step(target_s)
+    v1, s1 = samp.one_core(4.0)
+    r["value_1core"] = v1
+    r["sample_1core"] = s1
+    return r
 
 
 def run_reference(args):
