@@ -152,26 +152,40 @@ def _traffic_per_atom(kernel):
     return None
 
 
-# algorithmic work per atom ("Kernels and their rooflines")
-def _algorithmic(kernel, groups, n_atoms, d_full, d_single, pairs_per_atom):
-    """(amount, unit, bound) for one launch of `kernel`."""
+# Algorithmic work of one launch, from the method (not from what the kernels
+# execute).  N = 8 radial functions, 16 real harmonics (l <= 3); p = pairs
+# inside r_cut per atom; C_g = radial channels of the atom's class (16 for a
+# two-species environment, 8 for a one-species one); K = descriptor length
+# of the class (544 or 144).
+#   descriptor, per pair: A_{n,lm} += R_n Y_lm            2 N 16 flop
+#                         geometry, R_n f_c, Y_lm           70 flop
+#               per atom: B2 = sum_m A A (C_g(C_g+1)/2 channel pairs x 16 m
+#                         products) 32 C_g(C_g+1)/2 flop, norm and scaling 3 K flop
+#   quadratic forms, per atom: P = d [beta | Sigma]        2 K (2K) flop
+#   force, per pair: c_lm, c'_lm = sum_n w (R_n, R'_n)     4 N 16 flop
+#                    geometry, radial with derivatives, Y_lm and grad P_lm,
+#                    the three l-weighted sums, f_ij        325 flop
+#          per atom: w = G~ A                               2 C_g^2 16 flop
+DESC_PAIR = 2 * 8 * 16 + 70
+FORCE_PAIR = 4 * 8 * 16 + 325
+
+
+def _class_counts(groups):
     g = np.bincount(groups + 1, minlength=7)[1:]   # counts of the 6 compaction groups
-    n_full = int(g[0] + g[3])
-    n_single = int(g[1] + g[2] + g[4] + g[5])
+    return int(g[0] + g[3]), int(g[1] + g[2] + g[4] + g[5])
+
+
+def _algorithmic(kernel, groups, n_atoms, d_full, d_single, pairs_per_atom):
+    """Algorithmic FLOPs of one launch of `kernel` (see the table above)."""
+    n_full, n_single = _class_counts(groups)
     if kernel == "qform":
-        flops = 2.0 * (n_full * d_full * 2 * d_full + n_single * d_single * 2 * d_single)
-        return flops, "TFLOP/s", "tensor"
+        return 2.0 * (n_full * d_full * 2 * d_full + n_single * d_single * 2 * d_single)
     if kernel == "force":
-        # per pair: 2 N 16 (c, c') FMA + ~130 flops gradients/radial; per atom w = G~A
-        per_pair = 2 * (2 * 8 * 16) + 130
-        per_atom_w = 2 * (16 * 8 * 16)
-        flops = n_atoms * pairs_per_atom * per_pair + n_full * 2 * per_atom_w + n_single * per_atom_w
-        return float(flops), "TFLOP/s", "alu"
+        return float(n_atoms * pairs_per_atom * FORCE_PAIR + n_full * 2 * 16 * 16 * 16 + n_single * 2 * 8 * 8 * 16)
     if kernel == "descriptor":
-        per_pair = 2 * 8 * 16 * 2 + 60
-        flops = n_atoms * pairs_per_atom * per_pair + 2 * (n_full * d_full * 2.5 + n_single * d_single * 2.5)
-        return float(flops), "TFLOP/s", "alu"
-    return None, None, None
+        # 32 flop per channel pair and d = 4 x channel pairs: 8 d + 3 d per atom
+        return float(n_atoms * pairs_per_atom * DESC_PAIR + n_full * 11 * d_full + n_single * 11 * d_single)
+    return None
 
 
 def _pairs_within_cutoff(nl, sysg, n, r_cut):
@@ -195,9 +209,19 @@ def _pairs_within_cutoff(nl, sysg, n, r_cut):
     return total
 
 
-def _fp32_peak_tflops(peaks):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
-    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+def measure_fp32_peak(device):
+    """FP32 FMA peak measured on this device (flr_fp32_fma_peak: all SMs, 8
+    independent register-resident FMA chains per thread, best of 20 timed
+    launches), with the SM clock sampled while it runs."""
+    from paper_2204_12573_gb300 import flare as F
+    clocks = Clocks(device)
+    with clocks:
+        r = F.fp32_fma_peak(device, 20)
+    r["clocks"] = clocks.summary()
+    r["nominal_tflops"] = r["num_sms"] * 128 * 2 * (r["clocks"].get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    r["note"] = ("flr_fp32_fma_peak: every SM at its occupancy limit, 8 independent FMA chains per thread, "
+                 "best of 20 launches timed with CUDA events; nominal = SMs x 128 lanes x 2 x max SM clock")
+    return r
 
 
 class OracleSample:
@@ -385,7 +409,8 @@ def run_ours(args):
     ms_mix, launches, _, st_mix = timed("bf16x3", clocks=clocks)
     clk = clocks.summary()
     _, _, prof_mix, _ = timed("bf16x3", profile=True)
-    ms_fp32, _, prof_fp32, _ = timed("fp32", profile=False)
+    ms_fp32, _, _, _ = timed("fp32", profile=False)
+    _, _, prof_fp32, _ = timed("fp32", profile=True)
 
     value = job_throughput(world, n, args.steps, ms_mix)
     value_fp32 = job_throughput(world, n, args.steps, ms_fp32)
@@ -396,26 +421,35 @@ def run_ours(args):
         ffn = F.FlareGB(precision="bf16x3", max_nbr=64, compaction=False)
         ffn.set_model(beta, sigma)
         nln = ffn.nbrlist(n)
-        sysg.pos.copy_(torch.as_tensor(pos0, device="cuda"))
-        vel.copy_(torch.as_tensor(vel0, device="cuda"))
-        F.build_neighbors(ffn, sysg, nln)
-        stn = F.MDState(sysg, vel)
-        F.md_step(ffn, stn, nln, args.warmup, out)
-        ffn.sync()
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        F.md_step(ffn, stn, nln, steps, out)
-        e1.record(stream)
-        barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1), dist)
-        ffn.sync()
+        res = []
+        for profile in (False, True):
+            sysg.pos.copy_(torch.as_tensor(pos0, device="cuda"))
+            vel.copy_(torch.as_tensor(vel0, device="cuda"))
+            F.build_neighbors(ffn, sysg, nln)
+            stn = F.MDState(sysg, vel)
+            F.md_step(ffn, stn, nln, args.warmup, out)
+            ffn.sync()
+            if profile:
+                ffn.profile(True)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            F.md_step(ffn, stn, nln, steps, out)
+            e1.record(stream)
+            barrier()
+            res.append(max_over_ranks(e0.elapsed_time(e1), dist))
+            if profile:
+                res.append(ffn.profile_read())
+                ffn.profile(False)
+            ffn.sync()
+        _, _, groups_nc = nln.view(n)
+        groups_nc = groups_nc.cpu().numpy()
         del nln, ffn
         torch.cuda.synchronize()
-        return ms
+        return res[0], res[2], groups_nc
 
     nc_steps = max(1, min(args.steps, 10))
-    ms_nc = timed_no_compaction(nc_steps)
+    ms_nc, prof_nc, groups_nc = timed_no_compaction(nc_steps)
     value_nc = job_throughput(world, n, nc_steps, ms_nc)
 
     # sparse-GP -> (beta, Sigma) mapping on the device (once per model, not per step)
@@ -474,27 +508,45 @@ def run_ours(args):
     err_sample = f"{len(sample)} atoms (seed 2; {n_mixed} mixed-class), FP64 oracle at the same positions"
 
 
-    # roofline of the dominant kernel (mixed run)
+    # rooflines: every kernel of each run against its own peak
     peaks, peak_kind = _peaks()
+    fma = measure_fp32_peak(torch.cuda.current_device())
+    fp32_peak = fma["tflops_best"]
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1700.0)
     per_step = {k: v[0] / max(args.steps, 1) for k, v in prof_mix.items()}
     dom = max(("descriptor", "qform", "force"), key=lambda k: prof_mix[k][0])
     cnt = out["energy"].numel()
     pairs_per_atom = _pairs_within_cutoff(nl, sysg, n, ff.r_cut) / n
-    amount, unit, bound = _algorithmic(dom, groups, n, ff.d_full, ff.d_single, pairs_per_atom)
-    avg_ms = prof_mix[dom][0] / max(prof_mix[dom][1], 1)
-    achieved = amount / (avg_ms / 1e3) / 1e12
-    if bound == "tensor":
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak_note = f"bf16 dense, sustained, {peak_kind}"
-    else:
-        peak = _fp32_peak_tflops(peaks)
-        peak_note = "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock (derived)"
+
+    def kernel_rooflines(prof, grp, precision):
+        res = {}
+        for k in ("descriptor", "qform", "force"):
+            amt = _algorithmic(k, grp, n, ff.d_full, ff.d_single, pairs_per_atom)
+            avg = prof[k][0] / max(prof[k][1], 1)
+            ach = amt / (avg / 1e3) / 1e12
+            if k == "qform" and precision == "bf16x3":
+                pk, bound, src = bf16_sus, "tensor", f"BF16 dense sustained ({peak_kind})"
+            elif k == "qform" and precision == "tf32":
+                pk, bound, src = bf16_sus / 2, "tensor", f"TF32 = BF16 dense sustained ({peak_kind}) x 1/2 (nominal ratio)"
+            else:
+                pk, bound, src = fp32_peak, "alu", "FP32 FMA, measured (flr_fp32_fma_peak)"
+            r = {"ms_per_launch": round(avg, 4), "algorithmic_tflop": round(amt / 1e12, 4), "achieved": round(ach, 3),
+                 "peak": round(pk, 1), "unit": "TFLOP/s", "bound": bound, "frac": round(ach / pk, 4),
+                 "peak_source": src}
+            if k == "qform" and precision == "bf16x3":
+                r["frac_executed"] = round(3 * ach / pk, 4)   # the split issues 3 BF16 products per FP32 product
+            res[k] = r
+        return res
+
+    rooflines = {"bf16x3": kernel_rooflines(prof_mix, groups, "bf16x3"),
+                 "fp32": kernel_rooflines(prof_fp32, groups, "fp32"),
+                 "compaction_off_bf16x3": kernel_rooflines(prof_nc, groups_nc, "bf16x3")}
     # whole step against the sum of per-kernel bounds (kernels run one after another)
     step_bound = {}
-    gcount = np.bincount(groups + 1, minlength=7)[1:]
+    n_full, n_single = _class_counts(groups)
     for k in ("descriptor", "qform", "force"):
-        amt, _, bnd = _algorithmic(k, groups, n, ff.d_full, ff.d_single, pairs_per_atom)
-        pk = peaks.get("bf16_tflops_sustained", 1700.0) if bnd == "tensor" else _fp32_peak_tflops(peaks)
+        amt = _algorithmic(k, groups, n, ff.d_full, ff.d_single, pairs_per_atom)
+        pk = bf16_sus if k == "qform" else fp32_peak
         step_bound[k + "_ms"] = round(amt / (pk * 1e12) * 1e3, 4)
     # HBM: positions, the list read twice, forces and E/V/sigma written (the unavoidable bytes)
     hbm_bytes = n * (16 + 2 * 64 * 4 + 12 + 12)
@@ -503,16 +555,20 @@ def run_ours(args):
                                  step_bound["hbm_ms"], 4)
     step_bound["measured_ms"] = round(ms_mix / args.steps, 4)
     step_bound["frac"] = round(step_bound["sum_ms"] / step_bound["measured_ms"], 4)
-    step_bound["atoms_mixed_class"] = int(gcount[0] + gcount[3])
-    step_bound["atoms_one_species_class"] = int(gcount[1] + gcount[2] + gcount[4] + gcount[5])
-    step_bound["note"] = ("algorithmic FLOPs of each kernel over its peak (FP32 FMA for the descriptor and force "
-                          "kernels, BF16 dense sustained for the quadratic forms, whose 3xBF16 split executes 3x "
-                          "these FLOPs) plus the step's unavoidable HBM bytes; frac = bound / measured")
+    step_bound["atoms_mixed_class"] = n_full
+    step_bound["atoms_one_species_class"] = n_single
+    step_bound["pairs_per_atom"] = round(pairs_per_atom, 3)
+    step_bound["note"] = ("algorithmic FLOPs of each kernel over its peak (measured FP32 FMA for the descriptor and "
+                          "force kernels, BF16 dense sustained for the quadratic forms, whose 3xBF16 split executes "
+                          "3x these FLOPs) plus the step's unavoidable HBM bytes; frac = bound / measured")
+    dr = rooflines["bf16x3"][dom]
     tpa = _traffic_per_atom(dom)
-    roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1),
-                "unit": unit, "frac": round(achieved / peak, 4), "peak_source": peak_note,
-                "traffic": None if tpa is None else tpa * cnt, "avg_launch_ms": round(avg_ms, 4),
-                "algorithmic_per_launch": amount}
+    roofline = {"kernel": dom, "bound": dr["bound"], "achieved": dr["achieved"], "peak": dr["peak"],
+                "unit": "TFLOP/s", "frac": dr["frac"], "peak_source": dr["peak_source"] + ", measured",
+                "traffic": None if tpa is None else tpa * cnt, "avg_launch_ms": dr["ms_per_launch"],
+                "algorithmic_per_launch": dr["algorithmic_tflop"] * 1e12,
+                "per_unit": {"descriptor_flop_per_pair": DESC_PAIR, "force_flop_per_pair": FORCE_PAIR,
+                             "pairs_per_atom": round(pairs_per_atom, 3)}}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -609,8 +665,9 @@ def run_ours(args):
                 "errors_vs_oracle": {"sample": err_sample, **errs},
                 "rebuilds_in_timed_steps": rebuild_count,
                 "kernels_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
-                "kernels_ms_per_step_fp32": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_fp32.items()}
-                if prof_fp32 else None,
+                "kernels_ms_per_step_fp32": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_fp32.items()},
+                "kernels_ms_per_step_compaction_off": {k: round(v[0] / nc_steps, 4) for k, v in prof_nc.items()},
+                "kernel_rooflines": rooflines, "fp32_fma_peak": fma,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "serving": serving}
         print(json.dumps(line), flush=True)

@@ -441,6 +441,16 @@ int flr_server_stats_read(flr_server *srv, flr_server_stats *stats);
  * still queued are dropped without a completion. */
 int flr_server_destroy(flr_server *srv);
 
+/* Measured FP32 FMA throughput of `device` (no counterpart in the paper: the
+ * roofline denominator of the descriptor and force kernels, which are bound
+ * by FP32 arithmetic).  Runs one warm-up and then `launches` launches of a
+ * kernel in which every thread advances 8 independent register-resident FMA
+ * chains, on every SM (SM count read from the device) at its occupancy
+ * limit, each launch timed with CUDA events.  Returns the best and the
+ * median rate in TFLOP/s (2 flop per FMA) and the SM count.  Allocates and
+ * frees a few bytes of device memory; synchronous; leaves `device` current. */
+int flr_fp32_fma_peak(int device, int32_t launches, double *tflops_best, double *tflops_median, int32_t *num_sms);
+
 /* Kernel classes of flr_profile_read. */
 #define FLR_KERNEL_DESCRIPTOR 0   /* A, B2, normalization (one launch per evaluation) */
 #define FLR_KERNEL_QFORM 1        /* quadratic-form GEMM (SIMT or tcgen05) */

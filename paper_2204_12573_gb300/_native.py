@@ -45,7 +45,7 @@ EXPORTED = [
     "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
     "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
     "flr_bytes_per_atom", "flr_server_create", "flr_server_submit", "flr_server_poll", "flr_server_stats_read",
-    "flr_server_destroy", "flr_set_variance_mode", "flr_map_sgp",
+    "flr_server_destroy", "flr_set_variance_mode", "flr_map_sgp", "flr_fp32_fma_peak",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
@@ -161,6 +161,8 @@ def lib():
             "flr_server_destroy": (ctypes.c_int, [P]),
             "flr_profile_read": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_int64)]),
+            "flr_fp32_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

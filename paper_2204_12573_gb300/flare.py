@@ -376,3 +376,12 @@ def energy_backward(ff: FlareGB, batch: Batch, nl: NbrList, grad_energy, want_be
     N.check(ff.lib.flr_energy_backward(ff.handle, ctypes.byref(b), nl.handle, _ptr(u), _ptr(gpos), _ptr(gbeta),
                                        _stream(stream)))
     return gpos, gbeta
+
+
+def fp32_fma_peak(device=0, launches=10):
+    """Measured FP32 FMA rate of a device (flr_fp32_fma_peak): best and
+    median TFLOP/s over `launches` timed launches, and the SM count."""
+    best, med, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    N.check(N.lib().flr_fp32_fma_peak(int(device), int(launches), ctypes.byref(best), ctypes.byref(med),
+                                      ctypes.byref(sms)))
+    return {"tflops_best": best.value, "tflops_median": med.value, "num_sms": sms.value}
