@@ -125,7 +125,9 @@ void free_workspace(flr_ctx *ctx)
         cudaFree(ctx->D32[r]);
         cudaFree(ctx->Dhi[r]);
         cudaFree(ctx->Dlo[r]);
+        cudaFree(ctx->Dtf[r]);
         cudaFree(ctx->P[r]);
+        ctx->Dtf[r] = nullptr;
         ctx->D32[r] = nullptr;
         ctx->Dhi[r] = ctx->Dlo[r] = nullptr;
         ctx->P[r] = nullptr;
@@ -452,6 +454,7 @@ int flr_destroy(flr_ctx *c)
         cudaFree(c->W32[g]);
         cudaFree(c->Whi[g]);
         cudaFree(c->Wlo[g]);
+        cudaFree(c->Wtf[g]);
         cudaFree(c->S64[g]);
     }
     for (int s = 0; s < kSpecies; ++s) {
@@ -605,7 +608,7 @@ int upload_species(flr_ctx *c, int species)
             }
             c->sigma_norm[g] = (float)lam;
         }
-        std::vector<float> w32((size_t)rows * D.kp32[r], 0.f);
+        std::vector<float> w32((size_t)rows * D.kp32[r], 0.f), wtf((size_t)rows * D.kp32[r], 0.f);
         std::vector<uint16_t> whi((size_t)rows * D.kp64[r], 0), wlo((size_t)rows * D.kp64[r], 0);
         for (int n = 0; n < 2 * K; ++n) {
             for (int k = 0; k < K; ++k) {
@@ -613,7 +616,12 @@ int upload_species(flr_ctx *c, int species)
                 if (n < K) v = bh[(size_t)idx[n] * d + idx[k]];
                 else if (!factored) v = sh[(size_t)idx[n - K] * d + idx[k]];
                 else v = Lf[(size_t)k * K + (n - K)];   // row n-K of L^T
-                w32[(size_t)n * D.kp32[r] + k] = (float)v;
+                const float v32 = (float)v;
+                w32[(size_t)n * D.kp32[r] + k] = v32;
+                uint32_t u;
+                std::memcpy(&u, &v32, 4);
+                u = tf32_round_bits(u);
+                std::memcpy(&wtf[(size_t)n * D.kp32[r] + k], &u, 4);
                 const uint16_t h = f2bf((float)v);
                 whi[(size_t)n * D.kp64[r] + k] = h;
                 wlo[(size_t)n * D.kp64[r] + k] = f2bf((float)(v - (double)bf2f(h)));
@@ -624,9 +632,12 @@ int upload_species(flr_ctx *c, int species)
             s = dev_alloc(&c->W32[g], w32.size(), "model");
             if (s == FLR_OK) s = dev_alloc(&c->Whi[g], whi.size(), "model");
             if (s == FLR_OK) s = dev_alloc(&c->Wlo[g], wlo.size(), "model");
+            if (s == FLR_OK) s = dev_alloc(&c->Wtf[g], wtf.size(), "model");
             if (s != FLR_OK) return s;
         }
         s = cuda_fail(cudaMemcpy(c->W32[g], w32.data(), w32.size() * 4, cudaMemcpyHostToDevice), "model upload");
+        if (s == FLR_OK)
+            s = cuda_fail(cudaMemcpy(c->Wtf[g], wtf.data(), wtf.size() * 4, cudaMemcpyHostToDevice), "model upload");
         if (s == FLR_OK)
             s = cuda_fail(cudaMemcpy(c->Whi[g], whi.data(), whi.size() * 2, cudaMemcpyHostToDevice), "model upload");
         if (s == FLR_OK)

@@ -34,6 +34,7 @@ struct DescArgs {
     float *D32[2];
     __nv_bfloat16 *Dhi[2], *Dlo[2];
     int bf16;                  // also write BF16 hi/lo rows
+    float *Dtf[2];             // also write rows rounded to nearest TF32 (TF32 precision), or nullptr
     float4 *pair_rec;          // [n][max_nbr] out: pairs inside r_cut (r_ij, j | s_j << 25)
     int32_t *pair_cnt;         // [n] out: their number
     const int32_t *order;      // order in which atoms are taken (nullptr: by index)
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         float *d32 = a.D32[reg] + (size_t)r * a.kp32[reg];
         __nv_bfloat16 *dh = a.bf16 ? a.Dhi[reg] + (size_t)r * a.kp64[reg] : nullptr;
         __nv_bfloat16 *dl = a.bf16 ? a.Dlo[reg] + (size_t)r * a.kp64[reg] : nullptr;
+        float *dt = a.Dtf[reg] ? a.Dtf[reg] + (size_t)r * a.kp32[reg] : nullptr;
 #pragma unroll
         for (int k = 0; k < MAXP; ++k) {
             const int t = lane + 32 * k;
@@ -276,6 +278,10 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
                 const float4 bb = sB[t];
                 const float4 v = make_float4(bb.x * inv, bb.y * inv, bb.z * inv, bb.w * inv);
                 *reinterpret_cast<float4 *>(d32 + 4 * t) = v;
+                if (dt)
+                    *reinterpret_cast<uint4 *>(dt + 4 * t) =
+                        make_uint4(tf32_round_bits(__float_as_uint(v.x)), tf32_round_bits(__float_as_uint(v.y)),
+                                   tf32_round_bits(__float_as_uint(v.z)), tf32_round_bits(__float_as_uint(v.w)));
                 if (dh) {
                     // hi = RN(v), lo = RN(v - hi), two values per conversion
                     const __nv_bfloat162 hi01 = __floats2bfloat162_rn(v.x, v.y);
@@ -353,6 +359,21 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.A = ctx->A;
     a.norm = ctx->norm;
     a.bf16 = ctx->p.precision == FLR_PREC_BF16X3;
+    for (int r = 0; r < 2; ++r) a.Dtf[r] = nullptr;
+    if (ctx->p.precision == FLR_PREC_TF32) {
+        // rows rounded to nearest TF32 for the tensor-core A operand, allocated
+        // (and their padding zeroed) on first use at this workspace size
+        if (!ctx->Dtf[0]) {
+            for (int r = 0; r < 2; ++r) {
+                const size_t bytes = sizeof(float) * (size_t)ctx->ws_n * ctx->dims.kp32[r];
+                cudaError_t e = cudaMalloc(&ctx->Dtf[r], bytes);
+                if (e == cudaSuccess) e = cudaMemset(ctx->Dtf[r], 0, bytes);
+                if (e != cudaSuccess) return cuda_fail(e, "workspace TF32 rows");
+            }
+            ctx->maps_n = -1;   // the A maps of the tensor-core kernel point at these rows
+        }
+        for (int r = 0; r < 2; ++r) a.Dtf[r] = ctx->Dtf[r];
+    }
     a.pair_rec = nl->pair_rec;
     a.pair_cnt = nl->pair_cnt;
     a.order = nullptr;

@@ -143,6 +143,7 @@ struct flr_ctx {
     float *W32[flr::kGroups];          // [nrows_pad][kp32]  B operand rows (beta rows, then Sigma rows)
     __nv_bfloat16 *Whi[flr::kGroups];  // [nrows_pad][kp64]
     __nv_bfloat16 *Wlo[flr::kGroups];
+    float *Wtf[flr::kGroups];          // [nrows_pad][kp32]  W32 rounded to nearest TF32 (TF32 B operand)
     // index tables (device): packed (a | b << 8 | l << 16) for each compact component
     int32_t *tab_full;
     int32_t *tab_single;
@@ -153,6 +154,8 @@ struct flr_ctx {
     float *D32[2];             // [n][kp32[r]]
     __nv_bfloat16 *Dhi[2];     // [n][kp64[r]]
     __nv_bfloat16 *Dlo[2];
+    float *Dtf[2];             // [n][kp32[r]] descriptor rows rounded to nearest TF32 (TF32 A operand;
+                               // allocated on first TF32 use, sized like D32)
     float *P[2];               // [n][2K[r]] quadratic-form products (FP32 SIMT path only)
     float *G[2];               // [n][K[r]]  g = dE/dB rows, consumed by the force kernel
     long long *Facc;           // [n][3] fixed point
@@ -322,6 +325,13 @@ struct WarpChunksT {
 using WarpChunks = WarpChunksT<kWarpChunk>;
 
 // ---- shared device helpers ----
+
+// Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits,
+// ties away from zero), kept in FP32 storage with the low 13 bits zero.  The
+// tensor core reads the top 19 bits of an FP32 operand, i.e. truncates; a
+// value that is already TF32 passes through unchanged, so operands rounded
+// here enter the product rounded to nearest instead of truncated.
+__host__ __device__ inline uint32_t tf32_round_bits(uint32_t u) { return (u + 0x1000u) & 0xFFFFE000u; }
 
 // Decode a neighbour entry: (j << 8) | (s_j << 7) | code,
 // code = (sx+2)*25 + (sy+2)*5 + (sz+2); s_j is the species of j (0 or 1).

@@ -667,7 +667,8 @@ int ensure_maps(flr_ctx *ctx)
             if (st == FLR_OK) st = encode(&ctx->maps->a[r][1], ctx->Dlo[r], true, D.kp64[r], ctx->ws_n, BM);
             if (st != FLR_OK) return st;
         } else {
-            int st = encode(&ctx->maps->a[r][0], ctx->D32[r], false, D.kp32[r], ctx->ws_n, BM);
+            // TF32: the rows rounded to nearest TF32 (the tensor core would truncate FP32 rows)
+            int st = encode(&ctx->maps->a[r][0], ctx->Dtf[r], false, D.kp32[r], ctx->ws_n, BM);
             if (st != FLR_OK) return st;
             ctx->maps->a[r][1] = ctx->maps->a[r][0];
         }
@@ -679,7 +680,7 @@ int ensure_maps(flr_ctx *ctx)
             if (st == FLR_OK) st = encode(&ctx->maps->b[g][1], ctx->Wlo[g], true, D.kp64[r], D.nrows_pad[r], NH);
             if (st != FLR_OK) return st;
         } else {
-            int st = encode(&ctx->maps->b[g][0], ctx->W32[g], false, D.kp32[r], D.nrows_pad[r], NH);
+            int st = encode(&ctx->maps->b[g][0], ctx->Wtf[g], false, D.kp32[r], D.nrows_pad[r], NH);
             if (st != FLR_OK) return st;
             ctx->maps->b[g][1] = ctx->maps->b[g][0];
         }

@@ -10,7 +10,7 @@ import pytest
 
 from paper_2204_12573_gb300 import synth
 
-from gpu_common import E_TOL_FP32, F_TOL_FP32, F_TOL_MIXED, V_TOL_FP32
+from gpu_common import E_TOL_FP32, F_TOL_FP32, F_TOL_MIXED, V_TOL_FP32, mixed_bounds
 import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -35,7 +35,7 @@ def _sample(groups, rng, n_mixed=64, n_rest=192):
                                    rng.choice(rest, n_rest, replace=False)]))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16x3"])
 def test_full_size_md_then_sampled_parity(slab, precision):
     import torch
     from paper_2204_12573_gb300 import flare as F
@@ -70,6 +70,11 @@ def test_full_size_md_then_sampled_parity(slab, precision):
         assert (np.abs(E - o["E"]) <= E_TOL_FP32 * np.maximum(np.abs(o["E"]), 1.0)).all()
         ok = o["V"] > 0
         assert (np.abs(V[ok] - o["V"][ok]) / o["V"][ok] <= V_TOL_FP32).all()
+    else:
+        g_idx = groups.cpu().numpy()[idx]
+        bE, bV = mixed_bounds(precision, o["dhat"], s.species[idx], g_idx, BETA, SIGMA, o["E"], o["V"])
+        assert (np.abs(E - o["E"]) <= bE).all(), float((np.abs(E - o["E"]) / bE).max())
+        assert (np.abs(V - o["V"]) <= bV).all(), float((np.abs(V - o["V"]) / bV).max())
     # properties over all atoms
     Fall = r["forces"].double()
     assert Fall.sum(0).abs().max().item() <= 1e-3          # fixed-point scatter: F_i + F_j = 0 per pair

@@ -121,22 +121,107 @@ def test_nose_hoover_reaches_and_holds_the_target_temperature():
     assert st.xi != 0.0
 
 
+def test_one_nvt_step_matches_the_fp64_oracle_step():
+    """One Nose-Hoover velocity-Verlet step at the paper's protocol (450 K,
+    dt = 0.1 fs) of the 44-atom H2/Pt(111) system, against the FP64 oracle's
+    step (oracle/md.py) driven by the oracle's own forces: positions,
+    velocities and the thermostat variables xi and eta."""
+    import oracle as O
+    from oracle import md as OM
+    from paper_2204_12573_gb300 import flare as F
+    s = synth.tiny_system(0)
+    dt, T, tau = 1e-4, 450.0, 0.01
+    ff, sysg, vel, nl, _ = _setup(s, dt)
+    x0 = sysg.pos[:, :3].double().cpu().numpy()
+    v0 = vel[:, :3].double().cpu().numpy()
+    st = F.MDState(sysg, vel, dt=dt, rebuild_every=10, temperature=T, tau=tau)
+    out = F.make_outputs(s.n_atoms)
+    F.md_step(ff, st, nl, 1, out)
+    ff.sync()
+    x1 = sysg.pos[:, :3].double().cpu().numpy()
+    v1 = vel[:, :3].double().cpu().numpy()
+
+    def force(x):
+        return O.energy_forces(O.Hyper(), x, s.species, s.cell, s.pbc, BETA, SIGMA, skin=0.5)["F"]
+
+    m = np.array([synth.MASS[int(k)] for k in s.species])
+    xr, vr, xir, etar, _ = OM.nvt_step(x0, v0, m, force, dt, T, tau, 0.0, 0.0)
+    # FP32 positions (|x| < 30 A) and the FP32 force tolerance (1e-4 eV/A over dt on 1 amu)
+    assert np.abs(x1 - xr).max() <= 1e-5
+    assert np.abs(v1 - vr).max() <= 5e-4
+    assert abs(st.xi - xir) <= 1e-5 * abs(xir) and xir < 0.0     # heating from 300 K: xi < 0
+    assert abs(st.eta - etar) <= 1e-5 * abs(etar)
+
+
+def test_nvt_paper_protocol_450K_0p1fs():
+    """The production protocol of Sec. VI-A: Nose-Hoover NVT at 450 K with a
+    0.1 fs step, on a Pt(111) slab with adsorbed H (225 atoms) started
+    from 300 K: after 60 thermostat periods the mean temperature is within
+    5 % of 450 K and E_pot + KE + thermostat energy drifts by less than
+    0.1 % of the kinetic energy (a 0.1 fs step conserves it closely)."""
+    from paper_2204_12573_gb300 import flare as F
+    s = synth.slab_batch(seed=3, n_slabs=1)[0]
+    dt, T, tau = 1e-4, 450.0, 0.01
+    ff, sysg, vel, nl, _ = _setup(s, dt)
+    st = F.MDState(sysg, vel, dt=dt, rebuild_every=10, temperature=T, tau=tau)
+    out = F.make_outputs(s.n_atoms)
+    temps, cons = [], []
+    for _ in range(120):
+        F.md_step(ff, st, nl, 50, out)
+        t = out["totals"].cpu().numpy()
+        temps.append(_temperature(t[12], s.n_atoms))
+        cons.append(t[0] + t[12] + t[17])
+    ff.sync()
+    assert st.step == 6000
+    t_mean = float(np.mean(temps[60:]))
+    assert abs(t_mean - T) <= 0.05 * T, t_mean
+    ke_scale = 1.5 * s.n_atoms * synth.KB_EV * T
+    assert np.abs(np.array(cons) - cons[0]).max() <= 1e-3 * ke_scale, (cons[0], max(cons), min(cons))
+
+
 def test_uncertainty_stop():
     """sigma_stop below the largest sigma halts after the first step; above it
-    every step runs."""
+    every step runs.  The count of uncertain atoms is integer work: it must
+    equal, exactly, the number of atoms whose returned sigma at the halting
+    step exceeds sigma_stop (the FP32 comparison the device makes)."""
     from paper_2204_12573_gb300 import flare as F
     s = synth.tiny_system(0)
     ff, sysg, vel, nl, _ = _setup(s, 0.0005)
     sig = F.energy_forces_uncertainty(ff, sysg, nl)["sigma"].cpu().numpy()
-    st = F.MDState(sysg, vel, dt=0.0005, sigma_stop=0.5 * float(sig.max()))
-    out = F.make_outputs(s.n_atoms)
-    F.md_step(ff, st, nl, 5, out)
-    assert st.halted and st.step == 1
-    assert out["totals"][15].item() >= 1
+    for frac in (0.5, 0.9, 0.999):
+        thr = frac * float(sig.max())
+        st = F.MDState(sysg, vel, dt=0.0005, sigma_stop=thr)
+        out = F.make_outputs(s.n_atoms)
+        F.md_step(ff, st, nl, 5, out)
+        ff.sync()
+        assert st.halted and st.step == 1
+        sig_step = out["sigma"].cpu().numpy()
+        n_above = int((sig_step > np.float32(thr)).sum())
+        assert n_above >= 1
+        assert out["totals"][15].item() == n_above
     st2 = F.MDState(sysg, vel, dt=0.0005, sigma_stop=10.0 * float(sig.max()))
+    out = F.make_outputs(s.n_atoms)
     F.md_step(ff, st2, nl, 5, out)
     assert not st2.halted and st2.step == 5
     assert out["totals"][15].item() == 0
+
+
+def test_uncertainty_count_on_a_large_slab():
+    """The same exact count on a 130k-atom slab with a threshold inside the
+    sigma distribution (thousands of atoms above it)."""
+    from paper_2204_12573_gb300 import flare as F
+    s = synth.big_slab(seed=1, nx=64, n_rows=64, n_layers=32, n_h2=1024)
+    ff, sysg, vel, nl, _ = _setup(s, 0.0005, precision="bf16x3")
+    sig = F.energy_forces_uncertainty(ff, sysg, nl)["sigma"].cpu().numpy()
+    thr = float(np.quantile(sig, 0.97))
+    st = F.MDState(sysg, vel, dt=0.0005, sigma_stop=thr)
+    out = F.make_outputs(s.n_atoms)
+    F.md_step(ff, st, nl, 3, out)
+    ff.sync()
+    assert st.halted and st.step == 1
+    n_above = int((out["sigma"].cpu().numpy() > np.float32(thr)).sum())
+    assert n_above > 1000
+    assert out["totals"][15].item() == n_above
 
 
 def test_coordination_count_of_h2():
