@@ -695,8 +695,11 @@ def run_serving(args, beta, sigma):
     ff = F.FlareGB(precision="bf16x3", max_nbr=64)
     ff.set_model(beta, sigma)
     res = []
-    with Server(ff, budget_bytes=150e9) as srv:
-        open_loop(srv, pool, rate=5000, seconds=0.5, seed=99)   # warm-up: grows the buffers
+    # batches are capped at 4M atoms (about 20 ms of device work), and device
+    # and pinned memory for such a batch is reserved up front
+    with Server(ff, budget_bytes=150e9, max_batch_atoms=4_000_000, reserve_atoms=4_000_000,
+                reserve_structs=4096) as srv:
+        open_loop(srv, pool, rate=5000, seconds=0.5, seed=99)   # warm-up
         for rate in SERVING_RATES:
             r = open_loop(srv, pool, rate=rate, seconds=args.serving_seconds, seed=4)
             res.append({k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()})
@@ -706,7 +709,8 @@ def run_serving(args, beta, sigma):
             "pool": f"64 structures, {min(len(p[1]) for p in pool)}-{max(len(p[1]) for p in pool)} atoms, "
                     f"mean {mean_atoms:.0f}", "precision": "bf16x3",
             "bytes_per_atom": st["bytes_per_atom"], "reserved_gb": round(st["reserved_bytes"] / 1e9, 2),
-            "max_batch_atoms": st["max_batch_atoms_seen"]}
+            "max_batch_atoms": st["max_batch_atoms_seen"], "batch_cap_atoms": 4_000_000,
+            "batches_overlapped": st["batches_overlapped"], "grow_events": st["grow_events"]}
 
 
 def main():
@@ -725,6 +729,8 @@ def main():
                     help="atoms sampled for the error report against the FP64 oracle")
     ap.add_argument("--serving-seconds", type=float, default=3.0,
                     help="open-loop serving run per arrival rate (0: skip)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the open-loop serving sweep and print its JSON line")
     ap.add_argument("--small", action="store_true",
                     help="64x64x32 slab + 1024 H2 (132k atoms) instead of the 2.1M-atom slab")
     args = ap.parse_args()
@@ -732,6 +738,14 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving_only:
+        import torch
+        from paper_2204_12573_gb300 import build
+        from paper_2204_12573_gb300 import synth
+        build.build()
+        torch.cuda.set_device(_env_rank()[2])
+        beta, sigma = synth.random_model()
+        print(json.dumps({"serving": run_serving(args, beta, sigma)}), flush=True)
     else:
         run_ours(args)
 

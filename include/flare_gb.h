@@ -354,17 +354,21 @@ int flr_build_neighbors_noalloc(const flr_system *sys, double r_list, int32_t ma
  * per atom, so a request's per-atom results do not depend on what else
  * shares its batch.)
  *
- * A server owns one worker thread and one CUDA stream on the context's
- * device.  flr_server_submit() queues a request (host inputs, host outputs)
- * and returns at once.  The worker takes queued requests in arrival order
- * into one batch while the batch's device memory stays within the budget
- * (and within max_batch_structs / max_batch_atoms), packs them into pinned
- * memory, copies them to the device in one transfer per array, plans the
- * bin grids on the host (no mid-batch synchronization), runs the neighbour
- * build and evaluation, copies the results back and writes them to each
- * request's output arrays.  Packing the next batch and unpacking the last
- * one overlap the GPU work of the current one.  Finished requests are
- * collected with flr_server_poll().
+ * A server owns one worker thread and two batch slots on the context's
+ * device; each slot has its own CUDA stream, pinned host arena, device
+ * input/output arrays and neighbour list.  flr_server_submit() queues a
+ * request (host inputs, host outputs) and returns at once.  The worker takes
+ * queued requests in arrival order into a free slot while the batch's device
+ * memory stays within the budget (and within max_batch_structs /
+ * max_batch_atoms), packs them into the slot's pinned arena, and enqueues on
+ * the slot's stream: one host-to-device copy per array, the bin-grid plan
+ * (made on the host, no mid-batch synchronization), the neighbour build,
+ * the evaluation, one device-to-host copy per array.  The two slots' batches
+ * overlap on the device: one batch's copies and neighbour build run while
+ * the other batch is evaluated.  Evaluations themselves run one at a time
+ * (they share the context's workspace).  When a batch's copies are done the
+ * worker writes each request's output arrays and reports the completions,
+ * which are collected with flr_server_poll().
  *
  * While a server exists its worker is the only user of the context: make no
  * other call on that context (or its neighbour lists) until
@@ -377,6 +381,10 @@ typedef struct {
                                     the model tables (a few MB) are outside it */
     int32_t max_batch_structs;   /* <= 0: no limit besides memory */
     int32_t max_batch_atoms;     /* <= 0: no limit besides memory */
+    int64_t reserve_atoms;       /* > 0: allocate device and pinned memory for batches of this many
+                                    atoms at creation, so no batch up to this size allocates;
+                                    0: grow on demand (doubling, synchronizes the device) */
+    int32_t reserve_structs;     /* structures per batch reserved with reserve_atoms (>= 1) */
 } flr_server_params;
 
 /* One structure to evaluate.  Inputs are host arrays read during
@@ -406,6 +414,12 @@ typedef struct {
     int64_t t_submit_ns;         /* steady-clock times: submitted, batch enqueued on the GPU, */
     int64_t t_start_ns;          /* outputs written */
     int64_t t_done_ns;
+    int32_t slot;                /* batch slot that ran the request (0 or 1) */
+    /* device timestamps of the request's batch (ms since the server was
+     * created, from CUDA events on the slot's stream): copies started,
+     * neighbour build done, evaluation started (after the previous batch's
+     * evaluation), evaluation done, outputs copied back */
+    float gpu_start_ms, gpu_built_ms, gpu_eval_start_ms, gpu_eval_end_ms, gpu_done_ms;
 } flr_completion;
 
 typedef struct {
@@ -417,14 +431,21 @@ typedef struct {
     int64_t reserved_bytes;      /* device memory the server holds now */
     int64_t bytes_per_atom;      /* admission cost of one atom */
     char last_error[256];        /* message of the last failed batch ("" if none) */
+    int64_t batches_overlapped;  /* batches enqueued while the other slot's batch was in flight */
+    int64_t grow_events;         /* times device memory had to grow under load (each synchronizes) */
+    double grow_ms, pack_ms, enqueue_ms, finish_ms;   /* worker host time: growing, packing inputs,
+                                                         enqueueing, writing outputs (ms, summed) */
 } flr_server_stats;
 
-/* Device bytes one atom of a batch costs (workspace, neighbour list row,
- * I/O), the figure the admission check multiplies by the atom count. */
+/* Device bytes one atom of a batch costs: the context's workspace once, and
+ * a neighbour-list row and the I/O arrays for each of the server's two
+ * slots; the figure the admission check multiplies by the atom count. */
 int flr_bytes_per_atom(const flr_ctx *ctx, int64_t *bytes);
 
 /* Start a server on ctx (the model must be set).  FLR_EBUDGET if the budget
- * cannot hold a single atom. */
+ * cannot hold a single atom or the reservation.  With reserve_atoms > 0 the
+ * call allocates the reservation (device and pinned host memory) before it
+ * returns. */
 int flr_server_create(flr_ctx *ctx, const flr_server_params *params, flr_server **out);
 
 /* Queue one request (thread-safe).  FLR_EBUDGET if the request alone
@@ -437,8 +458,8 @@ int flr_server_poll(flr_server *srv, flr_completion *out, int32_t max, int32_t *
 
 int flr_server_stats_read(flr_server *srv, flr_server_stats *stats);
 
-/* Stop the worker after the batch in flight and free the server.  Requests
- * still queued are dropped without a completion. */
+/* Stop the worker after the batches in flight and free the server.
+ * Requests still queued are dropped without a completion. */
 int flr_server_destroy(flr_server *srv);
 
 /* Measured FP32 FMA throughput of `device` (no counterpart in the paper: the

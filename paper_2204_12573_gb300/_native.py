@@ -85,7 +85,8 @@ class MDState(ctypes.Structure):
 
 class ServerParams(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch_structs", ctypes.c_int32),
-                ("max_batch_atoms", ctypes.c_int32)]
+                ("max_batch_atoms", ctypes.c_int32), ("reserve_atoms", ctypes.c_int64),
+                ("reserve_structs", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -98,14 +99,18 @@ class Request(ctypes.Structure):
 class Completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_structs", ctypes.c_int32),
                 ("batch_atoms", ctypes.c_int64), ("t_submit_ns", ctypes.c_int64), ("t_start_ns", ctypes.c_int64),
-                ("t_done_ns", ctypes.c_int64)]
+                ("t_done_ns", ctypes.c_int64), ("slot", ctypes.c_int32), ("gpu_start_ms", ctypes.c_float),
+                ("gpu_built_ms", ctypes.c_float), ("gpu_eval_start_ms", ctypes.c_float),
+                ("gpu_eval_end_ms", ctypes.c_float), ("gpu_done_ms", ctypes.c_float)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_int64), ("batches", ctypes.c_int64), ("atoms", ctypes.c_int64),
                 ("max_batch_atoms_seen", ctypes.c_int64), ("queued", ctypes.c_int64),
                 ("reserved_bytes", ctypes.c_int64), ("bytes_per_atom", ctypes.c_int64),
-                ("last_error", ctypes.c_char * 256)]
+                ("last_error", ctypes.c_char * 256), ("batches_overlapped", ctypes.c_int64),
+                ("grow_events", ctypes.c_int64), ("grow_ms", ctypes.c_double), ("pack_ms", ctypes.c_double),
+                ("enqueue_ms", ctypes.c_double), ("finish_ms", ctypes.c_double)]
 
 
 class FlareError(RuntimeError):

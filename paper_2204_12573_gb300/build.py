@@ -72,7 +72,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
                 raise RuntimeError(f"nvcc failed on {cmd[2]}")
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread"]
+        # every symbol must resolve at link time (a missing definition fails here, not at load)
+        cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread",
+                                                            "-Xlinker", "--no-undefined"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

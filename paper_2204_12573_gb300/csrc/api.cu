@@ -346,19 +346,21 @@ int srv_status_code(int st) { return status_to_code(st); }
 
 int srv_check_model(const flr_ctx *ctx) { return check_model(ctx); }
 
-// Device bytes per atom of one evaluation: the workspace (ensure_workspace),
-// a neighbour-list row and its per-atom tables (flr_nbrlist_create), and
-// the serving I/O arrays (positions, species, E, F, V, sigma).
-int64_t bytes_per_atom(const flr_ctx *ctx)
+// Device bytes per atom of one evaluation, in two parts: the context's
+// workspace (ensure_workspace) and what each batch slot of the serving loop
+// holds (a neighbour-list row and its per-atom tables, flr_nbrlist_create,
+// and the I/O arrays: positions, species, E, F, V, sigma).
+void bytes_per_atom_parts(const flr_ctx *ctx, int64_t *workspace, int64_t *slot)
 {
     const Dims &D = ctx->dims;
-    int64_t b = 4 * (int64_t)D.nA + 4;
-    for (int r = 0; r < 2; ++r) b += 4 * (int64_t)D.kp32[r] + 2 * 2 * (int64_t)D.kp64[r] + 4 * 3 * (int64_t)D.K[r];
-    b += 8 * 3 + 4 * 9 + 4 * 3;
-    b += 4 * (int64_t)ctx->p.max_nbr + 4 * 8 + 16 + 16 + 1;
-    b += 16 * (int64_t)ctx->p.max_nbr + 4;   // pair records
-    b += 16 + 4 + 4 * 6;
-    return b;
+    int64_t w = 4 * (int64_t)D.nA + 4;
+    for (int r = 0; r < 2; ++r) w += 4 * (int64_t)D.kp32[r] + 2 * 2 * (int64_t)D.kp64[r] + 4 * 3 * (int64_t)D.K[r];
+    w += 8 * 3 + 4 * 9 + 4 * 3 + 4;
+    int64_t l = 4 * (int64_t)ctx->p.max_nbr + 4 * 8 + 16 + 16 + 1;
+    l += 16 * (int64_t)ctx->p.max_nbr + 4;   // pair records
+    l += 16 + 4 + 4 * 4;                      // I/O arrays
+    *workspace = w;
+    *slot = l;
 }
 
 }  // namespace flr
@@ -710,6 +712,8 @@ int flr_nbrlist_create(flr_ctx *c, int32_t n_atoms, flr_nbrlist **out)
     nl->ctx = c;
     nl->n_cap = n_atoms;
     nl->max_nbr = c->p.max_nbr;
+    nl->status = c->status;
+    nl->sched = c->sched + 2;
     const size_t N = (size_t)std::max(n_atoms, 1);
     int s = dev_alloc(&nl->entries, N * nl->max_nbr, "nbrlist");
     if (s == FLR_OK) s = dev_alloc(&nl->count, N, "nbrlist");

@@ -96,6 +96,8 @@ struct flr_nbrlist {
     int32_t *blk_group;    // [n_blocks][8] per-block group counts
     flr::GroupTab *gtab;   // device
     int32_t *flags;        // device [4]: [0] rebuild needed, [1] rebuild counter
+    int *status;           // device status word the list build reports into (the context's by default)
+    int *sched;            // device work counter of the list build (one of the context's by default)
     float *bbox;           // device [structs_cap][8] fractional min / max
     long long nbins_cap;
     flr::Plan plan;        // structure 0 (the single-structure calls)
@@ -212,13 +214,28 @@ int srv_evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
                  flr_outputs *out, double *seg_totals, cudaStream_t st);
 int srv_status_code(int st);
 int srv_check_model(const flr_ctx *ctx);
-int64_t bytes_per_atom(const flr_ctx *ctx);
+void bytes_per_atom_parts(const flr_ctx *ctx, int64_t *workspace, int64_t *slot);
+// grow a list's per-structure tables and bin arrays ahead of use (so that
+// planning batches of up to n_structs structures and nbins bins allocates nothing)
+int nbrlist_reserve_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, long long nbins);
+// Descriptor kernel over atoms 0 .. n-1, or over order[0 .. m) with m read on
+// the device as *n_dev0 (+ *n_dev1), capped at n.
 int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
-                cudaStream_t st);
+                cudaStream_t st, const int32_t *order = nullptr, const int *n_dev0 = nullptr,
+                const int *n_dev1 = nullptr);
 int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat, float *norm,
                        cudaStream_t st);
 int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
-int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
+// only_full: take only the tiles of the two-species (full-descriptor) groups
+int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st, bool only_full = false);
+int encode_tile_map(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int box_cols, int box_rows,
+                    int swizzle_bytes);
+// The fused one-species kernel (descriptor -> tensor-core quadratic forms ->
+// E, V, sigma, g rows) over the one-species compaction groups; false from
+// fused_eligible when the context cannot take it (precision, compaction, N).
+bool fused_eligible(const flr_ctx *ctx);
+int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                 flr_outputs *out, cudaStream_t st);
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st);
 int launch_seg_totals(flr_ctx *ctx, const flr_nbrlist *nl, const flr_outputs *out, const float *vir_atom,

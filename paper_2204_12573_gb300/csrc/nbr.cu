@@ -915,6 +915,58 @@ void fill_shifts(const double *cl, float4 *out)
     }
 }
 
+// Per-structure tables of a list (offsets, image shifts, plans, bounding
+// boxes) for at least n_structs structures; grown by doubling (cudaFree and
+// cudaMalloc synchronize the device, so growth is kept rare).
+int grow_struct_tables(flr_nbrlist *nl, int n_structs)
+{
+    if (n_structs <= nl->structs_cap) return FLR_OK;
+    cudaFree(nl->offsets_d);
+    cudaFree(nl->shift_d);
+    cudaFree(nl->plans_d);
+    cudaFree(nl->bbox);
+    delete[] nl->plans_h;
+    delete[] nl->offsets_h;
+    const int cap = std::max(n_structs, 2 * nl->structs_cap);
+    nl->offsets_d = nullptr;
+    nl->shift_d = nullptr;
+    nl->plans_d = nullptr;
+    nl->bbox = nullptr;
+    cudaError_t e = cudaMalloc(&nl->offsets_d, sizeof(int32_t) * (cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&nl->shift_d, sizeof(float4) * 2 * kShiftCodes * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&nl->plans_d, sizeof(Plan) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&nl->bbox, sizeof(float) * 8 * cap);
+    nl->plans_h = new Plan[cap];
+    nl->offsets_h = new int32_t[cap + 1];
+    nl->structs_cap = cap;
+    if (e != cudaSuccess) return cuda_fail(e, "batch tables");
+    return FLR_OK;
+}
+
+// Bin arrays of a list for at least nbins bins (grown by doubling).
+int grow_bins(flr_nbrlist *nl, long long nbins)
+{
+    if (nbins + 1 <= nl->nbins_cap) return FLR_OK;
+    cudaFree(nl->bin_start);
+    cudaFree(nl->bin_fill);
+    nl->bin_start = nullptr;
+    nl->bin_fill = nullptr;
+    const long long cap = std::max(nbins + 1024, 2 * nl->nbins_cap);
+    cudaError_t e = cudaMalloc(&nl->bin_start, sizeof(int32_t) * (cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&nl->bin_fill, sizeof(int32_t) * (cap + 1));
+    if (e != cudaSuccess) return cuda_fail(e, "allocating bins");
+    nl->nbins_cap = cap;
+    return FLR_OK;
+}
+
+int nbrlist_reserve_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, long long nbins)
+{
+    (void)ctx;
+    int s = grow_struct_tables(nl, n_structs);
+    if (s == FLR_OK) s = grow_bins(nl, nbins);
+    return s;
+}
+
 int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offsets, const double *cells,
                const int32_t *pbc, const float4 *pos, int n, cudaStream_t st, const float *host_bb)
 {
@@ -927,26 +979,9 @@ int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offs
             set_error("neighbour build: batch offsets must be non-decreasing");
             return FLR_EINVAL;
         }
-    if (n_structs > nl->structs_cap) {
-        cudaFree(nl->offsets_d);
-        cudaFree(nl->shift_d);
-        cudaFree(nl->plans_d);
-        cudaFree(nl->bbox);
-        delete[] nl->plans_h;
-        delete[] nl->offsets_h;
-        const int cap = std::max(n_structs, 2 * nl->structs_cap);
-        nl->offsets_d = nullptr;
-        nl->shift_d = nullptr;
-        nl->plans_d = nullptr;
-        nl->bbox = nullptr;
-        cudaError_t e = cudaMalloc(&nl->offsets_d, sizeof(int32_t) * (cap + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&nl->shift_d, sizeof(float4) * 2 * kShiftCodes * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&nl->plans_d, sizeof(Plan) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&nl->bbox, sizeof(float) * 8 * cap);
-        nl->plans_h = new Plan[cap];
-        nl->offsets_h = new int32_t[cap + 1];
-        nl->structs_cap = cap;
-        if (e != cudaSuccess) return cuda_fail(e, "batch tables");
+    {
+        const int g = grow_struct_tables(nl, n_structs);
+        if (g != FLR_OK) return g;
     }
     nl->n_structs = n_structs;
     for (int s = 0; s <= n_structs; ++s) nl->offsets_h[s] = offsets[s];
@@ -1005,16 +1040,9 @@ int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offs
         return FLR_EINVAL;
     }
     nl->nbins_total = base;
-    if (base + 1 > nl->nbins_cap) {
-        cudaFree(nl->bin_start);
-        cudaFree(nl->bin_fill);
-        nl->bin_start = nullptr;
-        nl->bin_fill = nullptr;
-        const long long cap = base + 1024;
-        cudaError_t e = cudaMalloc(&nl->bin_start, sizeof(int32_t) * (cap + 1));
-        if (e == cudaSuccess) e = cudaMalloc(&nl->bin_fill, sizeof(int32_t) * (cap + 1));
-        if (e != cudaSuccess) return cuda_fail(e, "allocating bins");
-        nl->nbins_cap = cap;
+    {
+        const int g = grow_bins(nl, base);
+        if (g != FLR_OK) return g;
     }
     nl->plan = nl->plans_h[0];
     nl->planned = true;
@@ -1049,13 +1077,13 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     b.pos_ref = nl->pos_ref;
     b.gtab = nl->gtab;
     b.flags = nl->flags;
-    b.status = ctx->status;
+    b.status = nl->status;
     k_bin<<<std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8)), 256, 0, st>>>(b);
 
     // bin_start = exclusive scan of counts; block sums live in blk_group's tail
     int32_t *bsums = nl->blk_group + (size_t)8 * ((nl->n_cap + kGroupBlock - 1) / kGroupBlock + 1);
     k_scan_blocks<<<nbb, kScanBlock, 0, st>>>(nl->bin_fill, nl->bin_start, bsums, nbins, nl->flags);
-    k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, nl->bin_start + nbins, nl->flags, ctx->status);
+    k_scan_top<<<1, kScanBlock, 0, st>>>(bsums, nbb, nl->bin_start + nbins, nl->flags, nl->status);
     k_scan_add<<<nbb, kScanBlock, 0, st>>>(nl->bin_start, nl->bin_fill, bsums, nbins, nl->flags);
     k_scatter<<<std::max(1, std::min((n + 255) / 256, ctx->num_sms * 8)), 256, 0, st>>>(nl->atom_bin, nl->bin_fill,
                                                                                         nl->bin_atoms, n, nl->flags);
@@ -1086,9 +1114,9 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     r.group = nl->group;
     r.gtab = nl->gtab;
     r.flags = nl->flags;
-    r.status = ctx->status;
+    r.status = nl->status;
     r.nbins = nbins;
-    r.sched = ctx->sched + 2;
+    r.sched = nl->sched;
     {
         const cudaError_t e = cudaMemsetAsync(r.sched, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_fail(e, "list build work counter");

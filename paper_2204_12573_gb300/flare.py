@@ -289,6 +289,10 @@ class MDState:
     def xi(self):
         return float(self.c.xi)
 
+    @property
+    def eta(self):
+        return float(self.c.eta)
+
 
 def md_step(ff: FlareGB, state: MDState, nl: NbrList, n_steps: int, out, stream=None):
     """n_steps of velocity Verlet with on-device rebuild decisions (asynchronous)."""

@@ -24,10 +24,12 @@ FIELDS = ("energy", "forces", "variance", "sigma", "totals")
 
 
 class Server:
-    def __init__(self, ff, budget_bytes=150e9, max_batch_structs=0, max_batch_atoms=0):
+    def __init__(self, ff, budget_bytes=150e9, max_batch_structs=0, max_batch_atoms=0, reserve_atoms=0,
+                 reserve_structs=0):
         self.ff = ff
         self.lib = ff.lib
-        p = N.ServerParams(int(budget_bytes), int(max_batch_structs), int(max_batch_atoms))
+        p = N.ServerParams(int(budget_bytes), int(max_batch_structs), int(max_batch_atoms), int(reserve_atoms),
+                           int(reserve_structs))
         h = ctypes.c_void_p()
         N.check(self.lib.flr_server_create(ff.handle, ctypes.byref(p), ctypes.byref(h)))
         self.handle = h
@@ -91,7 +93,10 @@ class Server:
                 out = self._pending.pop(c.tag)
             res.append((c.tag, out, dict(status=c.status, batch_structs=c.batch_structs,
                                          batch_atoms=c.batch_atoms, t_submit_ns=c.t_submit_ns,
-                                         t_start_ns=c.t_start_ns, t_done_ns=c.t_done_ns)))
+                                         t_start_ns=c.t_start_ns, t_done_ns=c.t_done_ns, slot=c.slot,
+                                         gpu_start_ms=c.gpu_start_ms, gpu_built_ms=c.gpu_built_ms,
+                                         gpu_eval_start_ms=c.gpu_eval_start_ms,
+                                         gpu_eval_end_ms=c.gpu_eval_end_ms, gpu_done_ms=c.gpu_done_ms)))
         return res
 
     def wait_all(self, tags, timeout=120.0):
@@ -112,7 +117,9 @@ class Server:
         return dict(requests=s.requests, batches=s.batches, atoms=s.atoms,
                     max_batch_atoms_seen=s.max_batch_atoms_seen, queued=s.queued,
                     reserved_bytes=s.reserved_bytes, bytes_per_atom=s.bytes_per_atom,
-                    last_error=s.last_error.decode())
+                    last_error=s.last_error.decode(), batches_overlapped=s.batches_overlapped,
+                    grow_events=s.grow_events, grow_ms=s.grow_ms, pack_ms=s.pack_ms,
+                    enqueue_ms=s.enqueue_ms, finish_ms=s.finish_ms)
 
     def close(self):
         h = getattr(self, "handle", None)
@@ -157,7 +164,9 @@ def open_loop(server, pool, rate, seconds, seed=4, drain_timeout=120.0):
     lat = []
     atoms_done = [0]
     batch_sizes = []
+    batches = {}                 # (slot, gpu_start_ms) -> (built, eval start, eval end, done)
     errors = [0]
+    st0 = server.stats()
     finished = threading.Event()
 
     def collect():
@@ -169,6 +178,8 @@ def open_loop(server, pool, rate, seconds, seed=4, drain_timeout=120.0):
                 lat.append(c["t_done_ns"] - sched[tag][0])
                 atoms_done[0] += sched[tag][1]
                 batch_sizes.append(c["batch_structs"])
+                batches[(c["slot"], c["gpu_start_ms"])] = (c["gpu_built_ms"], c["gpu_eval_start_ms"],
+                                                           c["gpu_eval_end_ms"], c["gpu_done_ms"])
             if finished.is_set() and time.monotonic() > t_drain_end[0]:
                 break
 
@@ -193,10 +204,17 @@ def open_loop(server, pool, rate, seconds, seed=4, drain_timeout=120.0):
     th.join()
     t_last = time.monotonic_ns()
     wall = (t_last - t0) / 1e9
+    st1 = server.stats()
+    # device overlap: batches whose copies or neighbour build ran while the
+    # previous batch (other slot) was still being evaluated or copied back
+    ivals = sorted((k[1], v) for k, v in batches.items())   # (copies started, (built, eval0, eval1, done))
+    overlap = sum(1 for (_, prev), (s1, cur) in zip(ivals, ivals[1:]) if s1 < prev[2] and cur[0] > prev[1])
     return dict(rate=rate, seconds=seconds, requests=n_req, completed=len(lat), errors=errors[0],
                 p50_ms=percentile_ms(lat, 50), p99_ms=percentile_ms(lat, 99), mean_ms=(
                     float(np.mean(lat) / 1e6) if lat else None),
                 atoms_per_s=atoms_done[0] / wall, offered_atoms_per_s=float(
                     sum(len(pool[p][1]) for p in picks) / seconds),
                 mean_batch_structs=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
-                late_submits=late)
+                late_submits=late, batches=len(ivals), batches_overlapping_previous=overlap,
+                grow_events=st1["grow_events"] - st0["grow_events"],
+                worker_ms={k: round(st1[k] - st0[k], 2) for k in ("grow_ms", "pack_ms", "enqueue_ms", "finish_ms")})

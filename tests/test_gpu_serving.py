@@ -142,3 +142,43 @@ def test_open_loop_reports_latency():
         r = open_loop(srv, pool, rate=200, seconds=1.0, seed=4)
     assert r["errors"] == 0 and r["completed"] == r["requests"]
     assert 0 < r["p50_ms"] <= r["p99_ms"]
+
+
+def test_batches_overlap_on_the_device():
+    """The two slots' batches overlap on the device: while one batch is being
+    evaluated, the next batch's copies and neighbour build run (device
+    timestamps of the completions).  Results stay the same bits as alone,
+    and with the memory reserved up front nothing grows under load."""
+    from paper_2204_12573_gb300.serving import Server
+    ff = _ff()
+    rng = np.random.default_rng(5)
+    big = [synth.serving_structure(rng, 150000) for _ in range(3)]
+    with Server(ff, budget_bytes=60e9, max_batch_structs=2, reserve_atoms=300000, reserve_structs=4) as srv:
+        alone = {}
+        for k, s in enumerate(big):
+            t = _submit(srv, s)
+            alone[k] = srv.wait_all([t])[t][0]
+        order = [k % 3 for k in range(12)]
+        tags = [_submit(srv, big[k]) for k in order]
+        got = srv.wait_all(tags)
+        st = srv.stats()
+    for t, k in zip(tags, order):
+        out, c = got[t]
+        assert c["status"] == 0
+        for key in ("energy", "forces", "variance", "sigma"):
+            assert np.array_equal(out[key], alone[k][key]), key
+    batches = {}
+    for t in tags:
+        c = got[t][1]
+        batches[c["gpu_start_ms"]] = (c["slot"], c["gpu_built_ms"], c["gpu_eval_start_ms"], c["gpu_eval_end_ms"],
+                                      c["gpu_done_ms"])
+    iv = sorted(batches.items())
+    assert len(iv) >= 6      # at most 2 structures per batch (fewer when requests trickle in)
+    for start, (_, built, e0, e1, done) in iv:
+        assert start <= built <= e0 <= e1 <= done
+    # evaluations run one at a time, in order
+    for (_, a), (_, b) in zip(iv, iv[1:]):
+        assert b[2] >= a[3]
+    overlapped = sum(1 for (_, a), (s1, b) in zip(iv, iv[1:]) if s1 < a[3] and b[1] > a[2] and b[0] != a[0])
+    assert overlapped >= 1, iv
+    assert st["grow_events"] == 0 and st["batches_overlapped"] >= 1
