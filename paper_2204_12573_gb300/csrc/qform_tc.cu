@@ -30,6 +30,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "tc_dev.cuh"
 
 namespace flr {
 namespace {
@@ -49,7 +50,7 @@ static_assert(kParkCol0 + kParkCols <= 512, "accumulator and park must fit in 51
 constexpr int kParkGroups = (kParkCols / 16 + kSubs - 1) / kSubs;   // 16-column groups per epilogue thread
 constexpr int kEpiWarps = 4 * kSubs;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr unsigned long long kDeadlineNs = 2000000000ull;
+using namespace tc;
 
 struct TcArgs {
     int K[2];
@@ -70,120 +71,8 @@ struct TcArgs {
     int *ref_count;
     int ref_cap;
     int *status;
+    int only_full;               // take only the tiles of the two-species groups
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on timeout or when another role already aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
-{
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (globaltimer() - t0 > kDeadlineNs) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
-    d |= (uint64_t)1 << 16;                           // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
-    d |= (uint64_t)1 << 46;                           // descriptor version
-    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
-    return d;
-}
-template <bool BF16>
-__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
-{
-    if (BF16)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-    else
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-// store 16 columns of this warp's TMEM lane quarter (one row per thread);
-// tmem_wait_st makes them visible to later tcgen05.ld of the same thread
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-          "r"(__float_as_uint(v[15]))
-        : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
 
 struct TileInfo {
     int g, reg, row0, rend, nch;
@@ -335,6 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const TileInfo ti = decode_tile(T, a.nch, t);
+                if (a.only_full && !group_full(ti.g)) continue;
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
                 for (int ch = 0; ch < ti.nch && ok; ++ch) {
@@ -383,6 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             bool issued = false;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const TileInfo ti = decode_tile(T, a.nch, t);
+                if (a.only_full && !group_full(ti.g)) continue;
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
                 const int K = a.K[ti.reg];
@@ -443,8 +334,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
         int it = 0;
         int tl = 0;                             // tiles done by this CTA
         bool alive = true;
-        for (int t = blockIdx.x; t < total && alive; t += gridDim.x, ++tl) {
+        for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
             const TileInfo ti = decode_tile(T, a.nch, t);
+            if (a.only_full && !group_full(ti.g)) continue;
             const int K = a.K[ti.reg];
             const int row = ti.row0 + rloc;
             const bool valid = row < ti.rend;
@@ -604,6 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     if (q < a.ref_cap) a.ref_list[q] = atom;
                 }
             }
+            ++tl;   // tiles this CTA processed (the exchange buffer's parity)
         }
     }
     fence_before();
@@ -633,6 +526,17 @@ EncodeTiledFn get_encoder()
 
 int encode(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int box_rows)
 {
+    return encode_tile_map(m, ptr, bf16, cols, rows, 128 / (bf16 ? 2 : 4), box_rows, 128);
+}
+
+}  // namespace
+
+// A 2-D row-major tensor map (FP32 or BF16) with a box of box_cols x box_rows
+// and the given swizzle width (32, 64 or 128 bytes; box_cols x element size
+// must equal it).
+int encode_tile_map(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int box_cols, int box_rows,
+                    int swizzle_bytes)
+{
     EncodeTiledFn fn = get_encoder();
     if (!fn) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -641,18 +545,22 @@ int encode(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int b
     const int esz = bf16 ? 2 : 4;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw = swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                  : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                        : CU_TENSOR_MAP_SWIZZLE_128B;
     CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                    const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
         return FLR_ECUDA;
     }
     return FLR_OK;
 }
+
+namespace {
 
 int ensure_maps(flr_ctx *ctx)
 {
@@ -692,7 +600,7 @@ int ensure_maps(flr_ctx *ctx)
 
 }  // namespace
 
-int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st)
+int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st, bool only_full)
 {
     int s = ensure_maps(ctx);
     if (s != FLR_OK) return s;
@@ -721,6 +629,7 @@ int launch_qform_tc(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaS
     a.ref_count = ctx->ref_count;
     a.ref_cap = ctx->ws_n;
     a.status = ctx->status;
+    a.only_full = only_full ? 1 : 0;
     // ring + barriers (128 B) + the E / V exchange (2 tiles x kSubs sets x BM float4);
     // more than half of the SM's shared memory, so one CTA (holding all 512 TMEM
     // columns) runs per SM
