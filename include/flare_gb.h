@@ -198,6 +198,20 @@ int flr_descriptor_dims(const flr_ctx *ctx, int32_t *d_full, int32_t *d_single);
 /* Switch the quadratic-form precision of an existing context. */
 int flr_set_precision(flr_ctx *ctx, int32_t precision);
 
+/* Context options (flr_set_option).
+ * FLR_OPT_FUSED_ONE_SPECIES: 1 evaluates the atoms of the
+ * one-species compaction classes (Sec. V-B: most atoms of a slab) with one
+ * kernel that computes their descriptors, writes them as the BF16 hi/lo
+ * operand tile of the tensor cores in shared memory, and runs the quadratic
+ * forms and their epilogue (E, V, sigma, dE/dB) from there, so their
+ * descriptor rows never reach device memory; used with FLR_PREC_BF16X3 and
+ * compaction on.  0 (default): descriptor and quadratic-form kernels run
+ * separately.
+ * Results agree within the 3xBF16 error (the epilogue uses the hi + lo
+ * descriptor instead of the FP32 one). */
+#define FLR_OPT_FUSED_ONE_SPECIES 1
+int flr_set_option(flr_ctx *ctx, int32_t option, int32_t value);
+
 /* Upload the mapped model of central species `species` (Eq. 1, Eq. 2):
  * beta and sigma are HOST double[d_full][d_full], row-major, symmetric
  * (the library uses (M + M^T)/2 and reports the largest asymmetry through
@@ -479,7 +493,8 @@ int flr_fp32_fma_peak(int device, int32_t launches, double *tflops_best, double 
 #define FLR_KERNEL_FINALIZE 3     /* fixed point -> forces, half kick, FP64 totals */
 #define FLR_KERNEL_DRIFT 4        /* MD half kick + drift + displacement check */
 #define FLR_KERNEL_REBUILD 5      /* the (conditional) neighbour rebuild sequence */
-#define FLR_KERNEL_CLASSES 6
+#define FLR_KERNEL_FUSED 6        /* fused one-species descriptor + quadratic forms (FLR_OPT_FUSED_ONE_SPECIES) */
+#define FLR_KERNEL_CLASSES 7
 
 /* Per-kernel device timing: when on, every launch of the classes above is
  * bracketed by CUDA events recorded on its own stream (off by default;

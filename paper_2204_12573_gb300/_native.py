@@ -45,10 +45,11 @@ EXPORTED = [
     "flr_profile_enable", "flr_profile_read", "flr_build_neighbors_noalloc",
     "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
     "flr_bytes_per_atom", "flr_server_create", "flr_server_submit", "flr_server_poll", "flr_server_stats_read",
-    "flr_server_destroy", "flr_set_variance_mode", "flr_map_sgp", "flr_fp32_fma_peak",
+    "flr_server_destroy", "flr_set_variance_mode", "flr_map_sgp", "flr_fp32_fma_peak", "flr_set_option",
 ]
 
-KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild"]
+KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild", "fused"]
+OPT_FUSED_ONE_SPECIES = 1
 
 
 class Params(ctypes.Structure):
@@ -137,6 +138,7 @@ def lib():
             "flr_destroy": (ctypes.c_int, [P]),
             "flr_descriptor_dims": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
             "flr_set_precision": (ctypes.c_int, [P, ctypes.c_int32]),
+            "flr_set_option": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32]),
             "flr_set_variance_mode": (ctypes.c_int, [P, ctypes.c_int32]),
             "flr_set_model": (ctypes.c_int, [P, ctypes.c_int32, P, P]),
             "flr_map_sgp": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, P, P, P, ctypes.c_double, P, P, P]),

@@ -1,6 +1,7 @@
 // C ABI of libflare_gb: context, model upload, workspace, entry points.
 // See include/flare_gb.h for the contract of every exported function.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -255,19 +256,47 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
     if (n == 0) return FLR_OK;
     cudaError_t e = cudaMemsetAsync(ctx->Facc, 0, sizeof(long long) * 3 * (size_t)n, st);
     if (e != cudaSuccess) return cuda_fail(e, "clear force accumulators");
-    prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
-    int s = launch_desc(ctx, nl, pos, species, n, st);
-    prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
-    if (s != FLR_OK) return s;
-    prof_begin(ctx, FLR_KERNEL_QFORM, st);
-    if (ctx->var_mode == FLR_VAR_AUTO) {
-        e = cudaMemsetAsync(ctx->ref_count, 0, sizeof(int), st);
-        if (e != cudaSuccess) return cuda_fail(e, "clear variance queue");
+    int s = FLR_OK;
+    if (fused_eligible(ctx)) {
+        // two-species atoms: descriptor rows and tensor-core tiles as below;
+        // one-species atoms: the fused kernel.  Atoms without neighbours keep
+        // ||B|| = 0 from this clear.
+        e = cudaMemsetAsync(ctx->norm, 0, sizeof(float) * (size_t)n, st);
+        if (e == cudaSuccess && ctx->var_mode == FLR_VAR_AUTO) e = cudaMemsetAsync(ctx->ref_count, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "clear norms");
+        const int *cnt = reinterpret_cast<const int *>(reinterpret_cast<const char *>(nl->gtab) + offsetof(GroupTab, count));
+        prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
+        s = launch_desc(ctx, nl, pos, species, n, st, nl->atom_of_row, cnt + 0, cnt + 3);
+        prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
+        prof_begin(ctx, FLR_KERNEL_QFORM, st);
+        if (s == FLR_OK) s = launch_qform_tc(ctx, nl, out, st, true);
+        prof_end(ctx, FLR_KERNEL_QFORM, st);
+        prof_begin(ctx, FLR_KERNEL_FUSED, st);
+        if (s == FLR_OK) s = launch_fused(ctx, nl, pos, species, n, out, st);
+        prof_end(ctx, FLR_KERNEL_FUSED, st);
+        if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) {
+            // the FP64 variance reads FP32 descriptor rows: write them for the queued atoms
+            prof_begin(ctx, FLR_KERNEL_QFORM, st);
+            s = launch_desc(ctx, nl, pos, species, ctx->ws_n, st, ctx->ref_list, ctx->ref_count);
+            if (s == FLR_OK) s = launch_variance_fp64(ctx, nl, out, st);
+            prof_end(ctx, FLR_KERNEL_QFORM, st);
+        }
+        if (s != FLR_OK) return s;
+    } else {
+        prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
+        s = launch_desc(ctx, nl, pos, species, n, st);
+        prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
+        if (s != FLR_OK) return s;
+        prof_begin(ctx, FLR_KERNEL_QFORM, st);
+        if (ctx->var_mode == FLR_VAR_AUTO) {
+            e = cudaMemsetAsync(ctx->ref_count, 0, sizeof(int), st);
+            if (e != cudaSuccess) return cuda_fail(e, "clear variance queue");
+        }
+        s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, out, st) : launch_qform_tc(ctx, nl, out, st);
+        if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) s = launch_variance_fp64(ctx, nl, out, st);
+        prof_end(ctx, FLR_KERNEL_QFORM, st);
+        if (s != FLR_OK) return s;
     }
-    s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, out, st) : launch_qform_tc(ctx, nl, out, st);
-    if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) s = launch_variance_fp64(ctx, nl, out, st);
-    prof_end(ctx, FLR_KERNEL_QFORM, st);
-    if (s != FLR_OK) return s;
     prof_begin(ctx, FLR_KERNEL_FORCE, st);
     s = launch_force(ctx, nl, pos, species, n, out, seg_totals ? ctx->vir_atom : nullptr, nullptr, st);
     prof_end(ctx, FLR_KERNEL_FORCE, st);
@@ -395,6 +424,7 @@ int flr_create(const flr_params *p, int device, flr_ctx **out)
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     flr_ctx *c = new flr_ctx();
+    c->use_fused = 0;   // the separate kernels are faster on GB300 so far
     std::memset(static_cast<void *>(c), 0, sizeof(flr_ctx));
     c->p = *p;
     c->device = device;
@@ -463,6 +493,7 @@ int flr_destroy(flr_ctx *c)
         delete[] c->beta_h[s];
         delete[] c->sigma_h[s];
     }
+    free_fused_maps(c);
     cudaFree(c->tab_full);
     cudaFree(c->tab_single);
     cudaFree(c->status);
@@ -498,6 +529,16 @@ int flr_set_precision(flr_ctx *c, int32_t precision)
         return FLR_EINVAL;
     }
     c->p.precision = precision;
+    return FLR_OK;
+}
+
+int flr_set_option(flr_ctx *c, int32_t option, int32_t value)
+{
+    if (!c || option != FLR_OPT_FUSED_ONE_SPECIES || (value != 0 && value != 1)) {
+        set_error("flr_set_option: invalid option or value");
+        return FLR_EINVAL;
+    }
+    c->use_fused = value;
     return FLR_OK;
 }
 

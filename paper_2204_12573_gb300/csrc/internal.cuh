@@ -165,6 +165,8 @@ struct flr_ctx {
     float *scratch_out;        // [3][n] E, V, sigma of the backward pass
     double *partials;          // [n_blocks][16]
     int n_part;
+    void *fmaps;               // tensor maps of the fused one-species kernel (built once per context)
+    int use_fused;             // FLR_OPT_FUSED_ONE_SPECIES
     TcMaps *maps;              // host copy of the current tensor maps
     int maps_n;                // workspace size the maps were encoded for
     int maps_prec;
@@ -236,6 +238,7 @@ int encode_tile_map(CUtensorMap *m, const void *ptr, bool bf16, int cols, int ro
 bool fused_eligible(const flr_ctx *ctx);
 int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, cudaStream_t st);
+void free_fused_maps(flr_ctx *ctx);
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st);
 int launch_seg_totals(flr_ctx *ctx, const flr_nbrlist *nl, const flr_outputs *out, const float *vir_atom,

@@ -90,6 +90,11 @@ class FlareGB:
         N.check(self.lib.flr_set_precision(self.handle, N.PREC[precision]))
         self.precision = precision
 
+    def set_fused(self, on: bool):
+        """FLR_OPT_FUSED_ONE_SPECIES: one-species atoms in the fused descriptor +
+        tensor-core kernel (3xBF16 with compaction), or separate kernels."""
+        N.check(self.lib.flr_set_option(self.handle, N.OPT_FUSED_ONE_SPECIES, 1 if on else 0))
+
     def set_variance_mode(self, mode: str):
         """"auto" (FP32 quadratic form, FP64 re-evaluation of cancelled
         variances), "direct" (FP32 only) or "factored" (V = |L^T d|^2)."""

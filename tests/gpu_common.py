@@ -85,11 +85,16 @@ def decode_entries(entries, count):
     return out[order]
 
 
-def gpu_run(struct, beta, sigma, precision="fp32", compaction=True, max_nbr=64, n_max=8, want_desc=False):
+def gpu_run(struct, beta, sigma, precision="fp32", compaction=True, max_nbr=64, n_max=8, want_desc=False,
+            fused=None, profile=False):
     import torch
     from paper_2204_12573_gb300 import flare as F
     ff = F.FlareGB(n_max=n_max, precision=precision, compaction=compaction, max_nbr=max_nbr)
     ff.set_model(beta, sigma)
+    if fused is not None:
+        ff.set_fused(fused)
+    if profile:
+        ff.profile(True)
     pos4 = synth.as_f32_positions(struct.pos)
     sysg = F.System.from_numpy(pos4, struct.species, struct.cell, struct.pbc)
     nl = ff.nbrlist(struct.n_atoms)
@@ -102,6 +107,8 @@ def gpu_run(struct, beta, sigma, precision="fp32", compaction=True, max_nbr=64, 
         res["norm"] = norm.cpu().numpy()
     ff.sync()
     res["entries"], res["count"], res["group"] = nl.view(struct.n_atoms)
+    if profile:
+        res["profile"] = ff.profile_read()
     torch.cuda.synchronize()
     return res, ff, nl, sysg
 
@@ -112,12 +119,13 @@ def oracle_run(struct, beta, sigma, n_max=8, skin=0.5):
     return O.energy_forces(h, pos, struct.species, struct.cell, struct.pbc, beta, sigma, skin=skin)
 
 
-def compare_mixed(g, o, precision, species, beta, sigma, beta_norm=1.0, f_tol=F_TOL_MIXED):
+def compare_mixed(g, o, precision, species, beta, sigma, beta_norm=1.0, f_tol=F_TOL_MIXED, d_full=544,
+                  d_single=144):
     """Mixed-precision results against the oracle: forces within f_tol
     (eV/A), energy and variance within the per-atom bounds above."""
     groups = g["group"].cpu().numpy() if hasattr(g["group"], "cpu") else np.asarray(g["group"])
     bE, bV = mixed_bounds(precision, o["dhat"], np.asarray(species), groups, beta, sigma, o["E"], o["V"],
-                          beta_norm=beta_norm)
+                          d_full=d_full, d_single=d_single, beta_norm=beta_norm)
     dE = np.abs(g["energy"] - o["E"])
     dV = np.abs(g["variance"] - o["V"])
     dF = np.abs(g["forces"] - o["F"]).max()

@@ -146,14 +146,30 @@ def test_fp32_slabs_match_oracle(k):
     compare_efv(g, o)
 
 
-@pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
-def test_mixed_precision_matches_oracle(precision):
+@pytest.mark.parametrize("precision,fused", [("tf32", None), ("bf16x3", True), ("bf16x3", False)])
+def test_mixed_precision_matches_oracle(precision, fused):
     """Forces within 1e-3 eV/A; every atom's energy and variance within the
-    bounds derived from the split-precision products (gpu_common)."""
+    bounds derived from the split-precision products (gpu_common).  3xBF16
+    runs with the one-species atoms in the fused descriptor + tensor-core
+    kernel and with separate kernels; the fused kernel must have run."""
     for s in [_tiny()] + _slabs(3):
-        g, *_ = gpu_run(s, BETA, SIGMA, precision=precision)
+        g, *_ = gpu_run(s, BETA, SIGMA, precision=precision, fused=fused, profile=True)
         o = oracle_run(s, BETA, SIGMA)
         compare_mixed(g, o, precision, s.species, BETA, SIGMA)
+        assert (g["profile"]["fused"][1] > 0) == bool(fused)
+
+
+def test_fused_and_separate_kernels_agree():
+    """The fused one-species path and the separate kernels compute the same
+    forms; their 3xBF16 results differ only by the epilogue's hi + lo
+    descriptor (relative 2^-16) against the FP32 row."""
+    s = _slabs(3)[2]
+    a, *_ = gpu_run(s, BETA, SIGMA, precision="bf16x3", fused=True)
+    b, *_ = gpu_run(s, BETA, SIGMA, precision="bf16x3", fused=False)
+    assert np.array_equal(a["group"].cpu().numpy(), b["group"].cpu().numpy())
+    assert np.abs(a["energy"] - b["energy"]).max() <= 1e-4
+    assert np.abs(a["forces"] - b["forces"]).max() <= 2e-4
+    assert (np.abs(a["variance"] - b["variance"]) <= 1e-4 * np.abs(b["variance"]) + 1e-5).all()
 
 
 @pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
@@ -201,6 +217,10 @@ def test_paper_dimensions_n7():
     assert (ff.d_full, ff.d_single) == (420, 112)
     o = oracle_run(s, b7, s7, n_max=7)
     compare_efv(g, o)
+    # the fused one-species kernel at N = 7 (K = 112, one MMA column half of 112)
+    gb, *_ = gpu_run(s, b7, s7, n_max=7, precision="bf16x3", fused=True, profile=True)
+    assert gb["profile"]["fused"][1] > 0
+    compare_mixed(gb, o, "bf16x3", s.species, b7, s7, d_full=420, d_single=112)
 
 
 # ------------------------------------------------------------ edge cases
