@@ -47,37 +47,41 @@ struct DescArgs {
     int *sched;                // work counter, zero at launch
 };
 
-// Per warp, the staged basis of a batch of pairs and, once the pairs are
-// done, the rows of A and the unnormalized B2 (kept here between the norm
-// reduction and the scaled stores instead of in registers) share one region.
-template <int N>
+// Per warp, the staged basis of a batch of up to BATCH pairs and, once the
+// pairs are done, the rows of A and the unnormalized B2 (kept here between
+// the norm reduction and the scaled stores instead of in registers) share one
+// region.  ONE: only one-species atoms are taken (B2 of one block).
+template <int N, int BATCH = 32, bool ONE = false>
 union __align__(16) DescStage {
     struct {
-        float Y[32][kYStride];           // harmonics of up to 32 staged pairs
-        float Rf[N][33];                 // their radial values, pair index fastest
+        float Y[BATCH][kYStride];        // harmonics of the staged pairs
+        float Rf[N][BATCH + 1];          // their radial values, pair index fastest
     } p;
     struct {
         float A[2 * N * kDescAStride];
-        float4 B[(2 * N) * (2 * N + 1) / 2];   // unnormalized B2 of the class's channel pairs
+        float4 B[ONE ? N * (N + 1) / 2 : (2 * N) * (2 * N + 1) / 2];   // unnormalized B2 of the class's channel pairs
     } b;
 };
 
 // One warp's shared memory: the compacted pairs inside r_cut (r_ij and the
-// neighbour's species) and the staging region.
-template <int N>
+// neighbour's species; a batch is evaluated once BATCH are queued, so fewer
+// than BATCH + 32 wait at a time) and the staging region.
+template <int N, int BATCH = 32, bool ONE = false>
 struct __align__(16) DescWarp {
-    float4 rec[64];
-    DescStage<N> st;
+    static constexpr int kBatch = BATCH;
+    static constexpr bool kOne = ONE;
+    float4 rec[BATCH + 32];
+    DescStage<N, BATCH, ONE> st;
 };
 
-// Basis of up to 32 staged pairs (lane p evaluates pair p), then the lanes
+// Basis of up to BATCH staged pairs (lane p evaluates pair p), then the lanes
 // that own A coefficients accumulate over them.  The basis is stored with the
 // pairs of a species-0 neighbour first (each species keeps list order, so
 // every accumulator sums in the same order as an unsorted pass), so the
 // accumulation picks the accumulator by a warp-uniform index test instead of
 // loading each pair's species.
-template <int N>
-__device__ __forceinline__ void desc_batch(DescWarp<N> &dw, int lane, int m, float rc, float acc0[4], float acc1[4])
+template <int N, class W>
+__device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, float acc0[4], float acc1[4])
 {
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     if (lane < m) r = dw.rec[lane];
@@ -167,13 +171,14 @@ __device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
 // contracts B2 of the class's channel pairs into dw.st.b.B (unnormalized),
 // writes ||B|| to norm[i] and returns it.  The caller scales B by 1 / ||B||
 // and writes the normalized row where its quadratic-form kernel reads it.
-template <int N>
-__device__ __forceinline__ float desc_atom(const DescArgs &a, DescWarp<N> &dw, int lane, const DescPre &cur, int i)
+template <int N, class W>
+__device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, const DescPre &cur, int i)
 {
     constexpr int C = 2 * N;
+    constexpr int BATCH = W::kBatch;
     constexpr int NPF = C * (C + 1) / 2;          // channel pairs of the full descriptor
     constexpr int NPS = N * (N + 1) / 2;          // channel pairs of a one-species block
-    constexpr int MAXP = (NPF + 31) / 32;
+    constexpr int MAXP = ((W::kOne ? NPS : NPF) + 31) / 32;
     const float rc = a.rcut, rc2 = rc * rc;
     const int g = cur.g;
     const int cls = group_cls(g);
@@ -210,10 +215,12 @@ __device__ __forceinline__ float desc_atom(const DescArgs &a, DescWarp<N> &dw, i
         nv += __popc(m);
         np += __popc(m);
         __syncwarp();
-        if (nv >= 32) {
-            desc_batch<N>(dw, lane, 32, rc, acc0, acc1);
-            if (lane < nv - 32) dw.rec[lane] = dw.rec[32 + lane];
-            nv -= 32;
+        while (nv >= BATCH) {
+            desc_batch<N>(dw, lane, BATCH, rc, acc0, acc1);
+            const float4 rest = lane < nv - BATCH ? dw.rec[BATCH + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            if (lane < nv - BATCH) dw.rec[lane] = rest;
+            nv -= BATCH;
             __syncwarp();
         }
     }
@@ -237,7 +244,7 @@ __device__ __forceinline__ float desc_atom(const DescArgs &a, DescWarp<N> &dw, i
     __syncwarp();
 
     // B2 of the class's channel pairs, four l per pair
-    const int npairs = cls == 0 ? NPF : NPS;
+    const int npairs = (W::kOne || cls != 0) ? NPS : NPF;
     const int choff = cls == 0 ? 0 : (cls - 1) * N;
     const int32_t *tab = a.tab[reg];
     float4 *sB = dw.st.b.B;

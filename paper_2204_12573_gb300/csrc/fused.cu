@@ -21,10 +21,16 @@
 // One CTA per SM (the A tile, the B ring and the workers' staging fill the
 // shared memory; the accumulator and the parked beta d take 432 of the 512
 // tensor-memory columns).  Warp 0 allocates tensor memory and its lane 0
-// issues the TMA loads; warp 1's lane 0 issues the MMAs; warps 2..17 are the
-// workers.  A tile goes: workers write the A tile (after every worker has
-// finished the previous tile's epilogue, which read the A tile) -> MMAs ->
-// workers read the accumulator.  Tiles are taken round-robin by CTA.
+// issues the TMA loads; warp 1's lane 0 issues the MMAs; warps 2..29 are the
+// 28 workers (7 per tensor-memory lane quarter).  The A tile holds K = 144
+// columns without padding: two 64-column atoms with 128-byte swizzle and a
+// 16-column tail with 32-byte swizzle, each MMA K step addressing its own
+// block.  Tiles are taken round-robin by CTA; within the CTA's tile sequence
+// the workers take rows one at a time from a shared-memory counter, so a
+// worker that draws a row of the next tile computes its descriptor while the
+// current tile's MMAs run, then does its share of the current tile's
+// epilogue, and writes the row into the A tile once every worker has
+// finished that epilogue (the epilogue reads the A tile).
 //
 // Every wait is bounded (about 2 s of %globaltimer); on expiry the kernel
 // records FLR_ETIMEOUT, stops, waits (bounded) for its own copies and MMAs,
@@ -40,17 +46,21 @@ namespace {
 using namespace tc;
 
 constexpr int kFM = 128;                        // atoms per tile (MMA M)
-constexpr int kFWorkers = 16;                   // worker warps, 4 per tensor-memory lane quarter
+constexpr int kFWorkers = 28;                   // worker warps, 7 per tensor-memory lane quarter
 constexpr int kFSubs = kFWorkers / 4;           // workers per lane quarter
 constexpr int kFThreads = 64 + 32 * kFWorkers;
-constexpr int kFStages = 2;                     // B ring stages (16-column K blocks, hi and lo)
-constexpr int kFAtomsPerWorker = kFM / kFWorkers;
+constexpr int kFStages = 3;                     // B ring stages (16-column K blocks, hi and lo)
+constexpr int kFBatch = 16;                     // pairs per basis batch of a worker's descriptor
+
+template <int N>
+using FWarp = DescWarp<N, kFBatch, true>;
 
 template <int N>
 struct FDims {
     static constexpr int K = N * (N + 1) / 2 * 4;       // one-species descriptor length (144 for N = 8)
-    static constexpr int KP = (K + 63) / 64 * 64;       // A row padded to 64-column swizzle atoms
-    static constexpr int A_PART = kFM * KP * 2;         // bytes of the hi (or lo) A tile
+    static constexpr int NA = K / 64;                   // 64-column atoms with 128-byte swizzle
+    static constexpr int NT = (K - 64 * NA) / 16;       // 16-column tail blocks with 32-byte swizzle
+    static constexpr int A_PART = NA * kFM * 128 + NT * kFM * 32;   // bytes of the hi (or lo) A tile
     static constexpr int KSTEPS = K / 16;               // MMA K steps of 16 BF16 values
     static constexpr int B_HALF = K * 32;               // K rows of a 16-column K block (32 bytes a row)
     static constexpr int B_PART = 2 * B_HALF;           // [beta; Sigma] rows of a K block
@@ -66,11 +76,12 @@ struct FusedSmem {
     static constexpr int OFF_A = 0;
     static constexpr int OFF_B = 2 * FDims<N>::A_PART;
     static constexpr int OFF_W = OFF_B + kFStages * FDims<N>::STAGE;
-    static constexpr int OFF_X = OFF_W + kFWorkers * (int)sizeof(DescWarp<N>);
+    static constexpr int OFF_X = OFF_W + kFWorkers * (int)sizeof(FWarp<N>);
     static constexpr int OFF_R = OFF_X + kFSubs * kFM * 16;
     static constexpr int OFF_BAR = OFF_R + 2 * kFM * 4;
     static constexpr int N_BARS = 2 * kFStages + 4 + 4;   // full, empty, afull, accfull, wfree, drain, evx[4]
-    static constexpr int BYTES = OFF_BAR + N_BARS * 8 + 16;
+    static constexpr int BYTES = OFF_BAR + N_BARS * 8 + 16;   // + tensor-memory address, abort flag, row counter
+    static_assert(FDims<N>::A_PART % 1024 == 0, "A parts must keep 1024-byte alignment");
 };
 
 struct FusedMaps {
@@ -118,31 +129,46 @@ __device__ __forceinline__ FTile fused_decode(const GroupTab &T, const int pre[5
     return ti;
 }
 
-// byte offset of (row r, column c) in a 128-byte-swizzled K-major A tile of
-// 64-column atoms (8 rows x 128 bytes per swizzle block; the 16-byte chunk
-// index is XORed with the row within the block)
+// Byte offset of (row r, column c) in the K-major A tile: columns below
+// 64 NA lie in 64-column atoms with 128-byte swizzle (8 rows x 128 bytes per
+// swizzle block, the 16-byte chunk index XORed with the row within the
+// block), the rest in 16-column blocks with 32-byte swizzle (8 rows x 32
+// bytes per block, the 16-byte half XORed with bit 2 of the row).
+template <int N>
 __device__ __forceinline__ uint32_t a_off(int r, int c)
 {
-    return (uint32_t)((c >> 6) * (kFM * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
-                      ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1));
+    constexpr int NA = FDims<N>::NA;
+    if (c < 64 * NA)
+        return (uint32_t)((c >> 6) * (kFM * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
+                          ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1));
+    const int ct = c - 64 * NA;
+    return (uint32_t)(NA * (kFM * 128) + (ct >> 4) * (kFM * 32) + (r >> 3) * 256 + (r & 7) * 32 +
+                      ((((ct & 15) >> 3) ^ ((r >> 2) & 1)) << 4) + ((ct & 7) << 1));
 }
 
-// 16 columns c .. c+15 of row r of d, rebuilt as hi + lo from the A tile
-__device__ __forceinline__ void read_d16(const uint8_t *sAhi, const uint8_t *sAlo, int r, int c, float v[16])
+// Shared-memory descriptor of MMA K step ks of an A part at byte address base
+template <int N>
+__device__ __forceinline__ uint64_t a_desc(uint32_t base, int ks)
 {
+    constexpr int NA = FDims<N>::NA;
+    if (ks < 4 * NA) return sw128_desc(base + (uint32_t)((ks >> 2) * (kFM * 128) + (ks & 3) * 32));
+    return sw32_desc(base + (uint32_t)(NA * (kFM * 128) + (ks - 4 * NA) * (kFM * 32)));
+}
+
+// 8 columns c .. c+7 of row r of d (c a multiple of 8), rebuilt as hi + lo from the A tile
+template <int N>
+__device__ __forceinline__ void read_d8(const uint8_t *sAhi, const uint8_t *sAlo, int r, int c, float v[8])
+{
+    const uint32_t o = a_off<N>(r, c);
+    const uint4 hi = *reinterpret_cast<const uint4 *>(sAhi + o);
+    const uint4 lo = *reinterpret_cast<const uint4 *>(sAlo + o);
+    const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t o = a_off(r, c + 8 * h);
-        const uint4 hi = *reinterpret_cast<const uint4 *>(sAhi + o);
-        const uint4 lo = *reinterpret_cast<const uint4 *>(sAlo + o);
-        const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[k]));
-            const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[k]));
-            v[8 * h + 2 * k] = fh.x + fl.x;
-            v[8 * h + 2 * k + 1] = fh.y + fl.y;
-        }
+    for (int k = 0; k < 4; ++k) {
+        const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[k]));
+        const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[k]));
+        v[2 * k] = fh.x + fl.x;
+        v[2 * k + 1] = fh.y + fl.y;
     }
 }
 
@@ -172,13 +198,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
     uint8_t *sAhi = base + L::OFF_A;
     uint8_t *sAlo = base + L::OFF_A + D::A_PART;
     uint8_t *sB = base + L::OFF_B;
-    DescWarp<N> *sW = reinterpret_cast<DescWarp<N> *>(base + L::OFF_W);
+    FWarp<N> *sW = reinterpret_cast<FWarp<N> *>(base + L::OFF_W);
     float4 *evx_buf = reinterpret_cast<float4 *>(base + L::OFF_X);
     int *atom_s = reinterpret_cast<int *>(base + L::OFF_R);
     float *norm_s = reinterpret_cast<float *>(base + L::OFF_R + kFM * 4);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + L::OFF_BAR);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + L::N_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    int *slot_ctr = reinterpret_cast<int *>(tmem_holder + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kFStages);
@@ -196,12 +223,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(afull, kFWorkers);
+        mbar_init(afull, kFM);          // one arrival per row written
         mbar_init(accfull, 1);
         mbar_init(wfree, kFWorkers);
         mbar_init(drain, 1);
         for (int q = 0; q < 4; ++q) mbar_init(evx0 + 8 * q, kFSubs);
         *abort_flag = 0;
+        *slot_ctr = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before();
@@ -211,6 +239,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
     const GroupTab &T = *a.gtab;
     int pre[5];
     const int total = fused_tiles(T, pre);
+    // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int my_tiles = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -220,8 +250,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             int last_phase[kFStages];
             for (int s = 0; s < kFStages; ++s) last_phase[s] = -1;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const FTile ti = fused_decode(T, pre, t);
+            for (int tl = 0; tl < my_tiles && ok; ++tl) {
+                const FTile ti = fused_decode(T, pre, (int)blockIdx.x + tl * (int)gridDim.x);
                 for (int ks = 0; ks < D::KSTEPS; ++ks) {
                     if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
                     const uint32_t fb = full0 + 8 * stage;
@@ -256,17 +286,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true, issued = false;
-            int tl = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
-                // the workers have written this tile's A rows (and are done with the accumulator)
+            const uint32_t ahi0 = smem_u32(sAhi), alo0 = smem_u32(sAlo);
+            for (int tl = 0; tl < my_tiles && ok; ++tl) {
+                // all 128 rows of this tile are written (and every worker is done
+                // with the previous tile's accumulator)
                 if (!mbar_wait(afull, (uint32_t)(tl & 1), abort_flag)) { ok = false; break; }
                 fence_after();
                 for (int ks = 0; ks < D::KSTEPS; ++ks) {
                     if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
                     fence_after();
-                    const uint32_t aoff = (uint32_t)((ks >> 2) * (kFM * 128) + (ks & 3) * 32);
-                    const uint64_t ahi = sw128_desc(smem_u32(sAhi) + aoff);
-                    const uint64_t alo = sw128_desc(smem_u32(sAlo) + aoff);
+                    const uint64_t ahi = a_desc<N>(ahi0, ks), alo = a_desc<N>(alo0, ks);
                     const uint32_t sb = smem_u32(sB + stage * D::STAGE);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -295,89 +324,37 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             }
         }
     } else {
-        // ---------------- workers: descriptors, then the epilogue ----------------
+        // ---------------- workers: descriptors, then their share of each epilogue ----------------
         const int wk = warp - 2;                 // worker index
         const int qw = warp & 3;                 // tensor-memory lane quarter this warp may access
         const int sub = wk >> 2;                 // which column groups of that quarter
         const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
-        DescWarp<N> &dw = sW[wk];
+        FWarp<N> &dw = sW[wk];
         const DescArgs &da = a.d;
         bool alive = true;
-        int tl = 0;
-        // the atoms of this warp: rows wk + 16 j of each tile, j = 0..7; the
-        // next atom's scalars and first list entries are loaded one atom ahead
-        int t = blockIdx.x;
-        FTile ti = t < total ? fused_decode(T, pre, t) : FTile{0, 0, 0};
-        auto atom_at = [&](const FTile &x, int j) -> int {
-            const int row = x.row0 + wk + kFWorkers * j;
+        int tl_epi = 0;                          // the next tile whose epilogue this warp owes
+        const int n_slots = my_tiles * kFM;
+        // rows are drawn one at a time; the next row is drawn (and its atom's
+        // scalars and first list entries loaded) while the current one is computed
+        auto draw = [&]() -> int {
+            int v = 0;
+            if (lane == 0) v = atomicAdd(slot_ctr, 1);
+            return __shfl_sync(0xffffffffu, v, 0);
+        };
+        auto atom_of_slot = [&](int sl) -> int {
+            if (sl >= n_slots) return -1;
+            const FTile x = fused_decode(T, pre, (int)blockIdx.x + (sl / kFM) * (int)gridDim.x);
+            const int row = x.row0 + sl % kFM;
             return row < x.rend ? __ldg(a.atom_of_row1 + row) : -1;
         };
-        int i_cur = t < total ? atom_at(ti, 0) : -1;
-        DescPre cur = desc_preload(da, i_cur < 0 ? 0x7fffffff : i_cur, 0x7fffffff, lane);
-        for (; t < total && alive; t += gridDim.x, ++tl) {
-            const int tn = t + gridDim.x;
-            const FTile tin = tn < total ? fused_decode(T, pre, tn) : FTile{0, 0, 0};
-            // ---- descriptor pass over this warp's 8 rows ----
-            for (int j = 0; j < kFAtomsPerWorker; ++j) {
-                const int r = wk + kFWorkers * j;
-                const int i = i_cur;
-                const int i_nx = j + 1 < kFAtomsPerWorker ? atom_at(ti, j + 1) : (tn < total ? atom_at(tin, 0) : -1);
-                const DescPre nx = desc_preload(da, i_nx < 0 ? 0x7fffffff : i_nx, 0x7fffffff, lane);
-                float nrm = 0.f;
-                if (i >= 0) nrm = desc_atom<N>(da, dw, lane, cur, i);
-                if (j == 0 && tl > 0) {
-                    // every worker has finished the previous tile's epilogue (it reads the A tile and the row table)
-                    if (!warp_wait(wfree, (uint32_t)((tl - 1) & 1), lane, abort_flag, a.status)) {
-                        alive = false;
-                        break;
-                    }
-                }
-                if (i >= 0) {
-                    const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
-                    const float4 *sBv = dw.st.b.B;
-                    constexpr int NPS = K / 4;
-#pragma unroll
-                    for (int k = 0; k < (NPS + 31) / 32; ++k) {
-                        const int tt = lane + 32 * k;
-                        if (tt < NPS) {
-                            const float4 bb = sBv[tt];
-                            const float4 v = make_float4(bb.x * inv, bb.y * inv, bb.z * inv, bb.w * inv);
-                            const __nv_bfloat162 hi01 = __floats2bfloat162_rn(v.x, v.y);
-                            const __nv_bfloat162 hi23 = __floats2bfloat162_rn(v.z, v.w);
-                            const float2 f01 = __bfloat1622float2(hi01), f23 = __bfloat1622float2(hi23);
-                            const __nv_bfloat162 lo01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
-                            const __nv_bfloat162 lo23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
-                            uint2 hv, lv;
-                            hv.x = *reinterpret_cast<const uint32_t *>(&hi01);
-                            hv.y = *reinterpret_cast<const uint32_t *>(&hi23);
-                            lv.x = *reinterpret_cast<const uint32_t *>(&lo01);
-                            lv.y = *reinterpret_cast<const uint32_t *>(&lo23);
-                            const uint32_t o = a_off(r, 4 * tt);
-                            *reinterpret_cast<uint2 *>(sAhi + o) = hv;
-                            *reinterpret_cast<uint2 *>(sAlo + o) = lv;
-                        }
-                    }
-                }
-                if (lane == 0) {
-                    atom_s[r] = i;
-                    norm_s[r] = nrm;
-                }
-                __syncwarp();
-                cur = nx;
-                i_cur = i_nx;
-            }
-            if (!alive) break;
-            // the A rows are written: make them visible to the tensor cores
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(afull);
-            // ---- epilogue: rows 32 qw .. 32 qw + 31, column groups sub, sub + 4, ... ----
+        // the epilogue of CTA tile tl: rows 32 qw .. 32 qw + 31, the column
+        // groups sub, sub + kFSubs, ... of 8 columns
+        auto epilogue = [&](int tl) -> bool {
             if (!warp_wait(afull, (uint32_t)(tl & 1), lane, abort_flag, a.status) ||
-                !warp_wait(accfull, (uint32_t)(tl & 1), lane, abort_flag, a.status)) {
-                alive = false;
-                break;
-            }
+                !warp_wait(accfull, (uint32_t)(tl & 1), lane, abort_flag, a.status))
+                return false;
             fence_after();
+            const FTile ti = fused_decode(T, pre, (int)blockIdx.x + tl * (int)gridDim.x);
             const int rloc = qw * 32 + lane;
             const int atom = atom_s[rloc];
             const bool valid = atom >= 0;
@@ -386,16 +363,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             const bool fact = a.var_factored[ti.g] != 0;
             float E = 0.f, V = 0.f, Va = 0.f;
 #pragma unroll 1
-            for (int c = 16 * sub; c < K; c += 16 * kFSubs) {
-                float dv[16], v[16];
-                read_d16(sAhi, sAlo, rloc, c, dv);
-                tmem_ld16(tbase + (uint32_t)c, v);
-                tmem_st16(tbase + (uint32_t)(D::PARK + c), v);   // park beta d
+            for (int c = 8 * sub; c < K; c += 8 * kFSubs) {
+                float dv[8], v[8];
+                read_d8<N>(sAhi, sAlo, rloc, c, dv);
+                tmem_ld8(tbase + (uint32_t)c, v);
+                tmem_st8(tbase + (uint32_t)(D::PARK + c), v);   // park beta d
 #pragma unroll
-                for (int k = 0; k < 16; ++k) E += dv[k] * v[k];
-                tmem_ld16(tbase + (uint32_t)(K + c), v);
+                for (int k = 0; k < 8; ++k) E += dv[k] * v[k];
+                tmem_ld8(tbase + (uint32_t)(K + c), v);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < 8; ++k) {
                     const float tq = (fact ? v[k] : dv[k]) * v[k];
                     V += tq;
                     Va += fabsf(tq);
@@ -405,10 +382,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             evx_buf[sub * kFM + rloc] = make_float4(E, V, Va, 0.f);
             __syncwarp();
             if (lane == 0) mbar_arrive(evx0 + 8 * qw);
-            if (!warp_wait(evx0 + 8 * qw, (uint32_t)(tl & 1), lane, abort_flag, a.status)) {
-                alive = false;
-                break;
-            }
+            if (!warp_wait(evx0 + 8 * qw, (uint32_t)(tl & 1), lane, abort_flag, a.status)) return false;
             E = 0.f;
             V = 0.f;
             Va = 0.f;
@@ -422,13 +396,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             tmem_wait_st();
             float *grow = a.G1 + (size_t)(valid ? ti.row0 + rloc : 0) * K;
 #pragma unroll 1
-            for (int c = 16 * sub; c < K; c += 16 * kFSubs) {
-                float dv[16], pv[16];
-                tmem_ld16(tbase + (uint32_t)(D::PARK + c), pv);
-                read_d16(sAhi, sAlo, rloc, c, dv);
+            for (int c = 8 * sub; c < K; c += 8 * kFSubs) {
+                float dv[8], pv[8];
+                tmem_ld8(tbase + (uint32_t)(D::PARK + c), pv);
+                read_d8<N>(sAhi, sAlo, rloc, c, dv);
                 if (valid) {
 #pragma unroll
-                    for (int k = 0; k < 16; k += 4)
+                    for (int k = 0; k < 8; k += 4)
                         *reinterpret_cast<float4 *>(grow + c + k) =
                             make_float4(s2 * (pv[k] - E * dv[k]), s2 * (pv[k + 1] - E * dv[k + 1]),
                                         s2 * (pv[k + 2] - E * dv[k + 2]), s2 * (pv[k + 3] - E * dv[k + 3]));
@@ -447,7 +421,71 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(wfree);
-            ti = tin;
+            return true;
+        };
+
+        int s_cur = draw();
+        int i_cur = atom_of_slot(s_cur);
+        DescPre cur = desc_preload(da, i_cur < 0 ? 0x7fffffff : i_cur, 0x7fffffff, lane);
+        while (s_cur < n_slots && alive) {
+            const int tl = s_cur / kFM, r = s_cur % kFM;
+            const int s_nx = draw();
+            const int i_nx = atom_of_slot(s_nx);
+            const DescPre nx = desc_preload(da, i_nx < 0 ? 0x7fffffff : i_nx, 0x7fffffff, lane);
+            float nrm = 0.f;
+            if (i_cur >= 0) nrm = desc_atom<N>(da, dw, lane, cur, i_cur);
+            // before this row goes into the A tile: this warp's share of the
+            // epilogues of the earlier tiles, then every worker's
+            while (tl_epi < tl && alive) {
+                alive = epilogue(tl_epi);
+                ++tl_epi;
+            }
+            if (!alive) break;
+            if (tl > 0 && !warp_wait(wfree, (uint32_t)((tl - 1) & 1), lane, abort_flag, a.status)) {
+                alive = false;
+                break;
+            }
+            if (i_cur >= 0) {
+                const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
+                const float4 *sBv = dw.st.b.B;
+                constexpr int NPS = K / 4;
+#pragma unroll
+                for (int k = 0; k < (NPS + 31) / 32; ++k) {
+                    const int tt = lane + 32 * k;
+                    if (tt < NPS) {
+                        const float4 bb = sBv[tt];
+                        const float4 v = make_float4(bb.x * inv, bb.y * inv, bb.z * inv, bb.w * inv);
+                        const __nv_bfloat162 hi01 = __floats2bfloat162_rn(v.x, v.y);
+                        const __nv_bfloat162 hi23 = __floats2bfloat162_rn(v.z, v.w);
+                        const float2 f01 = __bfloat1622float2(hi01), f23 = __bfloat1622float2(hi23);
+                        const __nv_bfloat162 lo01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+                        const __nv_bfloat162 lo23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+                        uint2 hv, lv;
+                        hv.x = *reinterpret_cast<const uint32_t *>(&hi01);
+                        hv.y = *reinterpret_cast<const uint32_t *>(&hi23);
+                        lv.x = *reinterpret_cast<const uint32_t *>(&lo01);
+                        lv.y = *reinterpret_cast<const uint32_t *>(&lo23);
+                        const uint32_t o = a_off<N>(r, 4 * tt);
+                        *reinterpret_cast<uint2 *>(sAhi + o) = hv;
+                        *reinterpret_cast<uint2 *>(sAlo + o) = lv;
+                    }
+                }
+            }
+            if (lane == 0) {
+                atom_s[r] = i_cur;
+                norm_s[r] = nrm;
+            }
+            // the row is written: make it visible to the tensor cores, count it
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(afull);
+            s_cur = s_nx;
+            i_cur = i_nx;
+            cur = nx;
+        }
+        while (tl_epi < my_tiles && alive) {
+            alive = epilogue(tl_epi);
+            ++tl_epi;
         }
     }
     fence_before();
