@@ -26,47 +26,73 @@
 // evaluated alongside.  The per-warp state and the per-atom and per-pair
 // steps are in force_dev.cuh; each warp's state is one contiguous block of
 // shared memory.
+#include <cstddef>
+
 #include "force_dev.cuh"
 
 namespace flr {
 namespace {
 
 constexpr int kWarpsForce = 4;                // warps per CTA
+constexpr int kForceBlocks = 4;               // CTAs per SM, any class (shared memory and registers allow 4)
+#ifndef FLR_FORCE1_BLOCKS
+#define FLR_FORCE1_BLOCKS 5
+#endif
+constexpr int kForce1Blocks = FLR_FORCE1_BLOCKS;   // CTAs per SM, one-species classes only
 
-template <int N>
+template <class FW, int N>
 struct ForceSmem {
-    ForceWarp<N> wp[kWarpsForce];
+    FW wp[kWarpsForce];
     float vir[kWarpsForce][9];
     int2 goff[goff_count<N>()];
 };
 
-template <int N>
-__global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
+// The atoms a force launch takes: a.n by index, or order[0 .. m) with m on the device.
+__device__ __forceinline__ int force_count(const ForceArgs &a)
 {
-    __shared__ __align__(16) ForceSmem<N> sm;
+    if (!a.n_dev[0]) return a.n;
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (a.n_dev[k]) m += *a.n_dev[k];
+    return m < a.n ? m : a.n;
+}
+
+// FW = ForceWarp<N> takes atoms of any class; FW = ForceWarp1<N> only atoms
+// of the one-species classes (their smaller per-warp state lets more warps
+// share an SM).
+template <int N, class FW, int MINB>
+__global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
+{
+    __shared__ __align__(16) ForceSmem<FW, N> sm;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    ForceWarp<N> &fw = sm.wp[w];
+    FW &fw = sm.wp[w];
     float vir[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) vir[k] = 0.f;
-    init_warp<N>(fw, lane);
+    init_warp(fw, lane);
     const bool want_vatom = a.vir_atom != nullptr;
     init_goff<N>(a, sm.goff, threadIdx.x, blockDim.x);
     __syncthreads();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
-    // warps take chunks of consecutive atoms dynamically; the next atom's
-    // scalars are loaded, and its g and A rows copied, one atom ahead
+    // warps take chunks of consecutive positions of the atom sequence
+    // dynamically; the next atom's scalars are loaded, and its g and A rows
+    // copied, one atom ahead
+    const int n_take = force_count(a);
+    const int i_end = a.order ? 0x7fffffff : a.n;
     WarpChunks wc;
-    wc.init(a.sched, a.n, lane);
-    int i = wc.pos();
-    AtomPre cur = preload(a, i, a.n, lane);
-    rows_async<N>(a, cur, i, a.n, fw.gr, fw.A, lane);
-    int i2 = a.n;
+    wc.init(a.sched, n_take, lane);
+    int p = wc.pos();
+    int i = p < n_take ? (a.order ? __ldg(a.order + p) : p) : i_end;
+    AtomPre cur = preload(a, i, i_end, lane);
+    rows_async<N, FW::kOne>(a, cur, i, i_end, fw.gr, fw.A, lane);
+    int p2 = n_take, i2 = i_end;
     AtomPre nxt;
-    for (; i < a.n; i = i2, cur = nxt, wc.advance(lane)) {
-        i2 = wc.peek();
-        nxt = preload(a, i2, a.n, lane);
+    for (; p < n_take; p = p2, i = i2, cur = nxt, wc.advance(lane)) {
+        p2 = wc.peek();
+        i2 = p2 < n_take ? (a.order ? __ldg(a.order + p2) : p2) : i_end;
+        nxt = preload(a, i2, i_end, lane);
         const int g = cur.g;
         if (g < 0 || !(cur.nrm > 0.f)) {
             // no environment inside r_cut: no forces from this centre
@@ -76,14 +102,14 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
                 if (a.sigma) a.sigma[i] = 0.f;
             }
             if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
-            rows_async<N>(a, nxt, i2, a.n, fw.gr, fw.A, lane);
+            rows_async<N, FW::kOne>(a, nxt, i2, i_end, fw.gr, fw.A, lane);
             continue;
         }
-        force_atom<N>(a, fw, sm.goff, lane, cur, i, nxt, i2, a.n, nq, seq, vir, want_vatom);
+        force_atom<N, FW>(a, fw, sm.goff, lane, cur, i, nxt, i2, i_end, nq, seq, vir, want_vatom);
     }  // atoms
-    drain<N>(fw, lane, nq, true, a.rcut, a.Facc, a.status, vir, want_vatom);
+    drain<N, FW>(fw, lane, nq, true, a.rcut, a.Facc, a.status, vir, want_vatom);
     if (want_vatom)
-        for (int s = 0; s < kSlots; ++s) flush_slot<N>(fw, lane, s, a.vir_atom);
+        for (int s = 0; s < kSlots; ++s) flush_slot(fw, lane, s, a.vir_atom);
 
     // virial: warp reduce, then a fixed-order FP64 sum over the block's warps
 #pragma unroll
@@ -96,8 +122,23 @@ __global__ void __launch_bounds__(kWarpsForce * 32, 4) k_force(ForceArgs a)
     if (threadIdx.x < 9) {
         double s = 0.0;
         for (int q = 0; q < kWarpsForce; ++q) s += (double)sm.vir[q][threadIdx.x];
-        a.vir_part[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
+        a.vir_part[(size_t)(a.vir_base + blockIdx.x) * 9 + threadIdx.x] = s;
     }
+}
+
+// Atoms with an empty neighbour list (group < 0) belong to no compaction
+// group, so neither the quadratic forms nor the class-ordered force launches
+// visit them: their outputs are zero.
+__global__ void __launch_bounds__(256) k_zero_isolated(const int32_t *group, int n, float *energy, float *variance,
+                                                       float *sigma, float *vir_atom)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n || group[i] >= 0) return;
+    energy[i] = 0.f;
+    if (variance) variance[i] = 0.f;
+    if (sigma) sigma[i] = 0.f;
+    if (vir_atom)
+        for (int k = 0; k < 9; ++k) vir_atom[9 * (size_t)i + k] = 0.f;
 }
 
 // ---- finalize: fixed point -> float forces, optional velocity half-kick,
@@ -304,6 +345,45 @@ int launch_seg_totals(flr_ctx *ctx, const flr_nbrlist *nl, const flr_outputs *ou
     return cuda_fail(cudaGetLastError(), "per-structure totals");
 }
 
+template <int N>
+int launch_force_n(flr_ctx *ctx, const flr_nbrlist *nl, ForceArgs a, int n, cudaStream_t st)
+{
+    // two launches over the compaction rows: the two-species rows with the
+    // general per-warp state, the one-species rows (nearly all atoms) with the
+    // smaller one; each launch's block partials of the virial follow the other's
+    const int *cnt = reinterpret_cast<const int *>(reinterpret_cast<const char *>(nl->gtab) + offsetof(GroupTab, count));
+    cudaError_t e = cudaMemsetAsync(ctx->sched + 1, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->sched + 3, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "force work counters");
+    const long long work = (n + kWarpsForce - 1) / kWarpsForce;
+    ForceArgs a0 = a, a1 = a;
+    a0.order = nl->atom_of_row;
+    a0.n_dev[0] = cnt + 0;
+    a0.n_dev[1] = cnt + 3;
+    a0.n_dev[2] = a0.n_dev[3] = nullptr;
+    a0.sched = ctx->sched + 1;
+    a0.vir_base = 0;
+    const int grid0 = persistent_grid(k_force<N, ForceWarp<N>, kForceBlocks>, kWarpsForce * 32, ctx->num_sms, work);
+    a1.order = nl->atom_of_row + nl->n_cap;
+    a1.n_dev[0] = cnt + 1;
+    a1.n_dev[1] = cnt + 2;
+    a1.n_dev[2] = cnt + 4;
+    a1.n_dev[3] = cnt + 5;
+    a1.sched = ctx->sched + 3;
+    a1.vir_base = grid0;
+    const int grid1 = persistent_grid(k_force<N, ForceWarp1<N>, kForce1Blocks>, kWarpsForce * 32, ctx->num_sms, work);
+    if (grid0 + grid1 > kMaxPartials) {
+        set_error("force launch: too many blocks for the virial partials");
+        return FLR_EINVAL;
+    }
+    k_force<N, ForceWarp<N>, kForceBlocks><<<grid0, kWarpsForce * 32, 0, st>>>(a0);
+    k_force<N, ForceWarp1<N>, kForce1Blocks><<<grid1, kWarpsForce * 32, 0, st>>>(a1);
+    k_zero_isolated<<<(n + 255) / 256, 256, 0, st>>>(nl->group, n, a.energy, a.variance, a.sigma, a.vir_atom);
+    ctx->n_part = grid0 + grid1;
+    count_launch(ctx, 3);
+    return cuda_fail(cudaGetLastError(), "force kernels");
+}
+
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st)
 {
@@ -336,22 +416,14 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.tab[1] = ctx->tab_single;
     a.status = ctx->status;
     a.sched = ctx->sched + 1;
-    {
-        const cudaError_t e = cudaMemsetAsync(a.sched, 0, sizeof(int), st);
-        if (e != cudaSuccess) return cuda_fail(e, "force work counter");
+    a.order = nullptr;
+    for (int k = 0; k < 4; ++k) a.n_dev[k] = nullptr;
+    a.vir_base = 0;
+    if (n <= 0) {
+        ctx->n_part = 0;
+        return FLR_OK;
     }
-    const long long work = (n + kWarpsForce - 1) / kWarpsForce;
-    int grid;
-    if (ctx->dims.N == 8) {
-        grid = std::min(kMaxPartials, persistent_grid(k_force<8>, kWarpsForce * 32, ctx->num_sms, work));
-        k_force<8><<<grid, kWarpsForce * 32, 0, st>>>(a);
-    } else {
-        grid = std::min(kMaxPartials, persistent_grid(k_force<7>, kWarpsForce * 32, ctx->num_sms, work));
-        k_force<7><<<grid, kWarpsForce * 32, 0, st>>>(a);
-    }
-    ctx->n_part = grid;
-    count_launch(ctx);
-    return cuda_fail(cudaGetLastError(), "force kernel");
+    return ctx->dims.N == 8 ? launch_force_n<8>(ctx, nl, a, n, st) : launch_force_n<7>(ctx, nl, a, n, st);
 }
 
 int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out, const KickArgs &kick, float sign,

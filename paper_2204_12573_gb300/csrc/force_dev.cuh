@@ -51,6 +51,9 @@ struct ForceArgs {
     const int32_t *tab[2];     // compact index -> channel pair (a | b << 8), per region
     int *sched;                // work counter, zero at launch
     int *status;
+    const int32_t *order;      // atoms taken as order[0 .. m) (nullptr: 0 .. n-1 by index), with
+    const int *n_dev[4];       // m = the sum of the counts these point to (capped at n)
+    int vir_base;              // first row of this launch's block partials in vir_part
 };
 
 // Dense G~ layout for a class of CG channels: lane half h owns channels
@@ -60,9 +63,11 @@ __host__ __device__ constexpr int gd_half(int CG) { return ((CG + 1) / 2 + 3) / 
 __host__ __device__ constexpr int gd_row(int CG) { return 2 * gd_half(CG); }
 __host__ __device__ constexpr int gd_plane(int CG) { return CG * gd_row(CG) + 8; }
 
-// Shared-memory state of one warp (one contiguous block per warp).
+// Shared-memory state of one warp (one contiguous block per warp), for atoms
+// of any compaction class.
 template <int N>
 struct __align__(16) ForceWarp {
+    static constexpr bool kOne = false;               // holds both species blocks
     static constexpr int CGM = 2 * N;                 // widest class
     static constexpr int WSLOT = 2 * 16 * 8 + 4;      // [species][lm][n (8, padded)] + pad
     float4 q[64];                      // queued pairs: r_ij, packed (j | s_j << 25 | slot << 26)
@@ -73,6 +78,24 @@ struct __align__(16) ForceWarp {
     long long V[kSlots][9];            // virial of each slot's atom (when requested), fixed point
     int atom[kSlots];
     int qseq[64];                      // atom sequence number of each queued pair
+};
+
+// The same state for atoms of the one-species classes only: one block of N
+// channels in G~, A and w (all of such an atom's pairs have a neighbour of
+// that species), so a warp needs less than half the shared memory.
+template <int N>
+struct __align__(16) ForceWarp1 {
+    static constexpr bool kOne = true;
+    static constexpr int CGM = N;
+    static constexpr int WSLOT = 16 * 8 + 4;          // [lm][n (8, padded)] + pad
+    float4 q[64];
+    float Gd[4 * gd_plane(N)];
+    float A[N * kAStride];
+    float gr[N * (N + 1) / 2 * 4];
+    float W[kSlots * WSLOT];
+    long long V[kSlots][9];
+    int atom[kSlots];
+    int qseq[64];
 };
 
 // Where each compact channel pair (a, b) of g lands in the dense G~ of its
@@ -107,8 +130,8 @@ __device__ __forceinline__ long long to_fix(float v, int *status)
 }
 
 // Evaluate m <= 32 queued pairs, one per lane.
-template <int N>
-__device__ __forceinline__ void force_batch(ForceWarp<N> &fw, int lane, int m, float rc,
+template <int N, class FW>
+__device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
                                             unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     int my_slot = -1;
@@ -124,7 +147,7 @@ __device__ __forceinline__ void force_batch(ForceWarp<N> &fw, int lane, int m, f
         const float ux = rec.x * inv, uy = rec.y * inv, uz = rec.z * inv;
         float Rf[N], dRf[N];
         radial<N, true>(rr, rc, Rf, dRf);
-        const float *wp = fw.W + slot * ForceWarp<N>::WSLOT + sj * 128;
+        const float *wp = fw.W + slot * FW::WSLOT + (FW::kOne ? 0 : sj * 128);
         const float xx = ux * ux, yy = uy * uy, zz = uz * uz;
         // f = u (sum_lm c'_lm Y_lm - (1/r) sum_lm l c_lm Y_lm) + (1/r) sum_lm c_lm grad P_lm(u),
         // c_lm = sum_n w_{n,lm} R_n f_c,  c'_lm = sum_n w_{n,lm} (R_n f_c)'
@@ -204,13 +227,13 @@ __device__ __forceinline__ void force_batch(ForceWarp<N> &fw, int lane, int m, f
 }
 
 // Evaluate every queued pair (all) or every full batch, and compact the queue.
-template <int N>
-__device__ __forceinline__ void drain(ForceWarp<N> &fw, int lane, int &nq, bool all, float rc,
+template <int N, class FW>
+__device__ __forceinline__ void drain(FW &fw, int lane, int &nq, bool all, float rc,
                                       unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     while (nq >= 32 || (all && nq > 0)) {
         const int m = nq < 32 ? nq : 32;
-        force_batch<N>(fw, lane, m, rc, Facc, status, vir, want_vatom);
+        force_batch<N, FW>(fw, lane, m, rc, Facc, status, vir, want_vatom);
         const int rest = nq - m;
         float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
         int sq = 0;
@@ -229,8 +252,8 @@ __device__ __forceinline__ void drain(ForceWarp<N> &fw, int lane, int &nq, bool 
 }
 
 // Release a slot: write its atom's virial (when requested) and clear it.
-template <int N>
-__device__ __forceinline__ void flush_slot(ForceWarp<N> &fw, int lane, int slot, float *vir_atom)
+template <class FW>
+__device__ __forceinline__ void flush_slot(FW &fw, int lane, int slot, float *vir_atom)
 {
     const int i = fw.atom[slot];
     if (lane < 9) {
@@ -243,8 +266,8 @@ __device__ __forceinline__ void flush_slot(ForceWarp<N> &fw, int lane, int slot,
 }
 
 // Warp start: no slot in use, no virial.
-template <int N>
-__device__ __forceinline__ void init_warp(ForceWarp<N> &fw, int lane)
+template <class FW>
+__device__ __forceinline__ void init_warp(FW &fw, int lane)
 {
     if (lane < kSlots) fw.atom[lane] = -1;
     for (int k = lane; k < 9 * kSlots; k += 32) fw.V[k / 9][k % 9] = 0;
@@ -254,7 +277,7 @@ __device__ __forceinline__ void init_warp(ForceWarp<N> &fw, int lane)
 // (lm, half) owns harmonic lm of half of the channels a; G~ is dense in
 // shared memory as [l][b][a] (row b contiguous in a), so each b costs one
 // A value and H/4 float4 loads of G~ for H FMAs per lane.
-template <int CG, int N>
+template <int CG, int N, bool ONE = false>
 __device__ __forceinline__ void w_dense(const float *sGd, const float *sA, float *ws, int choff, int half, int lm)
 {
     constexpr int H = gd_half(CG);
@@ -268,7 +291,7 @@ __device__ __forceinline__ void w_dense(const float *sGd, const float *sA, float
     for (int k = 0; k < H; ++k) acc[k] = 0.f;
 #pragma unroll
     for (int b = 0; b < CG; ++b) {
-        const float av = sA[(choff + b) * kAStride + lm];
+        const float av = sA[(ONE ? b : choff + b) * kAStride + lm];
 #pragma unroll
         for (int k = 0; k < H; k += 4) {
             const float4 gv = *reinterpret_cast<const float4 *>(gp + b * RS + k);
@@ -281,8 +304,12 @@ __device__ __forceinline__ void w_dense(const float *sGd, const float *sA, float
 #pragma unroll
     for (int k = 0; k < H; ++k) {
         if (a0 + k < CG) {                         // the last half may be padded
-            const int ch = choff + a0 + k;        // channel = species * N + n
-            ws[(ch / N) * 128 + lm * 8 + (ch % N)] = acc[k];
+            if (ONE) {
+                ws[lm * 8 + a0 + k] = acc[k];     // the one block
+            } else {
+                const int ch = choff + a0 + k;    // channel = species * N + n
+                ws[(ch / N) * 128 + lm * 8 + (ch % N)] = acc[k];
+            }
         }
     }
 }
@@ -327,7 +354,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 // Start copying atom i's g row (raw, compact order) and the A rows of its
 // class's channels into the warp's shared buffers (cp.async; lane t % 32
 // copies chunk t).  The buffers must no longer be in use.
-template <int N>
+template <int N, bool ONE = false>
 __device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p, int i, int i_end, float *gr, float *sA,
                                            int lane)
 {
@@ -342,7 +369,7 @@ __device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p,
     const float *Ag = a.A + (size_t)i * (C * 16);
     for (int k = lane; k < Cg * 4; k += 32) {
         const int ch = choff + (k >> 2);
-        cp_async16(sA + ch * kAStride + 4 * (k & 3), Ag + ch * 16 + 4 * (k & 3));
+        cp_async16(sA + (ONE ? (k >> 2) : ch) * kAStride + 4 * (k & 3), Ag + ch * 16 + 4 * (k & 3));
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -352,8 +379,8 @@ __device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p,
 // atom's g row, form w = G~ A, start copying the next atom's rows (nxt, i2;
 // nothing when i2 >= i_end), then queue the atom's pairs and evaluate every
 // full batch.
-template <int N>
-__device__ __forceinline__ void force_atom(const ForceArgs &a, ForceWarp<N> &fw, const int2 *goff_all, int lane,
+template <int N, class FW>
+__device__ __forceinline__ void force_atom(const ForceArgs &a, FW &fw, const int2 *goff_all, int lane,
                                            const AtomPre &cur, int i, const AtomPre &nxt, int i2, int i_end,
                                            int &nq, int &seq, float vir[9], bool want_vatom)
 {
@@ -366,8 +393,8 @@ __device__ __forceinline__ void force_atom(const ForceArgs &a, ForceWarp<N> &fw,
 
     // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
     const int slot = seq & (kSlots - 1);
-    if (nq > 0 && fw.qseq[0] <= seq - kSlots) drain<N>(fw, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
-    if (want_vatom) flush_slot<N>(fw, lane, slot, a.vir_atom);   // otherwise the slot holds nothing to write
+    if (nq > 0 && fw.qseq[0] <= seq - kSlots) drain<N, FW>(fw, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
+    if (want_vatom) flush_slot(fw, lane, slot, a.vir_atom);   // otherwise the slot holds nothing to write
     if (lane == 0) fw.atom[slot] = i;
 
     // this atom's g row and A rows were copied into shared memory while the
@@ -401,20 +428,22 @@ __device__ __forceinline__ void force_atom(const ForceArgs &a, ForceWarp<N> &fw,
             fw.Gd[3 * LS + o2] = v.w;
         }
     }
-    float *ws = fw.W + slot * ForceWarp<N>::WSLOT;
+    float *ws = fw.W + slot * FW::WSLOT;
     // w_dense writes every channel of the atom's class; pairs only read
     // the species blocks of that class, so the slot needs no clearing
     __syncwarp();
     {
         const int lm = lane & 15, half = lane >> 4;
-        if (cls == 0)
+        if (FW::kOne)
+            w_dense<N, N, true>(fw.Gd, fw.A, ws, choff, half, lm);
+        else if (cls == 0)
             w_dense<C, N>(fw.Gd, fw.A, ws, 0, half, lm);
         else
             w_dense<N, N>(fw.Gd, fw.A, ws, choff, half, lm);
     }
     __syncwarp();
     // the g and A buffers are free: start copying the next atom's rows
-    rows_async<N>(a, nxt, i2, i_end, fw.gr, fw.A, lane);
+    rows_async<N, FW::kOne>(a, nxt, i2, i_end, fw.gr, fw.A, lane);
 
     // queue the atom's pairs inside r_cut (recorded by the descriptor kernel)
     const int np = cur.np;
@@ -429,7 +458,7 @@ __device__ __forceinline__ void force_atom(const ForceArgs &a, ForceWarp<N> &fw,
         }
         nq += take;
         __syncwarp();
-        drain<N>(fw, lane, nq, false, rc, a.Facc, a.status, vir, want_vatom);
+        drain<N, FW>(fw, lane, nq, false, rc, a.Facc, a.status, vir, want_vatom);
     }
     ++seq;
 }
