@@ -400,6 +400,7 @@ def run_ours(args):
 
     if args.profile_run:
         # the mixed-precision timed region only (for launch lists and ncu captures)
+        ff.set_fused(args.fused)
         ms, launches, _, _ = timed(args.precision)
         if rank == 0:
             print(json.dumps({"profile_run": True, "n_atoms": n, "precision": args.precision,
@@ -725,6 +726,8 @@ def main():
     ap.add_argument("--profile-run", action="store_true",
                     help="time only the MD steps at --precision (for ncu launch lists)")
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--fused", action="store_true",
+                    help="with --profile-run: one-species atoms in the fused descriptor + tensor-core kernel")
     ap.add_argument("--err-atoms", type=int, default=4096,
                     help="atoms sampled for the error report against the FP64 oracle")
     ap.add_argument("--serving-seconds", type=float, default=3.0,

@@ -250,6 +250,22 @@ int status_to_code(int st)
     return FLR_OK;
 }
 
+// The quadratic forms of every compaction group at the context's precision
+// (the forward and the backward pass use the same kernels, so the forces of
+// the weighted energy with unit weights are bitwise the forward forces).
+int launch_qform(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st)
+{
+    if (ctx->p.precision == FLR_PREC_FP32) return launch_qform_simt(ctx, nl, out, st);
+    if (ctx->p.precision == FLR_PREC_BF16X3 && ctx->p.compaction) {
+        // two-species tiles on the general kernel, one-species tiles on the
+        // kernel that loads each operand of a K block once
+        int s = launch_qform_tc(ctx, nl, out, st, true);
+        if (s == FLR_OK) s = launch_qform1(ctx, nl, out, st);
+        return s;
+    }
+    return launch_qform_tc(ctx, nl, out, st);
+}
+
 int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
              flr_outputs *out, const KickArgs &kick, cudaStream_t st, double *seg_totals = nullptr)
 {
@@ -292,7 +308,7 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
             e = cudaMemsetAsync(ctx->ref_count, 0, sizeof(int), st);
             if (e != cudaSuccess) return cuda_fail(e, "clear variance queue");
         }
-        s = ctx->p.precision == FLR_PREC_FP32 ? launch_qform_simt(ctx, nl, out, st) : launch_qform_tc(ctx, nl, out, st);
+        s = launch_qform(ctx, nl, out, st);
         if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) s = launch_variance_fp64(ctx, nl, out, st);
         prof_end(ctx, FLR_KERNEL_QFORM, st);
         if (s != FLR_OK) return s;
@@ -494,6 +510,7 @@ int flr_destroy(flr_ctx *c)
         delete[] c->sigma_h[s];
     }
     free_fused_maps(c);
+    free_q1_maps(c);
     cudaFree(c->tab_full);
     cudaFree(c->tab_single);
     cudaFree(c->status);
@@ -915,7 +932,7 @@ int flr_energy_backward(flr_ctx *c, const flr_batch *b, const flr_nbrlist *nl, c
     s = cuda_fail(cudaMemsetAsync(c->Facc, 0, sizeof(long long) * 3 * (size_t)n, st), "clear force accumulators");
     if (s == FLR_OK) s = launch_desc(c, nl, pos, b->species, n, st);
     if (s == FLR_OK)
-        s = c->p.precision == FLR_PREC_FP32 ? launch_qform_simt(c, nl, &o, st) : launch_qform_tc(c, nl, &o, st);
+        s = launch_qform(c, nl, &o, st);
     // dL/dr = -(forces of sum_i u_i E_i): the force kernel with g_i scaled by u_i
     if (s == FLR_OK) s = launch_force(c, nl, pos, b->species, n, &o, nullptr, grad_energy, st);
     KickArgs none;

@@ -103,75 +103,6 @@ struct FusedArgs {
     int *status;
 };
 
-// The one-species compaction groups, in the order their tiles are numbered.
-__constant__ int kOneSpeciesGroups[4] = {1, 2, 4, 5};
-
-struct FTile {
-    int g, row0, rend;
-};
-
-__device__ __forceinline__ int fused_tiles(const GroupTab &T, int pre[5])
-{
-    pre[0] = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) pre[k + 1] = pre[k] + (T.count[kOneSpeciesGroups[k]] + kFM - 1) / kFM;
-    return pre[4];
-}
-
-__device__ __forceinline__ FTile fused_decode(const GroupTab &T, const int pre[5], int t)
-{
-    int k = 0;
-    while (k < 3 && t >= pre[k + 1]) ++k;
-    FTile ti;
-    ti.g = kOneSpeciesGroups[k];
-    ti.row0 = T.off[ti.g] + (t - pre[k]) * kFM;
-    ti.rend = T.off[ti.g] + T.count[ti.g];
-    return ti;
-}
-
-// Byte offset of (row r, column c) in the K-major A tile: columns below
-// 64 NA lie in 64-column atoms with 128-byte swizzle (8 rows x 128 bytes per
-// swizzle block, the 16-byte chunk index XORed with the row within the
-// block), the rest in 16-column blocks with 32-byte swizzle (8 rows x 32
-// bytes per block, the 16-byte half XORed with bit 2 of the row).
-template <int N>
-__device__ __forceinline__ uint32_t a_off(int r, int c)
-{
-    constexpr int NA = FDims<N>::NA;
-    if (c < 64 * NA)
-        return (uint32_t)((c >> 6) * (kFM * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
-                          ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1));
-    const int ct = c - 64 * NA;
-    return (uint32_t)(NA * (kFM * 128) + (ct >> 4) * (kFM * 32) + (r >> 3) * 256 + (r & 7) * 32 +
-                      ((((ct & 15) >> 3) ^ ((r >> 2) & 1)) << 4) + ((ct & 7) << 1));
-}
-
-// Shared-memory descriptor of MMA K step ks of an A part at byte address base
-template <int N>
-__device__ __forceinline__ uint64_t a_desc(uint32_t base, int ks)
-{
-    constexpr int NA = FDims<N>::NA;
-    if (ks < 4 * NA) return sw128_desc(base + (uint32_t)((ks >> 2) * (kFM * 128) + (ks & 3) * 32));
-    return sw32_desc(base + (uint32_t)(NA * (kFM * 128) + (ks - 4 * NA) * (kFM * 32)));
-}
-
-// 8 columns c .. c+7 of row r of d (c a multiple of 8), rebuilt as hi + lo from the A tile
-template <int N>
-__device__ __forceinline__ void read_d8(const uint8_t *sAhi, const uint8_t *sAlo, int r, int c, float v[8])
-{
-    const uint32_t o = a_off<N>(r, c);
-    const uint4 hi = *reinterpret_cast<const uint4 *>(sAhi + o);
-    const uint4 lo = *reinterpret_cast<const uint4 *>(sAlo + o);
-    const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[k]));
-        const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[k]));
-        v[2 * k] = fh.x + fl.x;
-        v[2 * k + 1] = fh.y + fl.y;
-    }
-}
-
 // A warp-wide bounded wait on an mbarrier phase (lane 0 waits, the warp
 // follows its verdict); on failure records the timeout and raises the abort flag.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int lane, volatile int *abort_flag,
@@ -238,7 +169,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
     const uint32_t tmem = *tmem_holder;
     const GroupTab &T = *a.gtab;
     int pre[5];
-    const int total = fused_tiles(T, pre);
+    const int total = one_species_tiles(T, pre);
     // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
     const int my_tiles = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
@@ -251,7 +182,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             for (int s = 0; s < kFStages; ++s) last_phase[s] = -1;
             bool ok = true;
             for (int tl = 0; tl < my_tiles && ok; ++tl) {
-                const FTile ti = fused_decode(T, pre, (int)blockIdx.x + tl * (int)gridDim.x);
+                const OneTile ti = one_species_tile(T, pre, (int)blockIdx.x + tl * (int)gridDim.x);
                 for (int ks = 0; ks < D::KSTEPS; ++ks) {
                     if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
                     const uint32_t fb = full0 + 8 * stage;
@@ -295,7 +226,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
                 for (int ks = 0; ks < D::KSTEPS; ++ks) {
                     if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
                     fence_after();
-                    const uint64_t ahi = a_desc<N>(ahi0, ks), alo = a_desc<N>(alo0, ks);
+                    const uint64_t ahi = ATile<N>::desc(ahi0, ks), alo = ATile<N>::desc(alo0, ks);
                     const uint32_t sb = smem_u32(sB + stage * D::STAGE);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -343,7 +274,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
         };
         auto atom_of_slot = [&](int sl) -> int {
             if (sl >= n_slots) return -1;
-            const FTile x = fused_decode(T, pre, (int)blockIdx.x + (sl / kFM) * (int)gridDim.x);
+            const OneTile x = one_species_tile(T, pre, (int)blockIdx.x + (sl / kFM) * (int)gridDim.x);
             const int row = x.row0 + sl % kFM;
             return row < x.rend ? __ldg(a.atom_of_row1 + row) : -1;
         };
@@ -354,7 +285,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
                 !warp_wait(accfull, (uint32_t)(tl & 1), lane, abort_flag, a.status))
                 return false;
             fence_after();
-            const FTile ti = fused_decode(T, pre, (int)blockIdx.x + tl * (int)gridDim.x);
+            const OneTile ti = one_species_tile(T, pre, (int)blockIdx.x + tl * (int)gridDim.x);
             const int rloc = qw * 32 + lane;
             const int atom = atom_s[rloc];
             const bool valid = atom >= 0;
@@ -365,7 +296,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
 #pragma unroll 1
             for (int c = 8 * sub; c < K; c += 8 * kFSubs) {
                 float dv[8], v[8];
-                read_d8<N>(sAhi, sAlo, rloc, c, dv);
+                ATile<N>::read_d8(sAhi, sAlo, rloc, c, dv);
                 tmem_ld8(tbase + (uint32_t)c, v);
                 tmem_st8(tbase + (uint32_t)(D::PARK + c), v);   // park beta d
 #pragma unroll
@@ -399,7 +330,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
             for (int c = 8 * sub; c < K; c += 8 * kFSubs) {
                 float dv[8], pv[8];
                 tmem_ld8(tbase + (uint32_t)(D::PARK + c), pv);
-                read_d8<N>(sAhi, sAlo, rloc, c, dv);
+                ATile<N>::read_d8(sAhi, sAlo, rloc, c, dv);
                 if (valid) {
 #pragma unroll
                     for (int k = 0; k < 8; k += 4)
@@ -465,7 +396,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(const __grid_constant__ 
                         hv.y = *reinterpret_cast<const uint32_t *>(&hi23);
                         lv.x = *reinterpret_cast<const uint32_t *>(&lo01);
                         lv.y = *reinterpret_cast<const uint32_t *>(&lo23);
-                        const uint32_t o = a_off<N>(r, 4 * tt);
+                        const uint32_t o = ATile<N>::off(r, 4 * tt);
                         *reinterpret_cast<uint2 *>(sAhi + o) = hv;
                         *reinterpret_cast<uint2 *>(sAlo + o) = lv;
                     }

@@ -166,6 +166,8 @@ struct flr_ctx {
     double *partials;          // [n_blocks][16]
     int n_part;
     void *fmaps;               // tensor maps of the fused one-species kernel (built once per context)
+    void *q1maps;              // tensor maps of the one-species quadratic-form kernel
+    int q1maps_n;              // workspace size they were encoded for
     int use_fused;             // FLR_OPT_FUSED_ONE_SPECIES
     TcMaps *maps;              // host copy of the current tensor maps
     int maps_n;                // workspace size the maps were encoded for
@@ -239,6 +241,10 @@ bool fused_eligible(const flr_ctx *ctx);
 int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, cudaStream_t st);
 void free_fused_maps(flr_ctx *ctx);
+// Quadratic forms of the one-species tiles, 3xBF16 (each K block of A hi/lo
+// and B hi/lo loaded once per tile)
+int launch_qform1(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
+void free_q1_maps(flr_ctx *ctx);
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st);
 int launch_seg_totals(flr_ctx *ctx, const flr_nbrlist *nl, const flr_outputs *out, const float *vir_atom,
@@ -343,6 +349,30 @@ struct WarpChunksT {
     }
 };
 using WarpChunks = WarpChunksT<kWarpChunk>;
+
+// Tiles of 128 rows over the one-species compaction groups (1, 2, 4, 5), in
+// that order: pre[k] is the first tile of the k-th of them.
+struct OneTile {
+    int g, row0, rend;
+};
+__device__ __forceinline__ int one_species_group(int k) { return k < 2 ? k + 1 : k + 2; }
+__device__ __forceinline__ int one_species_tiles(const GroupTab &T, int pre[5])
+{
+    pre[0] = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pre[k + 1] = pre[k] + (T.count[one_species_group(k)] + 127) / 128;
+    return pre[4];
+}
+__device__ __forceinline__ OneTile one_species_tile(const GroupTab &T, const int pre[5], int t)
+{
+    int k = 0;
+    while (k < 3 && t >= pre[k + 1]) ++k;
+    OneTile ti;
+    ti.g = one_species_group(k);
+    ti.row0 = T.off[ti.g] + (t - pre[k]) * 128;
+    ti.rend = T.off[ti.g] + T.count[ti.g];
+    return ti;
+}
 
 // ---- shared device helpers ----
 

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 
 namespace flr {
@@ -166,6 +167,57 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
 }
+
+// The K-major A operand tile of 128 one-species rows, BF16, K = N(N+1)/2 * 4
+// columns without padding: columns below 64 NA lie in 64-column atoms with
+// 128-byte swizzle (8 rows x 128 bytes per swizzle block, the 16-byte chunk
+// index XORed with the row within the block), the rest in 16-column blocks
+// with 32-byte swizzle (8 rows x 32 bytes per block, the 16-byte half XORed
+// with bit 2 of the row) -- the layouts TMA loads of 64 x 128 and 16 x 128
+// boxes with those swizzles produce.  One MMA K step (16 columns) addresses
+// one block.
+template <int N>
+struct ATile {
+    static constexpr int M = 128;
+    static constexpr int K = N * (N + 1) / 2 * 4;
+    static constexpr int NA = K / 64;
+    static constexpr int NT = (K - 64 * NA) / 16;
+    static constexpr int PART = NA * M * 128 + NT * M * 32;   // bytes of the hi (or lo) part
+    static constexpr int KSTEPS = K / 16;
+    static_assert(PART % 1024 == 0, "A parts keep 1024-byte alignment");
+
+    __device__ __forceinline__ static uint32_t off(int r, int c)
+    {
+        if (c < 64 * NA)
+            return (uint32_t)((c >> 6) * (M * 128) + (r >> 3) * 1024 + (r & 7) * 128 +
+                              ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 7) << 1));
+        const int ct = c - 64 * NA;
+        return (uint32_t)(NA * (M * 128) + (ct >> 4) * (M * 32) + (r >> 3) * 256 + (r & 7) * 32 +
+                          ((((ct & 15) >> 3) ^ ((r >> 2) & 1)) << 4) + ((ct & 7) << 1));
+    }
+    // shared-memory descriptor of K step ks of a part at byte address base
+    __device__ __forceinline__ static uint64_t desc(uint32_t base, int ks)
+    {
+        if (ks < 4 * NA) return sw128_desc(base + (uint32_t)((ks >> 2) * (M * 128) + (ks & 3) * 32));
+        return sw32_desc(base + (uint32_t)(NA * (M * 128) + (ks - 4 * NA) * (M * 32)));
+    }
+    // 8 columns c .. c+7 of row r (c a multiple of 8), rebuilt as hi + lo
+    __device__ __forceinline__ static void read_d8(const uint8_t *hi_part, const uint8_t *lo_part, int r, int c,
+                                                   float v[8])
+    {
+        const uint32_t o = off(r, c);
+        const uint4 hi = *reinterpret_cast<const uint4 *>(hi_part + o);
+        const uint4 lo = *reinterpret_cast<const uint4 *>(lo_part + o);
+        const uint32_t hw[4] = {hi.x, hi.y, hi.z, hi.w}, lw[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 fh = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[k]));
+            const float2 fl = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lw[k]));
+            v[2 * k] = fh.x + fl.x;
+            v[2 * k + 1] = fh.y + fl.y;
+        }
+    }
+};
 
 }  // namespace tc
 }  // namespace flr
