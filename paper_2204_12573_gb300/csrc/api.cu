@@ -299,8 +299,11 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
         }
         if (s != FLR_OK) return s;
     } else {
+        // with 3xBF16 and compaction the one-species quadratic forms read only
+        // the BF16 rows, so their FP32 rows are not written here
+        const bool skip32 = ctx->p.precision == FLR_PREC_BF16X3 && ctx->p.compaction;
         prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
-        s = launch_desc(ctx, nl, pos, species, n, st);
+        s = launch_desc(ctx, nl, pos, species, n, st, nullptr, nullptr, nullptr, skip32);
         prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
         if (s != FLR_OK) return s;
         prof_begin(ctx, FLR_KERNEL_QFORM, st);
@@ -309,7 +312,11 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
             if (e != cudaSuccess) return cuda_fail(e, "clear variance queue");
         }
         s = launch_qform(ctx, nl, out, st);
-        if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) s = launch_variance_fp64(ctx, nl, out, st);
+        if (s == FLR_OK && ctx->var_mode == FLR_VAR_AUTO) {
+            // the FP64 variance reads FP32 descriptor rows: write them for the queued atoms
+            if (skip32) s = launch_desc(ctx, nl, pos, species, ctx->ws_n, st, ctx->ref_list, ctx->ref_count);
+            if (s == FLR_OK) s = launch_variance_fp64(ctx, nl, out, st);
+        }
         prof_end(ctx, FLR_KERNEL_QFORM, st);
         if (s != FLR_OK) return s;
     }

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
         const int npairs = cls == 0 ? NPF : NPS;
         const float4 *sB = dw.st.b.B;
         const int r = cur.row;
-        float *d32 = a.D32[reg] + (size_t)r * a.kp32[reg];
+        float *d32 = (a.skip_d32_one && reg == 1) ? nullptr : a.D32[reg] + (size_t)r * a.kp32[reg];
         __nv_bfloat16 *dh = a.bf16 ? a.Dhi[reg] + (size_t)r * a.kp64[reg] : nullptr;
         __nv_bfloat16 *dl = a.bf16 ? a.Dlo[reg] + (size_t)r * a.kp64[reg] : nullptr;
         float *dt = a.Dtf[reg] ? a.Dtf[reg] + (size_t)r * a.kp32[reg] : nullptr;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
             if (t < npairs) {
                 const float4 bb = sB[t];
                 const float4 v = make_float4(bb.x * inv, bb.y * inv, bb.z * inv, bb.w * inv);
-                *reinterpret_cast<float4 *>(d32 + 4 * t) = v;
+                if (d32) *reinterpret_cast<float4 *>(d32 + 4 * t) = v;
                 if (dt)
                     *reinterpret_cast<uint4 *>(dt + 4 * t) =
                         make_uint4(tf32_round_bits(__float_as_uint(v.x)), tf32_round_bits(__float_as_uint(v.y)),
@@ -111,7 +111,7 @@ __global__ void k_expand(ExpandArgs a)
 }  // namespace
 
 int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
-                cudaStream_t st, const int32_t *order, const int *n_dev0, const int *n_dev1)
+                cudaStream_t st, const int32_t *order, const int *n_dev0, const int *n_dev1, bool skip_d32_one)
 {
     DescArgs a;
     a.pos = pos;
@@ -138,6 +138,7 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.A = ctx->A;
     a.norm = ctx->norm;
     a.bf16 = ctx->p.precision == FLR_PREC_BF16X3;
+    a.skip_d32_one = skip_d32_one && a.bf16 ? 1 : 0;
     for (int r = 0; r < 2; ++r) a.Dtf[r] = nullptr;
     if (ctx->p.precision == FLR_PREC_TF32) {
         // rows rounded to nearest TF32 for the tensor-core A operand, allocated

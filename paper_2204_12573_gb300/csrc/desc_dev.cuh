@@ -39,6 +39,8 @@ struct DescArgs {
     float *D32[2];
     __nv_bfloat16 *Dhi[2], *Dlo[2];
     int bf16;                  // also write BF16 hi/lo rows
+    int skip_d32_one;          // do not write the FP32 rows of the one-species region (their
+                               // quadratic forms read only the BF16 rows)
     float *Dtf[2];             // also write rows rounded to nearest TF32 (TF32 precision), or nullptr
     float4 *pair_rec;          // [n][max_nbr] out: pairs inside r_cut (r_ij, j | s_j << 25)
     int32_t *pair_cnt;         // [n] out: their number

@@ -500,6 +500,7 @@ int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     d.A = ctx->A;
     d.norm = ctx->norm;
     d.bf16 = 0;
+    d.skip_d32_one = 0;
     d.pair_rec = nl->pair_rec;
     d.pair_cnt = nl->pair_cnt;
     d.order = nullptr;

@@ -226,7 +226,7 @@ int nbrlist_reserve_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, long lon
 // the device as *n_dev0 (+ *n_dev1), capped at n.
 int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                 cudaStream_t st, const int32_t *order = nullptr, const int *n_dev0 = nullptr,
-                const int *n_dev1 = nullptr);
+                const int *n_dev1 = nullptr, bool skip_d32_one = false);
 int launch_expand_desc(flr_ctx *ctx, const flr_nbrlist *nl, int n, float *d_hat, float *norm,
                        cudaStream_t st);
 int launch_qform_simt(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
