@@ -108,15 +108,18 @@ __device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, flo
     __syncwarp();
     const int my_n = lane >> 2, quad = lane & 3;
     if (my_n < N) {
+        // species-0 pairs, then species-1 pairs (the staged order), each in list order
 #pragma unroll 4
-        for (int p = 0; p < m; ++p) {
+        for (int p = 0; p < n0; ++p) {
             const float rf = dw.st.p.Rf[my_n][p];
             const float4 y = *reinterpret_cast<const float4 *>(&dw.st.p.Y[p][4 * quad]);
-            if (p < n0) {   // warp-uniform
-                acc0[0] += rf * y.x; acc0[1] += rf * y.y; acc0[2] += rf * y.z; acc0[3] += rf * y.w;
-            } else {
-                acc1[0] += rf * y.x; acc1[1] += rf * y.y; acc1[2] += rf * y.z; acc1[3] += rf * y.w;
-            }
+            acc0[0] += rf * y.x; acc0[1] += rf * y.y; acc0[2] += rf * y.z; acc0[3] += rf * y.w;
+        }
+#pragma unroll 4
+        for (int p = n0; p < m; ++p) {
+            const float rf = dw.st.p.Rf[my_n][p];
+            const float4 y = *reinterpret_cast<const float4 *>(&dw.st.p.Y[p][4 * quad]);
+            acc1[0] += rf * y.x; acc1[1] += rf * y.y; acc1[2] += rf * y.z; acc1[3] += rf * y.w;
         }
     }
     __syncwarp();
