@@ -81,8 +81,11 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
     // copied, one atom ahead
     const int n_take = force_count(a);
     const int i_end = a.order ? 0x7fffffff : a.n;
-    WarpChunks wc;
-    wc.init(a.sched, n_take, lane);
+    // chunks of up to kWarpChunk atoms, shorter when there are fewer than
+    // four chunks' worth per warp of the grid
+    const int per_warp = n_take / (4 * (int)gridDim.x * kWarpsForce);
+    WarpChunksR wc;
+    wc.init(a.sched, n_take, per_warp < 1 ? 1 : (per_warp < kWarpChunk ? per_warp : kWarpChunk), lane);
     int p = wc.pos();
     int i = p < n_take ? (a.order ? __ldg(a.order + p) : p) : i_end;
     AtomPre cur = preload(a, i, i_end, lane);

@@ -350,6 +350,50 @@ struct WarpChunksT {
 };
 using WarpChunks = WarpChunksT<kWarpChunk>;
 
+// The same claims with the chunk length chosen at launch: a launch over few
+// atoms (the two-species rows of a mostly one-species system) takes them one
+// by one, so they spread over all warps instead of 16 to a warp.
+struct WarpChunksR {
+    int n, ch, nchunks, cur, nxt, k;
+    int *counter;
+    __device__ __forceinline__ void init(int *ctr, int n_, int ch_, int lane)
+    {
+        counter = ctr;
+        n = n_;
+        ch = ch_;
+        nchunks = (n_ + ch_ - 1) / ch_;
+        k = 0;
+        int c0 = 0, c1 = 0;
+        if (lane == 0) {
+            c0 = atomicAdd(ctr, 1);
+            c1 = atomicAdd(ctr, 1);
+        }
+        cur = __shfl_sync(0xffffffffu, c0, 0);
+        nxt = __shfl_sync(0xffffffffu, c1, 0);
+    }
+    __device__ __forceinline__ int pos() const { return cur < nchunks ? cur * ch + k : n; }
+    __device__ __forceinline__ int peek() const
+    {
+        if (cur >= nchunks) return n;
+        const int p = cur * ch + k + 1;
+        if (k + 1 < ch && p < n) return p;
+        return nxt < nchunks ? nxt * ch : n;
+    }
+    __device__ __forceinline__ void advance(int lane)
+    {
+        const int p = cur * ch + k + 1;
+        if (cur < nchunks && k + 1 < ch && p < n) {
+            ++k;
+            return;
+        }
+        cur = nxt;
+        k = 0;
+        int c = nchunks;
+        if (lane == 0 && cur < nchunks) c = atomicAdd(counter, 1);
+        nxt = __shfl_sync(0xffffffffu, c, 0);
+    }
+};
+
 // Tiles of 128 rows over the one-species compaction groups (1, 2, 4, 5), in
 // that order: pre[k] is the first tile of the k-th of them.
 struct OneTile {

@@ -90,6 +90,31 @@ __device__ __forceinline__ TileInfo decode_tile(const GroupTab &T, const int *nc
     return ti;
 }
 
+// The tiles a launch takes: all of them, or (only_full) the two-species
+// groups' tiles alone, numbered 0 .. count-1 so that consecutive CTAs take
+// consecutive ones and no CTA gets a second tile before every CTA has one.
+__device__ __forceinline__ int tc_tile_count(const TcArgs &a, const GroupTab &T)
+{
+    if (!a.only_full) return T.tiles_tc[kGroups];
+    int m = 0;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g)
+        if (group_full(g)) m += T.tiles_tc[g + 1] - T.tiles_tc[g];
+    return m;
+}
+__device__ __forceinline__ int tc_tile(const TcArgs &a, const GroupTab &T, int u)
+{
+    if (!a.only_full) return u;
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+        if (!group_full(g)) continue;
+        const int m = T.tiles_tc[g + 1] - T.tiles_tc[g];
+        if (u < m) return T.tiles_tc[g] + u;
+        u -= m;
+    }
+    return T.tiles_tc[kGroups];
+}
+
 // d[c .. c+15] of a descriptor row (four float4 loads through the read-only
 // path, so they may be issued ahead of the g-row stores; c is a multiple of 4)
 __device__ __forceinline__ void load16(const float *p, float v[16])
@@ -125,7 +150,7 @@ __device__ __forceinline__ void prefetch_next_rows(const TcArgs &a, const GroupT
                                                    int sub)
 {
     if (tn >= total) return;
-    const TileInfo tj = decode_tile(T, a.nch, tn);
+    const TileInfo tj = decode_tile(T, a.nch, tc_tile(a, T, tn));
     const int rown = tj.row0 + rloc;
     if (rown >= tj.rend) return;
     const char *dn = reinterpret_cast<const char *>(a.D32[tj.reg] + (size_t)rown * a.kp32[tj.reg]);
@@ -212,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
     fence_after();
     const uint32_t tmem = *tmem_holder;
     const GroupTab &T = *a.gtab;
-    const int total = T.tiles_tc[kGroups];
+    const int total = tc_tile_count(a, T);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -222,9 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             int last_phase[kStages];
             for (int s = 0; s < kStages; ++s) last_phase[s] = -1;
             bool ok = true;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const TileInfo ti = decode_tile(T, a.nch, t);
-                if (a.only_full && !group_full(ti.g)) continue;
+            for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+                const TileInfo ti = decode_tile(T, a.nch, tc_tile(a, T, u));
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
                 for (int ch = 0; ch < ti.nch && ok; ++ch) {
@@ -271,9 +295,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
             int it = 0;   // accumulator uses (chunks)
             bool ok = true;
             bool issued = false;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const TileInfo ti = decode_tile(T, a.nch, t);
-                if (a.only_full && !group_full(ti.g)) continue;
+            for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+                const TileInfo ti = decode_tile(T, a.nch, tc_tile(a, T, u));
                 const int nkb = a.nkb[ti.reg];
                 const int nkt = BF16 ? 3 * nkb : nkb;
                 const int K = a.K[ti.reg];
@@ -334,9 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
         int it = 0;
         int tl = 0;                             // tiles done by this CTA
         bool alive = true;
-        for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
-            const TileInfo ti = decode_tile(T, a.nch, t);
-            if (a.only_full && !group_full(ti.g)) continue;
+        for (int u = blockIdx.x; u < total && alive; u += gridDim.x) {
+            const TileInfo ti = decode_tile(T, a.nch, tc_tile(a, T, u));
             const int K = a.K[ti.reg];
             const int row = ti.row0 + rloc;
             const bool valid = row < ti.rend;
@@ -384,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty);
-                prefetch_next_rows(a, T, t + gridDim.x, total, rloc, sub);
+                prefetch_next_rows(a, T, u + gridDim.x, total, rloc, sub);
                 if (!exchange(evx_buf, evx, tl, sub, rloc, lane, abort_flag, a.status, E, V, Va)) {
                     alive = false;
                     break;
@@ -460,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant_
                     if (lane == 0) mbar_arrive(tempty);
                 }
                 if (!alive) break;
-                prefetch_next_rows(a, T, t + gridDim.x, total, rloc, sub);
+                prefetch_next_rows(a, T, u + gridDim.x, total, rloc, sub);
                 if (!exchange(evx_buf, evx, tl, sub, rloc, lane, abort_flag, a.status, E, V, Va)) {
                     alive = false;
                     break;
