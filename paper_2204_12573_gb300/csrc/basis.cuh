@@ -154,4 +154,22 @@ __device__ __forceinline__ void radial(float r, float rc, float Rf[N], float dRf
     }
 }
 
+// T_n(x) and dT_n/dx for 2 <= n < N (T_0 = 1, T_1 = x, T_0' = 0, T_1' = 1
+// are left to the caller, which folds them into its sums)
+template <int N>
+__device__ __forceinline__ void cheb_tail(float x, float T[N], float dT[N])
+{
+    float tm2 = 1.f, tm1 = x;
+    float dm2 = 0.f, dm1 = 1.f;
+#pragma unroll
+    for (int n = 2; n < N; ++n) {
+        T[n] = 2.f * x * tm1 - tm2;
+        dT[n] = 2.f * tm1 + 2.f * x * dm1 - dm2;
+        tm2 = tm1;
+        tm1 = T[n];
+        dm2 = dm1;
+        dm1 = dT[n];
+    }
+}
+
 }  // namespace flr

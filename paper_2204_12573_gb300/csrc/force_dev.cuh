@@ -145,39 +145,50 @@ __device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
         const float d2 = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z;
         const float rr = sqrtf(d2), inv = 1.f / rr;
         const float ux = rec.x * inv, uy = rec.y * inv, uz = rec.z * inv;
-        float Rf[N], dRf[N];
-        radial<N, true>(rr, rc, Rf, dRf);
+        // R_n = T_n(x) f_c with x = 2r/r_cut - 1, f_c = (r_cut - r)^2 (the
+        // descriptor's radial basis).  The sums over n run on T_n and T_n'
+        // alone, and f_c, f_c' and dx/dr = 2/r_cut scale the per-pair totals:
+        //   c_lm = f_c s_lm,  c'_lm = (2/r_cut) f_c s'_lm + f_c' s_lm,
+        //   s_lm = sum_n w_{n,lm} T_n(x),  s'_lm = sum_n w_{n,lm} T_n'(x),
+        // so T_0 = 1 and T_1' = 1 cost no multiply and T_0' = 0 no term.
+        const float x = 2.f * rr / rc - 1.f;
+        const float tc = rc - rr;
+        const float fc = tc * tc, dfc = -2.f * tc, k1 = (2.f / rc) * fc;
+        float T[N], dT[N];
+        cheb_tail<N>(x, T, dT);
         const float *wp = fw.W + slot * FW::WSLOT + (FW::kOne ? 0 : sj * 128);
         const float xx = ux * ux, yy = uy * uy, zz = uz * uz;
-        // f = u (sum_lm c'_lm Y_lm - (1/r) sum_lm l c_lm Y_lm) + (1/r) sum_lm c_lm grad P_lm(u),
-        // c_lm = sum_n w_{n,lm} R_n f_c,  c'_lm = sum_n w_{n,lm} (R_n f_c)'
-        float radial_part = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-        float ls[4] = {0.f, 0.f, 0.f, 0.f};   // sum of c Y per l
+        // f = u (sum_lm c'_lm Y_lm - (1/r) sum_lm l c_lm Y_lm) + (1/r) sum_lm c_lm grad P_lm(u)
+        float sp_y = 0.f, s_y0 = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        float ls[4] = {0.f, 0.f, 0.f, 0.f};   // sum of s Y per l
 #pragma unroll
         for (int lm = 0; lm < 16; ++lm) {
             const float4 w0 = *reinterpret_cast<const float4 *>(wp + lm * 8);
             const float4 w1 = *reinterpret_cast<const float4 *>(wp + lm * 8 + 4);
             const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-            float c = 0.f, cp = 0.f;
+            float s = wv[0] + wv[1] * x, sp = wv[1];
 #pragma unroll
-            for (int n = 0; n < N; ++n) {
-                c += wv[n] * Rf[n];
-                cp += wv[n] * dRf[n];
+            for (int n = 2; n < N; ++n) {
+                s += wv[n] * T[n];
+                sp += wv[n] * dT[n];
             }
             float Y, dx, dy, dz;
             ylm_one(lm, ux, uy, uz, xx, yy, zz, Y, dx, dy, dz);
-            radial_part += cp * Y;
-            if (l_of(lm) > 0) ls[l_of(lm)] += c * Y;
+            sp_y += sp * Y;
+            if (l_of(lm) > 0) ls[l_of(lm)] += s * Y;
+            else s_y0 += s * Y;
             // only the components of grad P_lm that are not identically zero
-            if (grad_nz(lm, 0)) gx += c * dx;
-            if (grad_nz(lm, 1)) gy += c * dy;
-            if (grad_nz(lm, 2)) gz += c * dz;
+            if (grad_nz(lm, 0)) gx += s * dx;
+            if (grad_nz(lm, 1)) gy += s * dy;
+            if (grad_nz(lm, 2)) gz += s * dz;
         }
-        const float lsum = ls[1] + 2.f * ls[2] + 3.f * ls[3];
+        const float radial_part = k1 * sp_y + dfc * (s_y0 + ls[1] + ls[2] + ls[3]);
+        const float lsum = fc * (ls[1] + 2.f * ls[2] + 3.f * ls[3]);
         const float coef = radial_part - lsum * inv;
-        const float fx = coef * ux + gx * inv;
-        const float fy = coef * uy + gy * inv;
-        const float fz = coef * uz + gz * inv;
+        const float gsc = fc * inv;
+        const float fx = coef * ux + gx * gsc;
+        const float fy = coef * uy + gy * gsc;
+        const float fz = coef * uz + gz * gsc;
         const long long ix = to_fix(fx, status), iy = to_fix(fy, status), iz = to_fix(fz, status);
         unsigned long long *dj = Facc + 3 * (size_t)j;
         atomicAdd(dj + 0, (unsigned long long)(-ix));
