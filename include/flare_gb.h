@@ -210,6 +210,15 @@ int flr_set_precision(flr_ctx *ctx, int32_t precision);
  * Results agree within the 3xBF16 error (the epilogue uses the hi + lo
  * descriptor instead of the FP32 one). */
 #define FLR_OPT_FUSED_ONE_SPECIES 1
+/* FLR_OPT_OVERLAP_TWO_SPECIES: 1 (default) launches the one-species
+ * quadratic-form kernel as a programmatic dependent of the two-species one
+ * before it (Sec. V-B compaction classes; the two-species classes hold a few
+ * atoms of a slab, at the full descriptor length), so it starts on the SMs
+ * the two-species tiles leave free instead of after them; with
+ * FLR_PREC_BF16X3 and compaction on.  Everything stays on the caller's
+ * stream.  0: one kernel after the other.  Results are bitwise the same
+ * either way. */
+#define FLR_OPT_OVERLAP_TWO_SPECIES 2
 int flr_set_option(flr_ctx *ctx, int32_t option, int32_t value);
 
 /* Upload the mapped model of central species `species` (Eq. 1, Eq. 2):

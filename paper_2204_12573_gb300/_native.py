@@ -50,6 +50,7 @@ EXPORTED = [
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild", "fused"]
 OPT_FUSED_ONE_SPECIES = 1
+OPT_OVERLAP_TWO_SPECIES = 2
 
 
 class Params(ctypes.Structure):

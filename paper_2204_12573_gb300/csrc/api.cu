@@ -258,9 +258,14 @@ int launch_qform(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStre
     if (ctx->p.precision == FLR_PREC_FP32) return launch_qform_simt(ctx, nl, out, st);
     if (ctx->p.precision == FLR_PREC_BF16X3 && ctx->p.compaction) {
         // two-species tiles on the general kernel, one-species tiles on the
-        // kernel that loads each operand of a K block once
+        // kernel with the resident A tile.  With the overlap option the second
+        // starts as a programmatic dependent of the first, on the SMs its few
+        // tiles leave free (its tile counter is cleared before both, so no
+        // stream operation sits between the two launches)
+        const cudaError_t e = cudaMemsetAsync(ctx->sched + 4, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "quadratic-form tile counter");
         int s = launch_qform_tc(ctx, nl, out, st, true);
-        if (s == FLR_OK) s = launch_qform1(ctx, nl, out, st);
+        if (s == FLR_OK) s = launch_qform1(ctx, nl, out, st, ctx->overlap != 0);
         return s;
     }
     return launch_qform_tc(ctx, nl, out, st);
@@ -447,8 +452,9 @@ int flr_create(const flr_params *p, int device, flr_ctx **out)
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     flr_ctx *c = new flr_ctx();
-    c->use_fused = 0;   // the separate kernels are faster on GB300 so far
     std::memset(static_cast<void *>(c), 0, sizeof(flr_ctx));
+    c->use_fused = 0;   // the separate kernels are faster on GB300 so far
+    c->overlap = 1;
     c->p = *p;
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -467,7 +473,7 @@ int flr_create(const flr_params *p, int device, flr_ctx **out)
     }
     int s = dev_alloc(&c->status, 4, "status word");
     if (s == FLR_OK) s = dev_alloc(&c->ref_count, 1, "variance queue counter");
-    if (s == FLR_OK) s = dev_alloc(&c->sched, 4, "work counters");
+    if (s == FLR_OK) s = dev_alloc(&c->sched, 8, "work counters");
     if (s == FLR_OK) s = dev_alloc(&c->md_sc, 8 + 256, "MD scalars");
     if (s == FLR_OK) s = dev_alloc(&c->md_totals, FLR_NTOTALS, "MD totals");
     if (s == FLR_OK) s = dev_alloc(&c->md_cnt, 2, "MD counters");
@@ -558,11 +564,15 @@ int flr_set_precision(flr_ctx *c, int32_t precision)
 
 int flr_set_option(flr_ctx *c, int32_t option, int32_t value)
 {
-    if (!c || option != FLR_OPT_FUSED_ONE_SPECIES || (value != 0 && value != 1)) {
+    if (!c || (option != FLR_OPT_FUSED_ONE_SPECIES && option != FLR_OPT_OVERLAP_TWO_SPECIES) ||
+        (value != 0 && value != 1)) {
         set_error("flr_set_option: invalid option or value");
         return FLR_EINVAL;
     }
-    c->use_fused = value;
+    if (option == FLR_OPT_FUSED_ONE_SPECIES)
+        c->use_fused = value;
+    else
+        c->overlap = value;
     return FLR_OK;
 }
 

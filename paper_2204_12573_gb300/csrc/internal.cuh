@@ -138,7 +138,7 @@ struct flr_ctx {
     float sigma_norm[flr::kGroups];    // largest eigenvalue of each group's Sigma block (power iteration)
     int32_t *ref_list;                 // [ws_n] atoms queued for the FP64 variance
     int *ref_count;                    // device counter of ref_list
-    int *sched;                        // device work counters of the per-atom kernels [4]
+    int *sched;                        // device work counters [8]: descriptor, force (two-species), list build, force (one-species), one-species quadratic-form tiles
     double *md_sc;                     // MD scalars: [0] xi, [1] eta, [2] KE, [3] scale, [8..8+256) KE partials
     double *md_totals;                 // totals of flr_md_step when the caller passes none
     int *md_cnt;                       // [2] uncertainty and coordination counts
@@ -169,6 +169,7 @@ struct flr_ctx {
     void *q1maps;              // tensor maps of the one-species quadratic-form kernel
     int q1maps_n;              // workspace size they were encoded for
     int use_fused;             // FLR_OPT_FUSED_ONE_SPECIES
+    int overlap;               // FLR_OPT_OVERLAP_TWO_SPECIES
     TcMaps *maps;              // host copy of the current tensor maps
     int maps_n;                // workspace size the maps were encoded for
     int maps_prec;
@@ -241,9 +242,12 @@ bool fused_eligible(const flr_ctx *ctx);
 int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, cudaStream_t st);
 void free_fused_maps(flr_ctx *ctx);
-// Quadratic forms of the one-species tiles, 3xBF16 (each K block of A hi/lo
-// and B hi/lo loaded once per tile)
-int launch_qform1(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st);
+// Quadratic forms of the one-species tiles, 3xBF16 (each tile's A hi/lo
+// resident in shared memory; tiles past the first per CTA claimed from a counter)
+// pdl: launched as a programmatic dependent of the kernel before it on st
+// (which must trigger its dependents); its tile counter (sched[4]) must have
+// been cleared on st before that kernel
+int launch_qform1(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st, bool pdl);
 void free_q1_maps(flr_ctx *ctx);
 int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
                  flr_outputs *out, float *vir_atom, const float *weight, cudaStream_t st);

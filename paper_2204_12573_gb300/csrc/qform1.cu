@@ -21,6 +21,10 @@
 // MMAs, combine the partial E and V, write E, V, sigma and the g row, and
 // release the A buffer.
 //
+// Tiles: each CTA's first is blockIdx.x, the rest are claimed from a counter
+// by the producer, which hands the tile index to the MMA and epilogue warps
+// with the A buffer, so CTAs that start late take fewer tiles.
+//
 // Every wait is bounded (about 2 s of %globaltimer); on expiry the kernel
 // records FLR_ETIMEOUT, stops, waits (bounded) for its own copies and MMAs,
 // frees its tensor memory and returns.
@@ -77,6 +81,7 @@ struct Q1Args {
     int *ref_count;
     int ref_cap;
     int *status;
+    int *tile_ctr;            // tiles past the first gridDim.x are claimed from it (zero at launch)
 };
 
 __device__ __forceinline__ bool q_warp_wait(uint32_t bar, uint32_t parity, int lane, volatile int *abort_flag,
@@ -105,6 +110,9 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + D::OFF_BAR);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + D::N_BARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    // the tile each A buffer holds, written by the producer before it arms the
+    // buffer's barrier (total: no more tiles)
+    volatile int *tile_of = reinterpret_cast<volatile int *>(tmem_holder + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kQStages);
@@ -149,13 +157,21 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
             int last_phase[kQStages], last_a[2] = {-1, -1};
             for (int s = 0; s < kQStages; ++s) last_phase[s] = -1;
             bool ok = true;
-            int k = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++k) {
-                const OneTile ti = one_species_tile(T, pre, t);
+            // the first tile of each CTA is blockIdx.x, later ones are claimed
+            // from a counter, so CTAs that start late (their SM busy with other
+            // work) take fewer tiles instead of delaying the end
+            int t = blockIdx.x;
+            for (int k = 0; ok; ++k) {
                 const int buf = k & 1;
-                // the A buffer is free once the epilogue of the tile two back has finished
+                // the A buffer (and its tile slot) is free once the epilogue of the tile two back has finished
                 if (!mbar_wait(aempty0 + 8 * buf, (uint32_t)(((k >> 1) & 1) ^ 1), abort_flag)) { ok = false; break; }
                 const uint32_t ab = afull0 + 8 * buf;
+                tile_of[buf] = t < total ? t : total;
+                if (t >= total) {
+                    mbar_arrive(ab);   // no more tiles: release the consumers without data
+                    break;
+                }
+                const OneTile ti = one_species_tile(T, pre, t);
                 mbar_expect_tx(ab, D::A_BUF);
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
@@ -167,6 +183,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
                                     64 * AT::NA + 16 * ts, ti.row0, ab);
                 }
                 last_a[buf] = (k >> 1) & 1;
+                const int t_next = (int)gridDim.x + atomicAdd(a.tile_ctr, 1);
                 for (int ks = 0; ks < AT::KSTEPS; ++ks) {
                     if (!mbar_wait(empty0 + 8 * stage, phase ^ 1, abort_flag)) { ok = false; break; }
                     const uint32_t fb = full0 + 8 * stage;
@@ -181,6 +198,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
                     last_phase[stage] = (int)phase;
                     if (++stage == kQStages) { stage = 0; phase ^= 1; }
                 }
+                t = t_next;
             }
             if (!ok) {
                 atomicOr(a.status, kErrTimeout);
@@ -208,12 +226,12 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true, issued = false;
-            int k = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++k) {
+            for (int k = 0; ok; ++k) {
                 const int buf = k & 1;
                 if (!mbar_wait(tempty, (uint32_t)((k & 1) ^ 1), abort_flag)) { ok = false; break; }
                 if (!mbar_wait(afull0 + 8 * buf, (uint32_t)((k >> 1) & 1), abort_flag)) { ok = false; break; }
                 fence_after();
+                if (tile_of[buf] >= total) break;
                 const uint32_t ahi0 = smem_u32(base + buf * D::A_BUF), alo0 = ahi0 + AT::PART;
                 for (int ks = 0; ks < AT::KSTEPS; ++ks) {
                     if (!mbar_wait(full0 + 8 * stage, phase, abort_flag)) { ok = false; break; }
@@ -252,11 +270,18 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
         const int sub = (warp - 2) >> 2;
         const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
         const int rloc = qw * 32 + lane;
-        int k = 0;
         bool alive = true;
-        for (int t = blockIdx.x; t < total && alive; t += gridDim.x, ++k) {
-            const OneTile ti = one_species_tile(T, pre, t);
+        for (int k = 0; alive; ++k) {
             const int buf = k & 1;
+            // the tile's A rows (TMA-written: acquire their barrier) and which tile it is
+            if (!q_warp_wait(afull0 + 8 * buf, (uint32_t)((k >> 1) & 1), lane, abort_flag, a.status)) {
+                alive = false;
+                break;
+            }
+            fence_after();
+            const int t = tile_of[buf];
+            if (t >= total) break;
+            const OneTile ti = one_species_tile(T, pre, t);
             const uint8_t *shi = base + buf * D::A_BUF, *slo = shi + AT::PART;
             const int row = ti.row0 + rloc;
             const bool valid = row < ti.rend;
@@ -265,9 +290,8 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
             float *grow = a.G1 + (size_t)(valid ? row : 0) * K;
             const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
             const bool fact = a.var_factored[ti.g] != 0;
-            // the tile's A rows (TMA-written: acquire their barrier too) and its accumulator
-            if (!q_warp_wait(afull0 + 8 * buf, (uint32_t)((k >> 1) & 1), lane, abort_flag, a.status) ||
-                !q_warp_wait(tfull, (uint32_t)(k & 1), lane, abort_flag, a.status)) {
+            // its accumulator
+            if (!q_warp_wait(tfull, (uint32_t)(k & 1), lane, abort_flag, a.status)) {
                 alive = false;
                 break;
             }
@@ -345,16 +369,30 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
     __syncthreads();
     fence_after();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    // launched as a programmatic dependent: finish only after the kernel before
+    // it on the stream has (nothing here reads its results; the kernels after
+    // this one rely on both being complete).  Without that launch it returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <int N>
-int launch_qform1_n(flr_ctx *ctx, const Q1Args &a, cudaStream_t st)
+int launch_qform1_n(flr_ctx *ctx, const Q1Args &a, cudaStream_t st, bool pdl)
 {
     const size_t smem = 1024 + (size_t)QDims<N>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_qform1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "one-species quadratic-form kernel attributes");
-    k_qform1<N><<<ctx->num_sms, kQThreads, smem, st>>>(*reinterpret_cast<const Q1Maps *>(ctx->q1maps), a);
-    return FLR_OK;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctx->num_sms);
+    cfg.blockDim = dim3(kQThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, k_qform1<N>, *reinterpret_cast<const Q1Maps *>(ctx->q1maps), a);
+    return cuda_fail(e, "one-species quadratic-form kernel launch");
 }
 
 int ensure_q1_maps(flr_ctx *ctx)
@@ -394,7 +432,7 @@ void free_q1_maps(flr_ctx *ctx)
     ctx->q1maps = nullptr;
 }
 
-int launch_qform1(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st)
+int launch_qform1(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st, bool pdl)
 {
     int s = ensure_q1_maps(ctx);
     if (s != FLR_OK) return s;
@@ -415,7 +453,8 @@ int launch_qform1(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStr
     a.ref_count = ctx->ref_count;
     a.ref_cap = ctx->ws_n;
     a.status = ctx->status;
-    s = ctx->dims.N == 8 ? launch_qform1_n<8>(ctx, a, st) : launch_qform1_n<7>(ctx, a, st);
+    a.tile_ctr = ctx->sched + 4;
+    s = ctx->dims.N == 8 ? launch_qform1_n<8>(ctx, a, st, pdl) : launch_qform1_n<7>(ctx, a, st, pdl);
     if (s != FLR_OK) return s;
     count_launch(ctx);
     return cuda_fail(cudaGetLastError(), "one-species quadratic-form kernel");

@@ -196,6 +196,10 @@ __device__ __forceinline__ bool exchange(float4 *evx_buf, uint32_t evx, int tl, 
 template <bool BF16>
 __global__ void __launch_bounds__(kThreads, 1) k_qform_tc(const __grid_constant__ TcMaps maps, TcArgs a)
 {
+    // a kernel launched after this one as a programmatic dependent (the
+    // one-species tiles) may start once every CTA of this grid is resident:
+    // it takes the SMs this grid's few two-species tiles leave free
+    asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ uint8_t dyn[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = base;

@@ -95,6 +95,12 @@ class FlareGB:
         tensor-core kernel (3xBF16 with compaction), or separate kernels."""
         N.check(self.lib.flr_set_option(self.handle, N.OPT_FUSED_ONE_SPECIES, 1 if on else 0))
 
+    def set_overlap(self, on: bool):
+        """FLR_OPT_OVERLAP_TWO_SPECIES: the one-species quadratic-form kernel
+        starts beside the two-species one as a programmatic dependent (3xBF16
+        with compaction; default on), or after it."""
+        N.check(self.lib.flr_set_option(self.handle, N.OPT_OVERLAP_TWO_SPECIES, 1 if on else 0))
+
     def set_variance_mode(self, mode: str):
         """"auto" (FP32 quadratic form, FP64 re-evaluation of cancelled
         variances), "direct" (FP32 only) or "factored" (V = |L^T d|^2)."""

@@ -86,13 +86,15 @@ def decode_entries(entries, count):
 
 
 def gpu_run(struct, beta, sigma, precision="fp32", compaction=True, max_nbr=64, n_max=8, want_desc=False,
-            fused=None, profile=False):
+            fused=None, profile=False, overlap=None):
     import torch
     from paper_2204_12573_gb300 import flare as F
     ff = F.FlareGB(n_max=n_max, precision=precision, compaction=compaction, max_nbr=max_nbr)
     ff.set_model(beta, sigma)
     if fused is not None:
         ff.set_fused(fused)
+    if overlap is not None:
+        ff.set_overlap(overlap)
     if profile:
         ff.profile(True)
     pos4 = synth.as_f32_positions(struct.pos)

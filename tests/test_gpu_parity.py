@@ -172,6 +172,38 @@ def test_fused_and_separate_kernels_agree():
     assert (np.abs(a["variance"] - b["variance"]) <= 1e-4 * np.abs(b["variance"]) + 1e-5).all()
 
 
+def test_two_species_overlap_is_bitwise_serial():
+    """The one-species quadratic-form kernel launched as a programmatic
+    dependent of the two-species one (the default) and launched after it give
+    bitwise the same outputs: each tile is computed by one CTA either way,
+    whichever CTA claims it.  Over MD steps too, with the rebuilds in between."""
+    import torch
+    from paper_2204_12573_gb300 import flare as F
+    s = _slabs(3)[2]
+    a, *_ = gpu_run(s, BETA, SIGMA, precision="bf16x3", overlap=True)
+    b, *_ = gpu_run(s, BETA, SIGMA, precision="bf16x3", overlap=False)
+    groups = b["group"]
+    assert (groups % 3 == 0).sum() > 0 and (groups % 3 != 0).sum() > 0   # both compaction classes present
+    for k in ("energy", "forces", "variance", "sigma"):
+        assert np.array_equal(a[k], b[k]), k
+    runs = []
+    for ovl in (True, False):
+        ff = F.FlareGB(precision="bf16x3")
+        ff.set_model(BETA, SIGMA)
+        ff.set_overlap(ovl)
+        sysg = F.System.from_numpy(synth.as_f32_positions(s.pos), s.species, s.cell, s.pbc)
+        vel = torch.as_tensor(synth.maxwell_velocities(s.species, 300.0, 5), device="cuda")
+        nl = ff.nbrlist(s.n_atoms)
+        F.build_neighbors(ff, sysg, nl)
+        st = F.MDState(sysg, vel, dt=0.0005, rebuild_every=3)
+        out = F.make_outputs(s.n_atoms)
+        F.md_step(ff, st, nl, 8, out)
+        ff.sync()
+        runs.append((sysg.pos.cpu().numpy().copy(), st.vel.cpu().numpy().copy(), out["forces"].cpu().numpy().copy()))
+    for x, y in zip(runs[0], runs[1]):
+        assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("precision", ["tf32", "bf16x3"])
 def test_mixed_precision_other_models(precision):
     """The same bounds for other seeded models and for |beta|_2 = 2 eV (forces
