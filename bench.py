@@ -339,6 +339,7 @@ def run_ours(args):
     import oracle as O
     from paper_2204_12573_gb300 import flare as F
     from paper_2204_12573_gb300 import synth
+    from paper_2204_12573_gb300 import _native as N
 
     if args.small:
         struct = synth.big_slab(seed=1, nx=64, n_rows=64, n_layers=32, n_h2=1024)
@@ -388,8 +389,9 @@ def run_ours(args):
         if clocks:
             clocks.__exit__()
         ms = e0.elapsed_time(e1)
-        launches = ff.launch_count() - l0
         rebuild_count[precision] = int(out["totals"][13].item())
+        # host-counted launches, plus the rebuild kernels the conditional graph ran on rebuild steps
+        launches = ff.launch_count() - l0 + rebuild_count[precision] * N.REBUILD_KERNELS
         prof = None
         if profile:
             prof = ff.profile_read()

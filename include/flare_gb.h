@@ -341,7 +341,12 @@ int flr_md_step(flr_ctx *ctx, flr_md_state *st, flr_nbrlist *nl, int32_t n_steps
 /* Synchronize `stream` and report (and clear) device-side errors. */
 int flr_sync(flr_ctx *ctx, flr_stream_t stream);
 
-/* Number of kernels the library launched on this context so far. */
+/* Number of kernels the library launched on this context so far, as counted
+ * on the host.  flr_md_step runs each step's list rebuild as a conditional
+ * graph: it counts the graph's one condition kernel per step, and the
+ * FLR_REBUILD_KERNELS kernels of a rebuild run only on the steps that
+ * rebuild (FLR_TOT_N_REBUILDS of them), which the host cannot see. */
+#define FLR_REBUILD_KERNELS 13
 int64_t flr_launch_count(const flr_ctx *ctx);
 
 /* Cell-list neighbour search that allocates no memory.  (No counterpart in

@@ -51,6 +51,7 @@ EXPORTED = [
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild", "fused"]
 OPT_FUSED_ONE_SPECIES = 1
 OPT_OVERLAP_TWO_SPECIES = 2
+REBUILD_KERNELS = 13   # FLR_REBUILD_KERNELS
 
 
 class Params(ctypes.Structure):

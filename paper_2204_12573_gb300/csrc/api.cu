@@ -822,6 +822,7 @@ int flr_nbrlist_destroy(flr_nbrlist *nl)
     if (!nl) return FLR_OK;
     cudaSetDevice(nl->ctx->device);
     cudaDeviceSynchronize();
+    free_rebuild_graph(nl);
     cudaFree(nl->entries);
     cudaFree(nl->count);
     cudaFree(nl->group);
@@ -1098,7 +1099,7 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
         prof_end(c, FLR_KERNEL_DRIFT, st);
         if (s == FLR_OK && (md->step + 1) % md->rebuild_every == 0) s = launch_set_rebuild(c, nl, st);
         prof_begin(c, FLR_KERNEL_REBUILD, st);
-        if (s == FLR_OK) s = launch_rebuild(c, nl, pos, md->species, n, st, true, pos);
+        if (s == FLR_OK) s = launch_rebuild_cond(c, nl, pos, md->species, n, st, true, pos);
         prof_end(c, FLR_KERNEL_REBUILD, st);
         if (s == FLR_OK) s = evaluate(c, nl, pos, md->species, n, &o, kick, st);
         if (s == FLR_OK && nvt) {

@@ -231,7 +231,11 @@ struct TotArgs {
     int kick;
 };
 
-__global__ void __launch_bounds__(1024) k_totals(TotArgs a)
+// One block of 128 threads: the FP64 pipe of one SM is narrow on this part,
+// and the warp-shuffle tree costs 12 FP64 adds per thread and level, so fewer
+// threads finish sooner (1024 threads spent most of 40 us in the tree).
+constexpr int kTotThreads = 128;
+__global__ void __launch_bounds__(kTotThreads) k_totals(TotArgs a)
 {
     __shared__ double red[32][12];
     double acc[12];
@@ -455,7 +459,7 @@ int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out
     t.nl_flags = nl ? nl->flags : nullptr;
     t.ref_count = ctx->var_mode == FLR_VAR_AUTO ? ctx->ref_count : nullptr;
     t.kick = kick.enabled;
-    if (out->totals) k_totals<<<1, 1024, 0, st>>>(t);
+    if (out->totals) k_totals<<<1, kTotThreads, 0, st>>>(t);
     count_launch(ctx, out->totals ? 2 : 1);
     return cuda_fail(cudaGetLastError(), "finalize");
 }

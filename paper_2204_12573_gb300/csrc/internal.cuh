@@ -112,6 +112,7 @@ struct flr_nbrlist {
     flr::Plan *plans_h;    // host  [structs_cap]
     int32_t *offsets_h;    // host  [structs_cap + 1]
     long long nbins_total; // bins of all structures
+    void *rgraph;          // the MD steps' conditional rebuild graph (nbr.cu), or nullptr
 };
 
 // TMA tensor maps of the tcgen05 path: A operands per region (BF16 hi / lo,
@@ -213,6 +214,14 @@ int plan_batch(flr_ctx *ctx, flr_nbrlist *nl, int n_structs, const int32_t *offs
                const int32_t *pbc, const float4 *pos, int n, cudaStream_t st, const float *host_bb = nullptr);
 void host_frac_bbox(const double *cell, const float *pos4, int n, float bb[8]);
 int launch_set_rebuild(flr_ctx *ctx, flr_nbrlist *nl, cudaStream_t st);
+// The rebuild sequence of launch_rebuild as the body of a conditional graph
+// node that runs only when the list's rebuild flag is set (MD steps): a step
+// that needs no rebuild then launches one small kernel instead of the whole
+// early-exiting sequence.  The graph is kept with the list and rebuilt when
+// any host-side argument of the sequence changes.
+int launch_rebuild_cond(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                        cudaStream_t st, bool wrap_positions, float4 *pos_mut);
+void free_rebuild_graph(flr_nbrlist *nl);
 // serving-loop access to the context (api.cu)
 int srv_reserve_workspace(flr_ctx *ctx, int n);
 int srv_evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,

@@ -1141,8 +1141,121 @@ int launch_rebuild(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *
     k_group_rows<<<nblk, kGroupBlock, 0, st>>>(nl->group, n, nl->blk_group, nl->gtab, nl->row,
                                                nl->atom_of_row, nl->n_cap, nl->flags);
     k_rebuild_done<<<1, 1, 0, st>>>(nl->flags);
-    count_launch(ctx, 14);
+    count_launch(ctx, FLR_REBUILD_KERNELS);
     return cuda_fail(cudaGetLastError(), "neighbour rebuild");
+}
+
+namespace {
+
+__global__ void k_rebuild_cond(cudaGraphConditionalHandle h, const int32_t *flags)
+{
+    cudaGraphSetConditional(h, flags[0] != 0 ? 1u : 0u);
+}
+
+// Every host-side value the rebuild sequence bakes into its launches.
+constexpr int kKeyWords = 40;
+struct RebuildGraph {
+    cudaGraphExec_t exec;
+    unsigned long long key[kKeyWords];
+};
+
+void rebuild_key(const flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                 bool wrap, const float4 *pos_mut, unsigned long long *k)
+{
+    int q = 0;
+    auto put = [&](unsigned long long v) { k[q++] = v; };
+    auto ptr = [&](const void *v) { put(reinterpret_cast<uintptr_t>(v)); };
+    ptr(pos); ptr(species); put((unsigned long long)n); put(wrap ? 1 : 0); ptr(pos_mut);
+    put((unsigned long long)nl->nbins_total); put((unsigned long long)nl->n_structs); ptr(nl->struct_of);
+    ptr(nl->bin_fill); ptr(nl->bin_start); ptr(nl->bin_atoms); ptr(nl->atom_bin); ptr(nl->img);
+    ptr(nl->pos_ref); ptr(nl->pos_bin); ptr(nl->gtab); ptr(nl->flags); ptr(nl->status); ptr(nl->sched);
+    ptr(nl->plans_d); ptr(nl->shift_d); ptr(nl->blk_group); put((unsigned long long)nl->n_cap);
+    put((unsigned long long)nl->max_nbr); ptr(nl->entries); ptr(nl->count); ptr(nl->group); ptr(nl->row);
+    ptr(nl->atom_of_row);
+    put((unsigned long long)ctx->num_sms); put((unsigned long long)ctx->p.compaction);
+    double rc = ctx->p.r_cut, sk = ctx->p.skin;
+    unsigned long long b;
+    std::memcpy(&b, &rc, 8); put(b);
+    std::memcpy(&b, &sk, 8); put(b);
+    put((unsigned long long)ctx->dims.K[0]); put((unsigned long long)ctx->dims.K[1]);
+    while (q < kKeyWords) put(0);
+}
+
+}  // namespace
+
+void free_rebuild_graph(flr_nbrlist *nl)
+{
+    RebuildGraph *rg = reinterpret_cast<RebuildGraph *>(nl->rgraph);
+    if (!rg) return;
+    if (rg->exec) cudaGraphExecDestroy(rg->exec);
+    delete rg;
+    nl->rgraph = nullptr;
+}
+
+int launch_rebuild_cond(flr_ctx *ctx, flr_nbrlist *nl, const float4 *pos, const int *species, int n,
+                        cudaStream_t st, bool wrap_positions, float4 *pos_mut)
+{
+    unsigned long long key[kKeyWords];
+    rebuild_key(ctx, nl, pos, species, n, wrap_positions, pos_mut, key);
+    RebuildGraph *rg = reinterpret_cast<RebuildGraph *>(nl->rgraph);
+    if (!rg || std::memcmp(rg->key, key, sizeof(key)) != 0) {
+        free_rebuild_graph(nl);
+        // graph: [k_rebuild_cond] -> [if (flag) { the rebuild sequence }]
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaGraphCreate(&g, 0);
+        cudaGraphConditionalHandle h = 0;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        cudaGraphNode_t n_cond = nullptr, n_if = nullptr;
+        if (e == cudaSuccess) {
+            cudaKernelNodeParams kp = {};
+            const int32_t *flags = nl->flags;
+            void *args[] = {&h, &flags};
+            kp.func = reinterpret_cast<void *>(k_rebuild_cond);
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(1);
+            kp.kernelParams = args;
+            e = cudaGraphAddKernelNode(&n_cond, g, nullptr, 0, &kp);
+        }
+        cudaGraphNodeParams cp = {};
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&n_if, g, &n_cond, nullptr, 1, &cp);
+        }
+        int s = FLR_OK;
+        if (e == cudaSuccess) {
+            // record the sequence into the body on a private stream (no work runs)
+            cudaStream_t cs = nullptr;
+            e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) {
+                e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const long long launches = ctx->launches;
+                    s = launch_rebuild(ctx, nl, pos, species, n, cs, wrap_positions, pos_mut);
+                    ctx->launches = launches;   // counted per graph launch instead
+                    cudaGraph_t body = nullptr;
+                    const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
+                    if (e == cudaSuccess) e = e2;
+                }
+                cudaStreamDestroy(cs);
+            }
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && s == FLR_OK) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (s != FLR_OK) return s;
+        if (e != cudaSuccess) return cuda_fail(e, "conditional rebuild graph");
+        rg = new RebuildGraph();
+        rg->exec = exec;
+        std::memcpy(rg->key, key, sizeof(key));
+        nl->rgraph = rg;
+    }
+    // one kernel per step; the sequence's 14 kernels only on rebuild steps
+    count_launch(ctx, 1);
+    return cuda_fail(cudaGraphLaunch(rg->exec, st), "conditional rebuild graph launch");
 }
 
 }  // namespace flr

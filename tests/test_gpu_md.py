@@ -251,3 +251,33 @@ def test_coordination_count_of_h2():
             cnt += int((dist < cut).any())
         assert out["totals"][16].item() == cnt
     assert cnt == 0                      # no H pair closer than 0.5 A
+
+
+def test_rebuild_steps_match_a_fresh_build():
+    """MD steps run the list rebuild as a conditional graph (the sequence runs
+    only when the rebuild flag is set).  With a rebuild due every step, the
+    list after the last step must equal, entry for entry, a fresh build at the
+    final (wrapped) positions; with rebuilds every 4 steps over 6 steps,
+    exactly one rebuild is counted unless the displacement trigger fired."""
+    from paper_2204_12573_gb300 import flare as F
+    s = _pt_slab(3)
+    ff, sysg, vel, nl, st = _setup(s, 0.002)
+    st.c.rebuild_every = 1
+    out = F.make_outputs(s.n_atoms)
+    F.md_step(ff, st, nl, 3, out)
+    ff.sync()
+    assert int(out["totals"][13].item()) == 3
+    e1, c1, g1 = (t.cpu().numpy() for t in nl.view(s.n_atoms))
+    nl2 = ff.nbrlist(s.n_atoms)
+    F.build_neighbors(ff, sysg, nl2)
+    e2, c2, g2 = (t.cpu().numpy() for t in nl2.view(s.n_atoms))
+    assert np.array_equal(c1, c2) and np.array_equal(g1, g2)
+    for i in range(s.n_atoms):
+        assert np.array_equal(np.sort(e1[i, :c1[i]]), np.sort(e2[i, :c2[i]]))
+    # a cadence of 4: steps 4 and (if the trigger fires) others rebuild; step 1-3 and 5-6 skip the body
+    ff3, sysg3, vel3, nl3, st3 = _setup(s, 0.0005)
+    st3.c.rebuild_every = 4
+    out3 = F.make_outputs(s.n_atoms)
+    F.md_step(ff3, st3, nl3, 6, out3)
+    ff3.sync()
+    assert 1 <= int(out3["totals"][13].item()) <= 6
