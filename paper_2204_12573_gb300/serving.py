@@ -12,6 +12,7 @@ alive until its completion is polled.
 from __future__ import annotations
 
 import ctypes
+import gc
 import itertools
 import threading
 import time
@@ -183,25 +184,51 @@ def open_loop(server, pool, rate, seconds, seed=4, drain_timeout=120.0):
             if finished.is_set() and time.monotonic() > t_drain_end[0]:
                 break
 
+    # host-side stalls of the load generator, reported with the result:
+    # garbage-collector pauses (timed by a gc callback), the longest submit
+    # call and the longest oversleep
+    gc_pause = []
+    gc_t = [0]
+
+    def on_gc(phase, info):
+        if phase == "start":
+            gc_t[0] = time.monotonic_ns()
+        else:
+            gc_pause.append(time.monotonic_ns() - gc_t[0])
+
+    # objects alive before the run (the pool, the server, the interpreter's
+    # own) are frozen out of the collector's full passes
+    gc.collect()
+    gc.freeze()
+    gc.callbacks.append(on_gc)
     t_drain_end = [float("inf")]
     th = threading.Thread(target=collect, daemon=True)
     t0 = time.monotonic_ns()
     th.start()
     late = 0
-    for k in range(n_req):
-        t_arr = t0 + int(arrivals[k] * 1e9)
-        dt = (t_arr - time.monotonic_ns()) / 1e9
-        if dt > 0:
-            time.sleep(dt)
-        elif dt < -1e-3:
-            late += 1
-        pos4, species, cell, pbc = pool[picks[k]]
-        tag = k + 1
-        sched[tag] = (t_arr, len(species))
-        server.submit(pos4, species, cell, pbc, fields=("energy", "forces", "sigma"), tag=tag)
-    t_drain_end[0] = time.monotonic() + drain_timeout
-    finished.set()
-    th.join()
+    max_submit = 0
+    max_oversleep = 0
+    try:
+        for k in range(n_req):
+            t_arr = t0 + int(arrivals[k] * 1e9)
+            dt = (t_arr - time.monotonic_ns()) / 1e9
+            if dt > 0:
+                time.sleep(dt)
+                max_oversleep = max(max_oversleep, time.monotonic_ns() - t_arr)
+            elif dt < -1e-3:
+                late += 1
+            pos4, species, cell, pbc = pool[picks[k]]
+            tag = k + 1
+            sched[tag] = (t_arr, len(species))
+            ts = time.monotonic_ns()
+            server.submit(pos4, species, cell, pbc, fields=("energy", "forces", "sigma"), tag=tag)
+            max_submit = max(max_submit, time.monotonic_ns() - ts)
+        t_drain_end[0] = time.monotonic() + drain_timeout
+        finished.set()
+        th.join()
+    finally:
+        gc.callbacks.remove(on_gc)
+        gc.unfreeze()
     t_last = time.monotonic_ns()
     wall = (t_last - t0) / 1e9
     st1 = server.stats()
@@ -215,6 +242,9 @@ def open_loop(server, pool, rate, seconds, seed=4, drain_timeout=120.0):
                 atoms_per_s=atoms_done[0] / wall, offered_atoms_per_s=float(
                     sum(len(pool[p][1]) for p in picks) / seconds),
                 mean_batch_structs=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
-                late_submits=late, batches=len(ivals), batches_overlapping_previous=overlap,
+                late_submits=late, max_submit_ms=max_submit / 1e6, max_oversleep_ms=max_oversleep / 1e6,
+                gc_pauses=len(gc_pause), gc_max_ms=(max(gc_pause) / 1e6 if gc_pause else 0.0),
+                max_batch_gpu_ms=max((v[3] - k0 for k0, v in ivals), default=0.0),
+                batches=len(ivals), batches_overlapping_previous=overlap,
                 grow_events=st1["grow_events"] - st0["grow_events"],
                 worker_ms={k: round(st1[k] - st0[k], 2) for k in ("grow_ms", "pack_ms", "enqueue_ms", "finish_ms")})
