@@ -1,7 +1,10 @@
 // Quadratic forms of the one-species compaction groups on the tensor cores,
 // 3xBF16 (Eq. 1, Eq. 2 restricted to one species block, Sec. V-B): P = D
 // [beta | Sigma] for 128-atom tiles, K = 144 (N = 8) or 112 (N = 7), with the
-// fused epilogue E, V, sigma and g = (2/||B||)(beta d - E d).
+// fused epilogue E, V, sigma and g = (2/||B||)(beta d - E d).  The g rows
+// are stored tile by tile ([K/8 column blocks][128 rows][8] per tile), so the
+// epilogue's stores are contiguous across a warp; the force kernel reads
+// them in that layout.
 //
 // The tile's A operand -- the BF16 hi and lo parts of its 128 descriptor
 // rows -- is loaded by TMA once and stays in shared memory for the whole
@@ -71,7 +74,7 @@ struct Q1Maps {
 struct Q1Args {
     const GroupTab *gtab;
     const int32_t *atom_of_row1;
-    float *G1;                // g rows of the one-species region [row][K]
+    float *G1;                // g rows of the one-species region, tile by tile (g1_tiled_offset)
     const float *norm;
     float *energy, *variance, *sigma;
     int var_factored[kGroups];
@@ -287,7 +290,9 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
             const bool valid = row < ti.rend;
             const int atom = valid ? __ldg(a.atom_of_row1 + row) : 0;
             const float nrm = valid ? __ldg(a.norm + atom) : 0.f;
-            float *grow = a.G1 + (size_t)(valid ? row : 0) * K;
+            // this row's g, tile by tile (g1_tiled_offset): a warp's stores of a
+            // column block cover 1 KB contiguously
+            float *grow = a.G1 + g1_tiled_offset(t, rloc, 0, K);
             const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
             const bool fact = a.var_factored[ti.g] != 0;
             // its accumulator
@@ -345,7 +350,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
                 if (valid) {
 #pragma unroll
                     for (int q = 0; q < 8; q += 4)
-                        *reinterpret_cast<float4 *>(grow + c + q) =
+                        *reinterpret_cast<float4 *>(grow + (c >> 3) * (kQM * 8) + q) =
                             make_float4(s2 * (pv[q] - E * dv[q]), s2 * (pv[q + 1] - E * dv[q + 1]),
                                         s2 * (pv[q + 2] - E * dv[q + 2]), s2 * (pv[q + 3] - E * dv[q + 3]));
                 }
