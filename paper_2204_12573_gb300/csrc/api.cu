@@ -168,7 +168,7 @@ int ensure_workspace(flr_ctx *ctx, int n)
         if (s == FLR_OK) s = dev_alloc(&ctx->Dhi[r], N * D.kp64[r], "workspace Dhi");
         if (s == FLR_OK) s = dev_alloc(&ctx->Dlo[r], N * D.kp64[r], "workspace Dlo");
         if (s == FLR_OK) s = dev_alloc(&ctx->P[r], N * 2 * D.K[r], "workspace P");
-        if (s == FLR_OK) s = dev_alloc(&ctx->G[r], (N + (r == 1 ? kG1PadRows : 0)) * D.K[r], "workspace G");
+        if (s == FLR_OK) s = dev_alloc(&ctx->G[r], N * D.K[r], "workspace G");
     }
     if (s == FLR_OK) s = dev_alloc(&ctx->Facc, N * 3, "workspace forces");
     if (s == FLR_OK) s = dev_alloc(&ctx->vir_atom, N * 9, "workspace virial");
@@ -255,10 +255,8 @@ int status_to_code(int st)
 // the weighted energy with unit weights are bitwise the forward forces).
 int launch_qform(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStream_t st)
 {
-    ctx->g1_tiled = 0;
     if (ctx->p.precision == FLR_PREC_FP32) return launch_qform_simt(ctx, nl, out, st);
     if (ctx->p.precision == FLR_PREC_BF16X3 && ctx->p.compaction) {
-        ctx->g1_tiled = 1;   // k_qform1 writes the one-species g rows tile by tile
         // two-species tiles on the general kernel, one-species tiles on the
         // kernel with the resident A tile.  With the overlap option the second
         // starts as a programmatic dependent of the first, on the SMs its few

@@ -45,7 +45,6 @@ struct ForceSmem {
     FW wp[kWarpsForce];
     float vir[kWarpsForce][9];
     int2 goff[goff_count<N>()];
-    G1Tiles g1;
 };
 
 // The atoms a force launch takes: a.n by index, or order[0 .. m) with m on the device.
@@ -62,8 +61,7 @@ __device__ __forceinline__ int force_count(const ForceArgs &a)
 // FW = ForceWarp<N> takes atoms of any class; FW = ForceWarp1<N> only atoms
 // of the one-species classes (their smaller per-warp state lets more warps
 // share an SM).
-// G1T: the one-species g rows are stored tile by tile (g1_tiled_offset).
-template <int N, class FW, int MINB, bool G1T>
+template <int N, class FW, int MINB>
 __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
 {
     __shared__ __align__(16) ForceSmem<FW, N> sm;
@@ -75,7 +73,6 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
     init_warp(fw, lane);
     const bool want_vatom = a.vir_atom != nullptr;
     init_goff<N>(a, sm.goff, threadIdx.x, blockDim.x);
-    if (G1T && threadIdx.x == 0) init_g1_tiles(a, sm.g1);
     __syncthreads();
     int nq = 0;        // queued pairs
     int seq = 0;       // atoms given a w slot so far by this warp
@@ -92,7 +89,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
     int p = wc.pos();
     int i = p < n_take ? (a.order ? __ldg(a.order + p) : p) : i_end;
     AtomPre cur = preload(a, i, i_end, lane);
-    rows_async<N, FW::kOne, G1T>(a, sm.g1, cur, i, i_end, fw.gr, fw.A, lane);
+    rows_async<N, FW::kOne>(a, cur, i, i_end, fw.gr, fw.A, lane);
     int p2 = n_take, i2 = i_end;
     AtomPre nxt;
     for (; p < n_take; p = p2, i = i2, cur = nxt, wc.advance(lane)) {
@@ -108,10 +105,10 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
                 if (a.sigma) a.sigma[i] = 0.f;
             }
             if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
-            rows_async<N, FW::kOne, G1T>(a, sm.g1, nxt, i2, i_end, fw.gr, fw.A, lane);
+            rows_async<N, FW::kOne>(a, nxt, i2, i_end, fw.gr, fw.A, lane);
             continue;
         }
-        force_atom<N, FW, G1T>(a, fw, sm.goff, sm.g1, lane, cur, i, nxt, i2, i_end, nq, seq, vir, want_vatom);
+        force_atom<N, FW>(a, fw, sm.goff, lane, cur, i, nxt, i2, i_end, nq, seq, vir, want_vatom);
     }  // atoms
     drain<N, FW>(fw, lane, nq, true, a.rcut, a.Facc, a.status, vir, want_vatom);
     if (want_vatom)
@@ -373,7 +370,7 @@ int launch_force_n(flr_ctx *ctx, const flr_nbrlist *nl, ForceArgs a, int n, cuda
     a0.n_dev[2] = a0.n_dev[3] = nullptr;
     a0.sched = ctx->sched + 1;
     a0.vir_base = 0;
-    const int grid0 = persistent_grid(k_force<N, ForceWarp<N>, kForceBlocks, false>, kWarpsForce * 32, ctx->num_sms, work);
+    const int grid0 = persistent_grid(k_force<N, ForceWarp<N>, kForceBlocks>, kWarpsForce * 32, ctx->num_sms, work);
     a1.order = nl->atom_of_row + nl->n_cap;
     a1.n_dev[0] = cnt + 1;
     a1.n_dev[1] = cnt + 2;
@@ -381,17 +378,13 @@ int launch_force_n(flr_ctx *ctx, const flr_nbrlist *nl, ForceArgs a, int n, cuda
     a1.n_dev[3] = cnt + 5;
     a1.sched = ctx->sched + 3;
     a1.vir_base = grid0;
-    // both forms have the same shared memory and registers, so the same grid
-    const int grid1 = persistent_grid(k_force<N, ForceWarp1<N>, kForce1Blocks, false>, kWarpsForce * 32, ctx->num_sms, work);
+    const int grid1 = persistent_grid(k_force<N, ForceWarp1<N>, kForce1Blocks>, kWarpsForce * 32, ctx->num_sms, work);
     if (grid0 + grid1 > kMaxPartials) {
         set_error("force launch: too many blocks for the virial partials");
         return FLR_EINVAL;
     }
-    k_force<N, ForceWarp<N>, kForceBlocks, false><<<grid0, kWarpsForce * 32, 0, st>>>(a0);
-    if (ctx->g1_tiled)
-        k_force<N, ForceWarp1<N>, kForce1Blocks, true><<<grid1, kWarpsForce * 32, 0, st>>>(a1);
-    else
-        k_force<N, ForceWarp1<N>, kForce1Blocks, false><<<grid1, kWarpsForce * 32, 0, st>>>(a1);
+    k_force<N, ForceWarp<N>, kForceBlocks><<<grid0, kWarpsForce * 32, 0, st>>>(a0);
+    k_force<N, ForceWarp1<N>, kForce1Blocks><<<grid1, kWarpsForce * 32, 0, st>>>(a1);
     k_zero_isolated<<<(n + 255) / 256, 256, 0, st>>>(nl->group, n, a.energy, a.variance, a.sigma, a.vir_atom);
     ctx->n_part = grid0 + grid1;
     count_launch(ctx, 3);
@@ -417,7 +410,6 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     }
     a.A = ctx->A;
     a.norm = ctx->norm;
-    a.gtab = nl->gtab;
     a.energy = out->energy;
     a.variance = out->variance;
     a.sigma = out->sigma;

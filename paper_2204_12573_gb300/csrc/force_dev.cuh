@@ -54,26 +54,7 @@ struct ForceArgs {
     const int32_t *order;      // atoms taken as order[0 .. m) (nullptr: 0 .. n-1 by index), with
     const int *n_dev[4];       // m = the sum of the counts these point to (capped at n)
     int vir_base;              // first row of this launch's block partials in vir_part
-    const GroupTab *gtab;      // group offsets and counts (tiled g rows)
 };
-
-// Where the tiled one-species g rows of each group start: first tile index
-// (OneTile numbering) and first compaction row, per group; filled once per CTA.
-struct G1Tiles {
-    int tile0[kGroups];
-    int row0[kGroups];
-};
-
-__device__ __forceinline__ void init_g1_tiles(const ForceArgs &a, G1Tiles &gt)
-{
-    int pre[5];
-    one_species_tiles(*a.gtab, pre);
-#pragma unroll
-    for (int g = 0; g < kGroups; ++g) {
-        gt.row0[g] = a.gtab->off[g];
-        gt.tile0[g] = group_full(g) ? 0 : pre[g < 3 ? g - 1 : g - 2];
-    }
-}
 
 // Dense G~ layout for a class of CG channels: lane half h owns channels
 // [h * gd_half(CG), ...), rows b are gd_row(CG) floats apart (a multiple of
@@ -384,9 +365,9 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 // Start copying atom i's g row (raw, compact order) and the A rows of its
 // class's channels into the warp's shared buffers (cp.async; lane t % 32
 // copies chunk t).  The buffers must no longer be in use.
-template <int N, bool ONE = false, bool G1T = false>
-__device__ __forceinline__ void rows_async(const ForceArgs &a, const G1Tiles &gt, const AtomPre &p, int i, int i_end,
-                                           float *gr, float *sA, int lane)
+template <int N, bool ONE = false>
+__device__ __forceinline__ void rows_async(const ForceArgs &a, const AtomPre &p, int i, int i_end, float *gr, float *sA,
+                                           int lane)
 {
     constexpr int C = 2 * N;
     if (i >= i_end || p.g < 0 || !(p.nrm > 0.f)) return;
@@ -394,15 +375,8 @@ __device__ __forceinline__ void rows_async(const ForceArgs &a, const G1Tiles &gt
     const int K = a.K[reg];
     const int Cg = cls == 0 ? C : N;
     const int choff = cls == 0 ? 0 : (cls - 1) * N;
-    if constexpr (G1T && ONE) {
-        // 16-byte piece t is half (t & 1) of the row's 8-column block t / 2 (g1_tiled_offset)
-        const int r = p.row - gt.row0[p.g];
-        const float *g = a.G[1] + g1_tiled_offset(gt.tile0[p.g] + (r >> 7), r & 127, 0, K);
-        for (int t = lane; 4 * t < K; t += 32) cp_async16(gr + 4 * t, g + (t >> 1) * (128 * 8) + 4 * (t & 1));
-    } else {
-        const float *g = a.G[reg] + (size_t)p.row * K;
-        for (int t = lane; 4 * t < K; t += 32) cp_async16(gr + 4 * t, g + 4 * t);
-    }
+    const float *g = a.G[reg] + (size_t)p.row * K;
+    for (int t = lane; 4 * t < K; t += 32) cp_async16(gr + 4 * t, g + 4 * t);
     const float *Ag = a.A + (size_t)i * (C * 16);
     for (int k = lane; k < Cg * 4; k += 32) {
         const int ch = choff + (k >> 2);
@@ -416,8 +390,8 @@ __device__ __forceinline__ void rows_async(const ForceArgs &a, const G1Tiles &gt
 // atom's g row, form w = G~ A, start copying the next atom's rows (nxt, i2;
 // nothing when i2 >= i_end), then queue the atom's pairs and evaluate every
 // full batch.
-template <int N, class FW, bool G1T>
-__device__ __forceinline__ void force_atom(const ForceArgs &a, FW &fw, const int2 *goff_all, const G1Tiles &gt, int lane,
+template <int N, class FW>
+__device__ __forceinline__ void force_atom(const ForceArgs &a, FW &fw, const int2 *goff_all, int lane,
                                            const AtomPre &cur, int i, const AtomPre &nxt, int i2, int i_end,
                                            int &nq, int &seq, float vir[9], bool want_vatom)
 {
@@ -480,7 +454,7 @@ __device__ __forceinline__ void force_atom(const ForceArgs &a, FW &fw, const int
     }
     __syncwarp();
     // the g and A buffers are free: start copying the next atom's rows
-    rows_async<N, FW::kOne, G1T>(a, gt, nxt, i2, i_end, fw.gr, fw.A, lane);
+    rows_async<N, FW::kOne>(a, nxt, i2, i_end, fw.gr, fw.A, lane);
 
     // queue the atom's pairs inside r_cut (recorded by the descriptor kernel)
     const int np = cur.np;

@@ -509,7 +509,6 @@ int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.gtab = nl->gtab;
     a.atom_of_row1 = nl->atom_of_row + nl->n_cap;
     a.G1 = ctx->G[1];
-    ctx->g1_tiled = 0;   // row layout
     a.energy = out->energy;
     a.variance = out->variance;
     a.sigma = out->sigma;

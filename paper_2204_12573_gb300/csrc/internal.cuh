@@ -171,7 +171,6 @@ struct flr_ctx {
     int q1maps_n;              // workspace size they were encoded for
     int use_fused;             // FLR_OPT_FUSED_ONE_SPECIES
     int overlap;               // FLR_OPT_OVERLAP_TWO_SPECIES
-    int g1_tiled;              // the one-species g rows were last written tile by tile (g1_tiled_offset)
     TcMaps *maps;              // host copy of the current tensor maps
     int maps_n;                // workspace size the maps were encoded for
     int maps_prec;
@@ -310,16 +309,6 @@ inline int persistent_grid(K kernel, int threads, int num_sms, long long work_bl
     return (int)(g < 1 ? 1 : g);
 }
 constexpr int kMaxPartials = 8192;   // rows of the reduction partials buffers
-// g rows of the one-species region written by the 3xBF16 tile kernel are
-// stored tile by tile: tile t (OneTile numbering) holds its 128 rows as
-// [K / 8 column blocks][128 rows][8], so the epilogue's stores of a column
-// block (one row per lane) cover 1 KB contiguously.  Partial last tiles of
-// the four one-species groups take up to this many rows beyond the atom count.
-constexpr int kG1PadRows = 4 * 128;
-__host__ __device__ inline size_t g1_tiled_offset(int tile, int rloc, int col, int K)
-{
-    return (size_t)tile * 128 * K + (size_t)(col >> 3) * (128 * 8) + (size_t)rloc * 8 + (col & 7);
-}
 
 // Dynamic work distribution for the per-atom kernels: a warp takes CH
 // consecutive positions of a work sequence at a time from a global counter

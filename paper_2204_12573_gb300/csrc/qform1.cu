@@ -1,10 +1,9 @@
 // Quadratic forms of the one-species compaction groups on the tensor cores,
 // 3xBF16 (Eq. 1, Eq. 2 restricted to one species block, Sec. V-B): P = D
 // [beta | Sigma] for 128-atom tiles, K = 144 (N = 8) or 112 (N = 7), with the
-// fused epilogue E, V, sigma and g = (2/||B||)(beta d - E d).  The g rows
-// are stored tile by tile ([K/8 column blocks][128 rows][8] per tile), so the
-// epilogue's stores are contiguous across a warp; the force kernel reads
-// them in that layout.
+// fused epilogue E, V, sigma and g = (2/||B||)(beta d - E d).  A full tile's
+// g rows are staged in the freed A buffer and stored by TMA, one box per
+// 8-column block, so the epilogue warps issue no scattered row stores.
 //
 // The tile's A operand -- the BF16 hi and lo parts of its 128 descriptor
 // rows -- is loaded by TMA once and stays in shared memory for the whole
@@ -58,9 +57,11 @@ struct QDims {
     static constexpr int OFF_B = 2 * A_BUF;             // two A buffers, then the ring
     static constexpr int OFF_X = OFF_B + kQStages * STAGE;
     static constexpr int OFF_BAR = OFF_X + 2 * kQSubs * kQM * 16;
-    static constexpr int N_BARS = 2 * kQStages + 4 + 4;   // full, empty, afull[2], aempty[2], tfull, tempty, drain, evx
+    // full, empty, afull[2], aempty[2], tfull, tempty, drain, evx, g staging (read, written)
+    static constexpr int N_BARS = 2 * kQStages + 4 + 4 + 2;
     static constexpr int BYTES = OFF_BAR + N_BARS * 8 + 16;
     static constexpr int PARK = 2 * K;
+    static constexpr int NCH = (K + 8 * kQSubs - 1) / (8 * kQSubs);   // 8-column chunks per epilogue thread
     static_assert(STAGE % 1024 == 0 && B_HALF % 256 == 0, "layout alignment");
     static_assert(PARK + K <= 512, "accumulator and park must fit the tensor memory");
 };
@@ -69,12 +70,13 @@ struct Q1Maps {
     CUtensorMap a_full[2];                // BF16 hi / lo descriptor rows, 64 x 128 boxes, 128-byte swizzle
     CUtensorMap a_step[2];                // 16 x 128 boxes, 32-byte swizzle
     CUtensorMap b_step[kGroups][2];       // [beta; Sigma] rows, 16 x K boxes, 32-byte swizzle
+    CUtensorMap g_rows;                   // FP32 g rows [row][K], 8 x 128 boxes, no swizzle (stores)
 };
 
 struct Q1Args {
     const GroupTab *gtab;
     const int32_t *atom_of_row1;
-    float *G1;                // g rows of the one-species region, tile by tile (g1_tiled_offset)
+    float *G1;                // g rows of the one-species region [row][K]
     const float *norm;
     float *energy, *variance, *sigma;
     int var_factored[kGroups];
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
     const uint32_t afull0 = smem_u32(bars + 2 * kQStages), aempty0 = smem_u32(bars + 2 * kQStages + 2);
     const uint32_t tfull = smem_u32(bars + 2 * kQStages + 4), tempty = smem_u32(bars + 2 * kQStages + 5);
     const uint32_t drain = smem_u32(bars + 2 * kQStages + 6), evx = smem_u32(bars + 2 * kQStages + 7);
+    const uint32_t gread = smem_u32(bars + 2 * kQStages + 8), gwritten = smem_u32(bars + 2 * kQStages + 9);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -141,6 +144,8 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
         mbar_init(tempty, kQEpi);
         mbar_init(drain, 1);
         mbar_init(evx, kQEpi);
+        mbar_init(gread, kQEpi);
+        mbar_init(gwritten, kQEpi);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -273,6 +278,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
         const int sub = (warp - 2) >> 2;
         const uint32_t tbase = tmem + ((uint32_t)(qw * 32) << 16);
         const int rloc = qw * 32 + lane;
+        int nfull = 0;   // full tiles staged so far (the staging barriers' phase)
         bool alive = true;
         for (int k = 0; alive; ++k) {
             const int buf = k & 1;
@@ -290,9 +296,6 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
             const bool valid = row < ti.rend;
             const int atom = valid ? __ldg(a.atom_of_row1 + row) : 0;
             const float nrm = valid ? __ldg(a.norm + atom) : 0.f;
-            // this row's g, tile by tile (g1_tiled_offset): a warp's stores of a
-            // column block cover 1 KB contiguously
-            float *grow = a.G1 + g1_tiled_offset(t, rloc, 0, K);
             const float s2 = nrm > 0.f ? 2.f / nrm : 0.f;
             const bool fact = a.var_factored[ti.g] != 0;
             // its accumulator
@@ -342,18 +345,62 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
                 Va += p.z;
             }
             tmem_wait_st();
-#pragma unroll 1
-            for (int c = 8 * sub; c < K; c += 8 * kQSubs) {
-                float dv[8], pv[8];
-                tmem_ld8(tbase + (uint32_t)(D::PARK + c), pv);
-                AT::read_d8(shi, slo, rloc, c, dv);
-                if (valid) {
+            // g = (2/||B||)(beta d - E d).  A full tile's g goes out by TMA: once every
+            // epilogue warp has read the A buffer, it becomes the tile's staging area
+            // [K/8 column blocks][128 rows][8], and one thread stores each column
+            // block as a box of the row-major g array.  A partial tile (the last of a
+            // group) is stored by its threads, valid rows only.
+            const bool full_tile = ti.rend - ti.row0 >= kQM;   // the same for every epilogue warp
+            float gv[D::NCH][8];
 #pragma unroll
-                    for (int q = 0; q < 8; q += 4)
-                        *reinterpret_cast<float4 *>(grow + (c >> 3) * (kQM * 8) + q) =
-                            make_float4(s2 * (pv[q] - E * dv[q]), s2 * (pv[q + 1] - E * dv[q + 1]),
-                                        s2 * (pv[q + 2] - E * dv[q + 2]), s2 * (pv[q + 3] - E * dv[q + 3]));
+            for (int j = 0; j < D::NCH; ++j) {
+                const int c = 8 * sub + 8 * kQSubs * j;
+                if (c < K) {
+                    float dv[8], pv[8];
+                    tmem_ld8(tbase + (uint32_t)(D::PARK + c), pv);
+                    AT::read_d8(shi, slo, rloc, c, dv);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) gv[j][q] = s2 * (pv[q] - E * dv[q]);
+                    if (!full_tile && valid) {
+                        float *grow = a.G1 + (size_t)row * K + c;
+                        *reinterpret_cast<float4 *>(grow) = make_float4(gv[j][0], gv[j][1], gv[j][2], gv[j][3]);
+                        *reinterpret_cast<float4 *>(grow + 4) = make_float4(gv[j][4], gv[j][5], gv[j][6], gv[j][7]);
+                    }
                 }
+            }
+            if (full_tile) {
+                const uint32_t ph = (uint32_t)(nfull & 1);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(gread);
+                if (!q_warp_wait(gread, ph, lane, abort_flag, a.status)) {
+                    alive = false;
+                    break;
+                }
+                float *stg = reinterpret_cast<float *>(base + buf * D::A_BUF);
+#pragma unroll
+                for (int j = 0; j < D::NCH; ++j) {
+                    const int c = 8 * sub + 8 * kQSubs * j;
+                    if (c < K) {
+                        float4 *dst = reinterpret_cast<float4 *>(stg + ((size_t)(c >> 3) * kQM + rloc) * 8);
+                        dst[0] = make_float4(gv[j][0], gv[j][1], gv[j][2], gv[j][3]);
+                        dst[1] = make_float4(gv[j][4], gv[j][5], gv[j][6], gv[j][7]);
+                    }
+                }
+                // the generic-proxy writes above are read by the TMA (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(gwritten);
+                if (!q_warp_wait(gwritten, ph, lane, abort_flag, a.status)) {
+                    alive = false;
+                    break;
+                }
+                if (warp == 2 && lane == 0) {
+                    for (int c8 = 0; c8 < K / 8; ++c8)
+                        tma_store_2d(&maps.g_rows, smem_u32(stg + (size_t)c8 * kQM * 8), 8 * c8, ti.row0);
+                    tma_store_commit();
+                    tma_store_wait_read();   // the buffer may be reloaded once the stores have read it
+                }
+                ++nfull;
             }
             // done with this A buffer
             fence_before();
@@ -370,6 +417,7 @@ __global__ void __launch_bounds__(kQThreads, 1) k_qform1(const __grid_constant__
             }
         }
     }
+    if (warp == 2 && lane == 0) tma_store_wait_all();   // the g stores have landed
     fence_before();
     __syncthreads();
     fence_after();
@@ -412,6 +460,8 @@ int ensure_q1_maps(flr_ctx *ctx)
         s = encode_tile_map(&m.a_full[part], rows, true, D.kp64[1], ctx->ws_n, 64, kQM, 128);
         if (s == FLR_OK) s = encode_tile_map(&m.a_step[part], rows, true, D.kp64[1], ctx->ws_n, 16, kQM, 32);
     }
+    // the g rows (row-major, K floats a row) for the epilogue's TMA stores
+    if (s == FLR_OK) s = encode_tile_map(&m.g_rows, ctx->G[1], false, K, ctx->ws_n, 8, kQM, 0);
     for (int g = 0; g < kGroups && s == FLR_OK; ++g) {
         if (group_full(g)) {
             m.b_step[g][0] = m.b_step[g][1] = CUtensorMap{};

@@ -559,7 +559,7 @@ int encode(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int b
 
 // A 2-D row-major tensor map (FP32 or BF16) with a box of box_cols x box_rows
 // and the given swizzle width (32, 64 or 128 bytes; box_cols x element size
-// must equal it).
+// must equal it), or none (0).
 int encode_tile_map(CUtensorMap *m, const void *ptr, bool bf16, int cols, int rows, int box_cols, int box_rows,
                     int swizzle_bytes)
 {
@@ -573,7 +573,8 @@ int encode_tile_map(CUtensorMap *m, const void *ptr, bool bf16, int cols, int ro
     cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
     cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    const CUtensorMapSwizzle sw = swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+    const CUtensorMapSwizzle sw = swizzle_bytes == 0    ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                  : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                   : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                         : CU_TENSOR_MAP_SWIZZLE_128B;
     CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
