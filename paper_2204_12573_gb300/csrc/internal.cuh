@@ -61,6 +61,7 @@ struct Plan {
     int R[3];           // stencil reach in bins
     float flo[3];       // lower fractional bound of the bin grid (0 along periodic dirs)
     float fspan[3];     // fractional span of the bin grid (1 along periodic dirs)
+    double bscale[3];   // nb / fspan in FP64 (bin coordinate = (frac - flo) * bscale)
     double cell[9];
     double inv[9];      // inverse of the cell matrix (frac = pos . inv)
     float invf[9];      // inv rounded to FP32 (the in-bin offsets used to prune the stencil)
