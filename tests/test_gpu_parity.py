@@ -172,6 +172,27 @@ def test_fused_and_separate_kernels_agree():
     assert (np.abs(a["variance"] - b["variance"]) <= 1e-4 * np.abs(b["variance"]) + 1e-5).all()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_virial_and_total_energy_match_oracle(precision):
+    """The FP64 totals against the oracle: the virial W_ab = -sum over pairs of
+    (r_ij)_a (dE_i/dr_ij)_b (the stress the model predicts, Sec. V-B) and the
+    total energy.  Each is a sum whose terms carry a relative error of at most
+    eps, so the bound is eps times the sum of the terms' absolute values:
+    eps = 1e-5 in FP32 (the per-atom energy bound), 1e-4 with the 3xBF16
+    quadratic forms.  The single-system path sums the pair terms directly; the
+    per-structure path of batches (compared with it in test_gpu_batch.py) sums
+    per-atom virials."""
+    s = _slabs(3)[1]
+    g, *_ = gpu_run(s, BETA, SIGMA, precision=precision)
+    o = oracle_run(s, BETA, SIGMA)
+    eps = 1e-5 if precision == "fp32" else 1e-4
+    abs_w = np.einsum("pa,pb->ab", np.abs(o["rij"]), np.abs(o["fpair"]))
+    w = g["totals"][1:10].reshape(3, 3)
+    assert np.abs(o["W"]).max() > 1e-3                       # a non-trivial virial
+    assert (np.abs(w - o["W"]) <= eps * abs_w + 1e-9).all()
+    assert abs(g["totals"][0] - o["E_tot"]) <= eps * np.abs(o["E"]).sum()
+
+
 def test_two_species_overlap_is_bitwise_serial():
     """The one-species quadratic-form kernel launched as a programmatic
     dependent of the two-species one (the default) and launched after it give
