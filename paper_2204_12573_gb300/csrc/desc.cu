@@ -11,7 +11,7 @@ namespace flr {
 namespace {
 
 template <int N>
-__global__ void __launch_bounds__(kWarpsDesc * 32, 4) k_desc(DescArgs a)
+__global__ void __launch_bounds__(kWarpsDesc * 32, 5) k_desc(DescArgs a)
 {
     constexpr int C = 2 * N;
     constexpr int NPF = C * (C + 1) / 2;          // channel pairs of the full descriptor
