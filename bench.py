@@ -573,81 +573,40 @@ def run_ours(args):
                 "per_unit": {"descriptor_flop_per_pair": DESC_PAIR, "force_flop_per_pair": FORCE_PAIR,
                              "pairs_per_atom": round(pairs_per_atom, 3)}}
 
-    # end to end through the public API with host buffers
+    # end to end through the C ABI with host buffers: flr_md_step_host, one
+    # call per step, uploads the step's positions and velocities from pinned
+    # host memory (x, y, z rows), steps on the device, downloads the new state
+    # and then reads back the step's energies, forces and sigma (asynchronous;
+    # the library overlaps one call's read-back with the next call's kernels
+    # and each chunk's upload with the previous download)
     e2e = None
     if not args.no_e2e:
         ff.set_precision("bf16x3")
         st = reset()
-        hpos = torch.empty_like(sysg.pos, device="cpu").pin_memory()
-        hvel = torch.empty_like(vel, device="cpu").pin_memory()
-        hpos.copy_(sysg.pos)
-        hvel.copy_(vel)
-        hout = {k: torch.empty_like(out[k], device="cpu").pin_memory() for k in ("energy", "forces", "sigma")}
-        # positions and velocities feed the next step and go through the host
-        # in order; a step's energies, forces and sigma are read back on a side
-        # stream from one of two output sets, overlapping the next step
-        outs = [out, F.make_outputs(n)]
-        side = torch.cuda.Stream()
-        ev_step = [torch.cuda.Event(), torch.cuda.Event()]
-        ev_read = [torch.cuda.Event(), torch.cuda.Event()]
-        # the round trip of positions and velocities (down after a step, up as
-        # the next step's inputs) goes in chunks on two copy streams, so each
-        # chunk's upload starts once its download has landed and the two
-        # directions overlap; the bytes per step are unchanged
-        down, up = torch.cuda.Stream(), torch.cuda.Stream()
-        n_chunks = 8
-        bounds = [(n * c) // n_chunks for c in range(n_chunks + 1)]
-        ev_down = [torch.cuda.Event() for _ in range(2 * n_chunks)]
-        F.md_step(ff, st, nl, 1, out)
+        host = F.HostState(sysg.pos.cpu(), vel.cpu(), results=("energy", "forces", "sigma"))
+        for _ in range(2):   # the first call creates the copy streams and staging rows
+            F.md_step_host(ff, st, nl, 1, out, host, stream)
         ff.sync()
         barrier()
         t0 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sysg.pos.copy_(hpos, non_blocking=True)       # the first step's inputs
-        vel.copy_(hvel, non_blocking=True)
-        for s_ in range(args.steps):
-            o = outs[s_ & 1]
-            stream.wait_stream(up)                     # this step's inputs are on the device
-            if s_ >= 2:
-                stream.wait_event(ev_read[s_ & 1])   # the read-back of this output set is done
-            F.md_step(ff, st, nl, 1, o)
-            ev_step[s_ & 1].record(stream)
-            down.wait_event(ev_step[s_ & 1])
-            last = s_ == args.steps - 1
-            for c in range(n_chunks):
-                a_, b_ = bounds[c], bounds[c + 1]
-                for t, (dev, host) in enumerate(((sysg.pos, hpos), (vel, hvel))):
-                    with torch.cuda.stream(down):
-                        host[a_:b_].copy_(dev[a_:b_], non_blocking=True)
-                        ev_down[2 * c + t].record(down)
-                    if not last:
-                        up.wait_event(ev_down[2 * c + t])
-                        with torch.cuda.stream(up):
-                            dev[a_:b_].copy_(host[a_:b_], non_blocking=True)
-            # the step's E, F and sigma follow the position/velocity download in
-            # the same direction, so they do not slow the round trip the next
-            # step waits for; they overlap the next step's kernels instead
-            side.wait_event(ev_down[2 * n_chunks - 1])
-            with torch.cuda.stream(side):
-                for k in hout:
-                    hout[k].copy_(o[k], non_blocking=True)
-            ev_read[s_ & 1].record(side)
-        stream.wait_stream(side)
-        stream.wait_stream(down)
-        stream.wait_stream(up)
+        for _ in range(args.steps):
+            F.md_step_host(ff, st, nl, 1, out, host, stream)
+        F.host_join(ff, stream)
         e1.record(stream)
+        ff.sync()
         barrier()
         wall = time.perf_counter() - t0
         ms_e2e = max(e0.elapsed_time(e1), wall * 1e3)
-        bi = 2 * n * 16
-        bo = 2 * n * 16 + sum(hout[k].numel() * 4 for k in hout)
+        bi = 2 * n * 12
+        bo = 2 * n * 12 + sum(v.numel() * v.element_size() for v in host.results.values())
         ms_e2e = max_over_ranks(ms_e2e, dist)
         e2e = {"value": job_throughput(world, n, args.steps, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-               "note": "per step: H2D pos+vel (pinned), md_step, D2H pos+vel, and D2H energy, forces, sigma; "
-                       "the pos/vel round trip in 8 chunks on two copy streams, E/F/sigma read back after it on a "
-                       "side stream overlapping the next step"}
+               "note": "per step one flr_md_step_host call: H2D pos+vel (pinned x, y, z rows), md step, D2H pos+vel, "
+                       "then D2H energy, forces, sigma; the state round trip in 8 chunks on two copy streams, the "
+                       "read-back overlapping the next call's kernels"}
 
     serving = None
     if args.serving_seconds > 0:

@@ -338,7 +338,51 @@ int flr_energy_forces_uncertainty(flr_ctx *ctx, const flr_system *sys, const flr
 int flr_md_step(flr_ctx *ctx, flr_md_state *st, flr_nbrlist *nl, int32_t n_steps,
                 flr_outputs *out, flr_stream_t stream);
 
-/* Synchronize `stream` and report (and clear) device-side errors. */
+/* Host copies of the MD state and of a step's results for flr_md_step_host.
+ * All are HOST arrays (page-locked memory gives full copy speed; pageable
+ * memory works but the copies then stage through the driver).  pos and vel
+ * are float[n][3] (x, y, z), read before each step and overwritten with the
+ * state after it.  energy (float[n]), forces (float[n][3]), variance
+ * (float[n]), sigma (float[n]) and totals (double[FLR_NTOTALS]) may each be
+ * NULL; those given receive the results of the call's last step.  The
+ * caller owns every array. */
+typedef struct {
+    float *pos;
+    float *vel;
+    float *energy;
+    float *forces;
+    float *variance;
+    float *sigma;
+    double *totals;
+} flr_host_state;
+
+/* flr_md_step with the MD state kept in host memory (the production loop of
+ * Sec. VI-A with the integrator's positions and velocities owned by the
+ * caller).  Each of n_steps copies host->pos and host->vel to the device
+ * (st->pos and st->vel, device float[n][4], are the working copies: their
+ * x, y, z are overwritten and w is set to 0), runs one flr_md_step and
+ * copies the new positions and velocities back; after the last step the
+ * requested results follow.  st and out are as for flr_md_step (forces
+ * must stay the same device buffer from call to call while forces_valid is
+ * set).
+ * Asynchronous: the copies run on two copy streams of the context, in eight
+ * chunks, each chunk's upload for the next step starting once its download
+ * has landed, and the results read-back of one call overlaps the next
+ * call's kernels (a call's quadratic forms wait for the previous call's
+ * read-back before they overwrite the outputs).  The host arrays may be
+ * read or changed only after flr_sync or after `stream` has passed
+ * flr_host_join.  FLR_EINVAL for NULL pos or vel or the conditions of
+ * flr_md_step. */
+int flr_md_step_host(flr_ctx *ctx, flr_md_state *st, flr_nbrlist *nl, int32_t n_steps, flr_outputs *out,
+                     const flr_host_state *host, flr_stream_t stream);
+
+/* Make `stream` wait (on the device, without blocking the host) until every
+ * copy that flr_md_step_host has enqueued on this context has landed. */
+int flr_host_join(flr_ctx *ctx, flr_stream_t stream);
+
+/* Synchronize `stream` (and the context's host-copy streams, if
+ * flr_md_step_host has created them) and report (and clear) device-side
+ * errors. */
 int flr_sync(flr_ctx *ctx, flr_stream_t stream);
 
 /* Number of kernels the library launched on this context so far, as counted

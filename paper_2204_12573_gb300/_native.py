@@ -46,6 +46,7 @@ EXPORTED = [
     "flr_build_neighbors_batch", "flr_energy_forces_uncertainty_batch", "flr_energy_backward",
     "flr_bytes_per_atom", "flr_server_create", "flr_server_submit", "flr_server_poll", "flr_server_stats_read",
     "flr_server_destroy", "flr_set_variance_mode", "flr_map_sgp", "flr_fp32_fma_peak", "flr_set_option",
+    "flr_md_step_host", "flr_host_join",
 ]
 
 KERNEL_CLASSES = ["descriptor", "qform", "force", "finalize", "drift", "rebuild", "fused"]
@@ -84,6 +85,12 @@ class MDState(ctypes.Structure):
                 ("tau", ctypes.c_double), ("xi", ctypes.c_double), ("eta", ctypes.c_double),
                 ("sigma_stop", ctypes.c_double), ("halted", ctypes.c_int32), ("cn_species", ctypes.c_int32),
                 ("cn_cutoff", ctypes.c_double)]
+
+
+class HostState(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("energy", ctypes.c_void_p),
+                ("forces", ctypes.c_void_p), ("variance", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("totals", ctypes.c_void_p)]
 
 
 class ServerParams(ctypes.Structure):
@@ -152,6 +159,9 @@ def lib():
             "flr_compute_descriptors": (ctypes.c_int, [P, ctypes.POINTER(System), P, P, P, P]),
             "flr_energy_forces_uncertainty": (ctypes.c_int, [P, ctypes.POINTER(System), P, ctypes.POINTER(Outputs), P]),
             "flr_md_step": (ctypes.c_int, [P, ctypes.POINTER(MDState), P, ctypes.c_int32, ctypes.POINTER(Outputs), P]),
+            "flr_md_step_host": (ctypes.c_int, [P, ctypes.POINTER(MDState), P, ctypes.c_int32,
+                                                ctypes.POINTER(Outputs), ctypes.POINTER(HostState), P]),
+            "flr_host_join": (ctypes.c_int, [P, P]),
             "flr_sync": (ctypes.c_int, [P, P]),
             "flr_launch_count": (ctypes.c_int64, [P]),
             "flr_profile_enable": (ctypes.c_int, [P, ctypes.c_int32]),

@@ -271,6 +271,15 @@ int launch_qform(flr_ctx *ctx, const flr_nbrlist *nl, flr_outputs *out, cudaStre
     return launch_qform_tc(ctx, nl, out, st);
 }
 
+// Outputs are written from the quadratic forms on: with a host read-back of
+// the previous results still in flight (flr_md_step_host), wait for it here,
+// after the descriptor kernel has already run beside it.
+int gate_outputs(flr_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx->out_gate) return FLR_OK;
+    return cuda_fail(cudaStreamWaitEvent(st, ctx->out_gate, 0), "wait for the host read-back");
+}
+
 int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *species, int n,
              flr_outputs *out, const KickArgs &kick, cudaStream_t st, double *seg_totals = nullptr)
 {
@@ -289,6 +298,7 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
         prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
         s = launch_desc(ctx, nl, pos, species, n, st, nl->atom_of_row, cnt + 0, cnt + 3);
         prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
+        if (s == FLR_OK) s = gate_outputs(ctx, st);
         prof_begin(ctx, FLR_KERNEL_QFORM, st);
         if (s == FLR_OK) s = launch_qform_tc(ctx, nl, out, st, true);
         prof_end(ctx, FLR_KERNEL_QFORM, st);
@@ -310,6 +320,7 @@ int evaluate(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const int *
         prof_begin(ctx, FLR_KERNEL_DESCRIPTOR, st);
         s = launch_desc(ctx, nl, pos, species, n, st, nullptr, nullptr, nullptr, skip32);
         prof_end(ctx, FLR_KERNEL_DESCRIPTOR, st);
+        if (s == FLR_OK) s = gate_outputs(ctx, st);
         if (s != FLR_OK) return s;
         prof_begin(ctx, FLR_KERNEL_QFORM, st);
         if (ctx->var_mode == FLR_VAR_AUTO) {
@@ -424,6 +435,10 @@ void bytes_per_atom_parts(const flr_ctx *ctx, int64_t *workspace, int64_t *slot)
 
 using namespace flr;
 
+namespace {
+void free_hostio(flr_ctx *c);   // host-state MD buffers (below)
+}
+
 extern "C" {
 
 const char *flr_last_error(void) { return g_err.c_str(); }
@@ -524,6 +539,7 @@ int flr_destroy(flr_ctx *c)
     }
     free_fused_maps(c);
     free_q1_maps(c);
+    free_hostio(c);
     cudaFree(c->tab_full);
     cudaFree(c->tab_single);
     cudaFree(c->status);
@@ -1012,8 +1028,146 @@ int flr_energy_forces_uncertainty(flr_ctx *c, const flr_system *sys, const flr_n
                     reinterpret_cast<cudaStream_t>(stream));
 }
 
-int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_outputs *out,
-                flr_stream_t stream)
+}  // extern "C"
+
+namespace {
+
+// Copy streams, events and staging rows for n atoms (created on first use,
+// the rows grown when too small; cudaFree waits for the copies in flight).
+int ensure_hostio(flr_ctx *c, int n)
+{
+    if (!c->hio) {
+        HostIO *io = new HostIO();
+        std::memset(static_cast<void *>(io), 0, sizeof(HostIO));
+        io->last_n = -1;
+        c->hio = io;
+        cudaError_t e = cudaStreamCreateWithFlags(&io->up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&io->down, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_up, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_packed, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_read, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_join, cudaEventDisableTiming);
+        for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&io->ev_down[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "host-state streams and events");
+    }
+    HostIO *io = c->hio;
+    if (io->cap < n) {
+        cudaFree(io->stage);
+        io->stage = nullptr;
+        io->cap = 0;
+        io->last_n = -1;   // the copies of earlier calls have landed
+        const cudaError_t e = cudaMalloc(&io->stage, sizeof(float) * 6 * (size_t)n);
+        if (e != cudaSuccess) return cuda_fail(e, "host-state staging rows");
+        io->cap = n;
+    }
+    return FLR_OK;
+}
+
+void free_hostio(flr_ctx *c)
+{
+    HostIO *io = c->hio;
+    if (!io) return;
+    if (io->up) cudaStreamSynchronize(io->up);
+    if (io->down) cudaStreamSynchronize(io->down);
+    cudaFree(io->stage);
+    if (io->up) cudaStreamDestroy(io->up);
+    if (io->down) cudaStreamDestroy(io->down);
+    cudaEvent_t evs[4] = {io->ev_up, io->ev_packed, io->ev_read, io->ev_join};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    for (int k = 0; k < kHostChunks; ++k)
+        if (io->ev_down[k]) cudaEventDestroy(io->ev_down[k]);
+    delete io;
+    c->hio = nullptr;
+}
+
+// Atoms [lo, hi) of chunk k of n.
+inline void chunk_range(int n, int k, size_t &lo, size_t &hi)
+{
+    lo = (size_t)n * k / kHostChunks;
+    hi = (size_t)n * (k + 1) / kHostChunks;
+}
+
+// Host state -> staging rows (chunk k after the previous download of the
+// same chunk has reached the host) -> working copies on `st`.
+int host_upload(flr_ctx *c, const flr_host_state *h, flr_md_state *md, cudaStream_t st)
+{
+    HostIO *io = c->hio;
+    const int n = md->n_atoms;
+    float *p3 = io->stage, *v3 = io->stage + 3 * (size_t)io->cap;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
+        size_t lo, hi;
+        chunk_range(n, k, lo, hi);
+        if (io->last_n >= 0)
+            e = cudaStreamWaitEvent(io->up, io->ev_down[io->last_n == n ? k : kHostChunks - 1], 0);
+        if (e == cudaSuccess && hi > lo)
+            e = cudaMemcpyAsync(p3 + 3 * lo, h->pos + 3 * lo, 12 * (hi - lo), cudaMemcpyHostToDevice, io->up);
+        if (e == cudaSuccess && hi > lo)
+            e = cudaMemcpyAsync(v3 + 3 * lo, h->vel + 3 * lo, 12 * (hi - lo), cudaMemcpyHostToDevice, io->up);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(io->ev_up, io->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, io->ev_up, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "upload host state");
+    return launch_state_unpack(c, p3, v3, reinterpret_cast<float4 *>(md->pos), reinterpret_cast<float4 *>(md->vel), n,
+                               st);
+}
+
+// Working copies -> staging rows on `st` -> host state, in chunks on the
+// download stream.
+int host_download(flr_ctx *c, const flr_host_state *h, flr_md_state *md, cudaStream_t st)
+{
+    HostIO *io = c->hio;
+    const int n = md->n_atoms;
+    float *p3 = io->stage, *v3 = io->stage + 3 * (size_t)io->cap;
+    int s = launch_state_pack(c, reinterpret_cast<const float4 *>(md->pos), reinterpret_cast<const float4 *>(md->vel),
+                              p3, v3, n, st);
+    if (s != FLR_OK) return s;
+    cudaError_t e = cudaEventRecord(io->ev_packed, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(io->down, io->ev_packed, 0);
+    for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
+        size_t lo, hi;
+        chunk_range(n, k, lo, hi);
+        if (hi > lo) e = cudaMemcpyAsync(h->pos + 3 * lo, p3 + 3 * lo, 12 * (hi - lo), cudaMemcpyDeviceToHost, io->down);
+        if (e == cudaSuccess && hi > lo)
+            e = cudaMemcpyAsync(h->vel + 3 * lo, v3 + 3 * lo, 12 * (hi - lo), cudaMemcpyDeviceToHost, io->down);
+        if (e == cudaSuccess) e = cudaEventRecord(io->ev_down[k], io->down);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "download host state");
+    io->last_n = n;
+    return FLR_OK;
+}
+
+// The requested results of the call's last step, on the download stream
+// after the state; the next call's outputs wait for ev_read.
+int host_results(flr_ctx *c, const flr_host_state *h, const flr_outputs &o, int n, cudaStream_t st)
+{
+    HostIO *io = c->hio;
+    cudaError_t e = cudaEventRecord(io->ev_packed, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(io->down, io->ev_packed, 0);
+    struct {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } cp[5] = {{h->energy, o.energy, 4 * (size_t)n},
+               {h->forces, o.forces, 12 * (size_t)n},
+               {h->variance, o.variance, 4 * (size_t)n},
+               {h->sigma, o.sigma, 4 * (size_t)n},
+               {h->totals, o.totals, sizeof(double) * FLR_NTOTALS}};
+    for (auto &x : cp)
+        if (e == cudaSuccess && x.dst && x.src && x.bytes)
+            e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDeviceToHost, io->down);
+    if (e == cudaSuccess) e = cudaEventRecord(io->ev_read, io->down);
+    if (e != cudaSuccess) return cuda_fail(e, "read back results");
+    c->out_gate = io->ev_read;   // stays set: later evaluations of this context wait for it
+    return FLR_OK;
+}
+
+// n_steps of velocity Verlet (flr_md_step); with h, every step's state goes
+// through the host arrays of h (flr_md_step_host).
+int md_run(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_outputs *out, flr_stream_t stream,
+           const flr_host_state *h)
 {
     if (!c || !md || !nl || !out || !out->forces || !out->energy || n_steps < 0) {
         set_error("flr_md_step: invalid argument");
@@ -1049,6 +1203,7 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int n = md->n_atoms;
     s = ensure_workspace(c, n);
+    if (s == FLR_OK && h) s = ensure_hostio(c, n);
     if (s != FLR_OK || n == 0) return s;
     const double ftm2v = 1.0 / 1.0364269e-4;   // (eV/A)/amu -> A/ps^2
     const double kB = 8.617333262e-5;           // eV/K
@@ -1075,6 +1230,7 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
     const double gkT = 3.0 * n * kB * md->temperature;          // g kB T, g = 3n degrees of freedom
     const double Q = gkT * md->tau * md->tau;                     // thermostat mass (eV ps^2)
     s = launch_clear_rebuild_counter(c, nl, st);
+    if (s == FLR_OK && h && n_steps > 0) s = host_upload(c, h, md, st);   // the first step's inputs
     if (s != FLR_OK) return s;
     if (!md->forces_valid) {
         KickArgs none;
@@ -1092,7 +1248,8 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
     }
     kick.enabled = 1;
     for (int k = 0; k < n_steps; ++k) {
-        if (nvt) s = launch_thermo_half(c, c->md_sc, nullptr, gkT, Q, md->dt, nullptr, st);
+        if (h && k > 0) s = host_upload(c, h, md, st);
+        if (s == FLR_OK && nvt) s = launch_thermo_half(c, c->md_sc, nullptr, gkT, Q, md->dt, nullptr, st);
         prof_begin(c, FLR_KERNEL_DRIFT, st);
         if (s == FLR_OK)
             s = launch_md_drift(c, nl, pos, kick.vel, o.forces, md->species, n, kick, (float)md->dt, disp2, st);
@@ -1118,13 +1275,14 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
                                            "uncertainty count");
             if (s == FLR_OK) s = cuda_fail(cudaStreamSynchronize(st), "uncertainty count");
             if (s != FLR_OK) return s;
-            if (cnt > 0) {
-                md->halted = 1;
-                break;
-            }
+            if (cnt > 0) md->halted = 1;
         }
+        if (h) s = host_download(c, h, md, st);
+        if (s != FLR_OK) return s;
+        if (md->halted) break;
     }
     s = launch_copy_rebuilds(c, nl, tot, st);
+    if (s == FLR_OK && h && n_steps > 0) s = host_results(c, h, o, n, st);
     if (s == FLR_OK && nvt) {
         double fin[2];
         s = cuda_fail(cudaMemcpyAsync(fin, c->md_sc, sizeof(fin), cudaMemcpyDeviceToHost, st), "thermostat state");
@@ -1137,11 +1295,47 @@ int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, 
     return s;
 }
 
+}  // namespace
+
+extern "C" {
+
+int flr_md_step(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_outputs *out,
+                flr_stream_t stream)
+{
+    return md_run(c, md, nl, n_steps, out, stream, nullptr);
+}
+
+int flr_md_step_host(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_outputs *out,
+                     const flr_host_state *host, flr_stream_t stream)
+{
+    if (!host || !host->pos || !host->vel) {
+        set_error("flr_md_step_host: host pos and vel are required");
+        return FLR_EINVAL;
+    }
+    return md_run(c, md, nl, n_steps, out, stream, host);
+}
+
+int flr_host_join(flr_ctx *c, flr_stream_t stream)
+{
+    if (!c) return FLR_EINVAL;
+    if (!c->hio || c->hio->last_n < 0) return FLR_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // every upload is followed on the compute stream by its unpack, which the
+    // caller's stream orders itself against; the down stream's work (state
+    // downloads and read-backs) is waited for here
+    cudaError_t e = cudaEventRecord(c->hio->ev_join, c->hio->down);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->hio->ev_join, 0);
+    return cuda_fail(e, "flr_host_join");
+}
+
 int flr_sync(flr_ctx *c, flr_stream_t stream)
 {
     if (!c) return FLR_EINVAL;
     cudaSetDevice(c->device);
     int s = cuda_fail(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)), "flr_sync");
+    if (s == FLR_OK && c->hio) s = cuda_fail(cudaStreamSynchronize(c->hio->up), "flr_sync (host uploads)");
+    if (s == FLR_OK && c->hio) s = cuda_fail(cudaStreamSynchronize(c->hio->down), "flr_sync (host downloads)");
     if (s != FLR_OK) return s;
     int st[4];
     s = cuda_fail(cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost), "flr_sync status");

@@ -177,6 +177,23 @@ struct flr_ctx {
     int maps_prec;
     // per-kernel event timing (flr_profile_*)
     struct ProfState *prof;
+    // host-state MD (flr_md_step_host): copy streams, events and staging rows
+    struct HostIO *hio;
+    cudaEvent_t out_gate;      // when set, evaluations wait for it before writing their outputs
+};
+
+// Copy streams, events and device staging rows of flr_md_step_host.
+constexpr int kHostChunks = 8;
+struct HostIO {
+    cudaStream_t up, down;
+    cudaEvent_t ev_up;                  // this step's inputs are in the staging rows (up)
+    cudaEvent_t ev_packed;              // the step's state is in the staging rows (compute stream)
+    cudaEvent_t ev_down[kHostChunks];   // chunk c of the state has reached the host (down)
+    cudaEvent_t ev_read;                // the last read-back of a call has landed (down)
+    cudaEvent_t ev_join;                // everything enqueued on down so far (flr_host_join)
+    float *stage;                       // [2][cap][3] positions, then velocities
+    int cap;
+    int last_n;                         // atoms of the previous call (-1: no copies in flight yet)
 };
 
 struct ProfState {
@@ -296,6 +313,12 @@ constexpr float kVarSmallBF16x3 = 2e-2f;
 int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, const float *forces,
                     const int *species, int n, const KickArgs &kick, float dt, float disp2_max,
                     cudaStream_t st);
+// MD state between host float[n][3] staging rows and the device float[n][4]
+// working copies (flr_md_step_host)
+int launch_state_unpack(flr_ctx *ctx, const float *pos3, const float *vel3, float4 *pos, float4 *vel, int n,
+                        cudaStream_t st);
+int launch_state_pack(flr_ctx *ctx, const float4 *pos, const float4 *vel, float *pos3, float *vel3, int n,
+                      cudaStream_t st);
 
 // Grid of a persistent kernel: every SM filled to its occupancy limit, but
 // never more blocks than there is work for.

@@ -61,6 +61,34 @@ __global__ void __launch_bounds__(256) k_md_drift(DriftArgs a)
     if (__any_sync(0xffffffffu, moved) && (threadIdx.x & 31) == 0) a.flags[0] = 1;
 }
 
+// Host-state MD: the state crosses the host link as x, y, z rows (12 bytes
+// per atom and array instead of 16); these two kernels move it between those
+// staging rows and the float4 working copies.  w of the positions is set to
+// 0 (unused by every kernel), w of the velocities likewise.
+__global__ void __launch_bounds__(256) k_state_unpack(const float *p3, const float *v3, float4 *pos, float4 *vel,
+                                                      int n)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const size_t k = 3 * (size_t)i;
+    pos[i] = make_float4(p3[k], p3[k + 1], p3[k + 2], 0.f);
+    vel[i] = make_float4(v3[k], v3[k + 1], v3[k + 2], 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_state_pack(const float4 *pos, const float4 *vel, float *p3, float *v3, int n)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const size_t k = 3 * (size_t)i;
+    const float4 p = pos[i], v = vel[i];
+    p3[k] = p.x;
+    p3[k + 1] = p.y;
+    p3[k + 2] = p.z;
+    v3[k] = v.x;
+    v3[k + 1] = v.y;
+    v3[k + 2] = v.z;
+}
+
 // Kinetic energy sum_i m_i v_i^2 / 2 (eV) in a fixed order: fixed grid,
 // per-block FP64 partials, then one block sums them.
 constexpr int kKeBlocks = 256;
@@ -185,6 +213,24 @@ int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, con
     k_md_drift<<<(n + 255) / 256, 256, 0, st>>>(a);
     count_launch(ctx);
     return cuda_fail(cudaGetLastError(), "md drift");
+}
+
+int launch_state_unpack(flr_ctx *ctx, const float *pos3, const float *vel3, float4 *pos, float4 *vel, int n,
+                        cudaStream_t st)
+{
+    if (n <= 0) return FLR_OK;
+    k_state_unpack<<<(n + 255) / 256, 256, 0, st>>>(pos3, vel3, pos, vel, n);
+    count_launch(ctx);
+    return cuda_fail(cudaGetLastError(), "unpack host state");
+}
+
+int launch_state_pack(flr_ctx *ctx, const float4 *pos, const float4 *vel, float *pos3, float *vel3, int n,
+                      cudaStream_t st)
+{
+    if (n <= 0) return FLR_OK;
+    k_state_pack<<<(n + 255) / 256, 256, 0, st>>>(pos, vel, pos3, vel3, n);
+    count_launch(ctx);
+    return cuda_fail(cudaGetLastError(), "pack host state");
 }
 
 int launch_kinetic(flr_ctx *ctx, const float4 *vel, const int32_t *species, int n, const double *masses,

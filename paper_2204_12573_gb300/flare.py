@@ -313,6 +313,51 @@ def md_step(ff: FlareGB, state: MDState, nl: NbrList, n_steps: int, out, stream=
     return out
 
 
+class HostState:
+    """MD state and results in page-locked host memory for md_step_host:
+    pos, vel [n, 3] float32 (read before and written after every step) and
+    the last step's energy [n], forces [n, 3], variance [n], sigma [n] and
+    totals [FLR_NTOTALS] (float64); `results` names the ones to read back."""
+
+    def __init__(self, pos, vel, results=("energy", "forces", "sigma")):
+        n = int(pos.shape[0])
+        self.pos = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        self.vel = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        self.pos.copy_(torch.as_tensor(pos, dtype=torch.float32)[:, :3])
+        self.vel.copy_(torch.as_tensor(vel, dtype=torch.float32)[:, :3])
+        shapes = {"energy": (n,), "forces": (n, 3), "variance": (n,), "sigma": (n,), "totals": (N.NTOTALS,)}
+        self.results = {}
+        for k in results:
+            dt = torch.float64 if k == "totals" else torch.float32
+            self.results[k] = torch.zeros(shapes[k], dtype=dt).pin_memory()
+        c = N.HostState()
+        c.pos = self.pos.data_ptr()
+        c.vel = self.vel.data_ptr()
+        for k, v in self.results.items():
+            setattr(c, k, v.data_ptr())
+        self.c = c
+
+    def __getitem__(self, k):
+        return self.results[k]
+
+
+def md_step_host(ff: FlareGB, state: MDState, nl: NbrList, n_steps: int, out, host: HostState, stream=None):
+    """n_steps of velocity Verlet with the state in host memory: each step
+    uploads host.pos / host.vel, steps on the device (state.system.pos and
+    state.vel are the working copies) and downloads the new state; the last
+    step's results follow.  Asynchronous: read `host` after ff.sync() or
+    host_join + a synchronize."""
+    o = _outputs_struct(out)
+    N.check(ff.lib.flr_md_step_host(ff.handle, ctypes.byref(state.c), nl.handle, int(n_steps), ctypes.byref(o),
+                                    ctypes.byref(host.c), _stream(stream)))
+    return out
+
+
+def host_join(ff: FlareGB, stream=None):
+    """Make `stream` wait for every copy md_step_host has enqueued."""
+    N.check(ff.lib.flr_host_join(ff.handle, _stream(stream)))
+
+
 def sync(ff: FlareGB, stream=None):
     ff.sync(stream)
 

@@ -281,3 +281,69 @@ def test_rebuild_steps_match_a_fresh_build():
     F.md_step(ff3, st3, nl3, 6, out3)
     ff3.sync()
     assert 1 <= int(out3["totals"][13].item()) <= 6
+
+
+def _host_vs_device(s, n_calls, steps_per_call, temperature=0.0, halve_vel_after=None):
+    """The same MD run through flr_md_step (state on the device) and through
+    flr_md_step_host (state in pinned host x, y, z rows, uploaded before and
+    downloaded after every step).  The unpack and pack are copies of x, y, z,
+    so every result must agree bit for bit."""
+    import torch
+    from paper_2204_12573_gb300 import flare as F
+    ffa, sysa, vela, nla, sta = _setup(s, 0.002)
+    ffb, sysb, velb, nlb, stb = _setup(s, 0.002)
+    for st in (sta, stb):
+        st.c.rebuild_every = 3
+        st.c.temperature = temperature
+    outa, outb = F.make_outputs(s.n_atoms), F.make_outputs(s.n_atoms)
+    host = F.HostState(sysb.pos.cpu(), velb.cpu(), results=("energy", "forces", "variance", "sigma", "totals"))
+    # the working copies start from something else: the host rows are the state
+    sysb.pos.zero_()
+    velb.zero_()
+    for k in range(n_calls):
+        F.md_step(ffa, sta, nla, steps_per_call, outa)
+        F.md_step_host(ffb, stb, nlb, steps_per_call, outb, host)
+        if halve_vel_after is not None and k == halve_vel_after:
+            ffa.sync()
+            ffb.sync()              # the host rows may be changed once the copies have landed
+            vela[:, :3] *= 0.5
+            host.vel.mul_(0.5)
+    ffa.sync()
+    ffb.sync()
+    torch.cuda.synchronize()
+    assert np.array_equal(host.pos.numpy(), sysa.pos[:, :3].cpu().numpy())
+    assert np.array_equal(host.vel.numpy(), vela[:, :3].cpu().numpy())
+    for key in ("energy", "forces", "variance", "sigma"):
+        assert np.array_equal(host[key].numpy(), outa[key].cpu().numpy()), key
+    # the virial's FP32 partial sums follow the force kernel's dynamic
+    # atom-to-warp assignment, so it agrees to rounding; every other total
+    # (fixed-order reductions and counts) bit for bit
+    ta, tb = outa["totals"].cpu().numpy(), host["totals"].numpy()
+    vir = slice(1, 10)
+    assert np.abs(ta[vir] - tb[vir]).max() <= 1e-6 * max(1.0, np.abs(ta[vir]).max())
+    assert np.array_equal(np.delete(ta, np.r_[vir]), np.delete(tb, np.r_[vir]))
+    assert sta.step == stb.step == n_calls * steps_per_call
+    # the device working copies hold the same state as the host rows
+    assert np.array_equal(sysb.pos[:, :3].cpu().numpy(), host.pos.numpy())
+    return ta
+
+
+def test_host_state_md_matches_device_md():
+    s = _pt_slab(5)
+    # cadence 3: the list is rebuilt at steps 3 and 6 of the 7
+    _host_vs_device(s, n_calls=7, steps_per_call=1, halve_vel_after=3)
+    _host_vs_device(s, n_calls=2, steps_per_call=3)
+    _host_vs_device(s, n_calls=3, steps_per_call=1, temperature=450.0)
+
+
+def test_host_state_requires_pos_and_vel():
+    import ctypes
+    from paper_2204_12573_gb300 import _native as N, flare as F
+    s = _pt_slab(6)
+    ff, sysg, vel, nl, st = _setup(s, 0.001)
+    out = F.make_outputs(s.n_atoms)
+    host = N.HostState()
+    rc = ff.lib.flr_md_step_host(ff.handle, ctypes.byref(st.c), nl.handle, 1, ctypes.byref(F._outputs_struct(out)),
+                                 ctypes.byref(host), F._stream(None))
+    assert rc != 0
+    assert st.step == 0
