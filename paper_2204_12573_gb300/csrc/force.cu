@@ -35,10 +35,7 @@ namespace {
 
 constexpr int kWarpsForce = 4;                // warps per CTA
 constexpr int kForceBlocks = 4;               // CTAs per SM, any class (shared memory and registers allow 4)
-#ifndef FLR_FORCE1_BLOCKS
-#define FLR_FORCE1_BLOCKS 5
-#endif
-constexpr int kForce1Blocks = FLR_FORCE1_BLOCKS;   // CTAs per SM, one-species classes only
+constexpr int kForce1Blocks = 5;              // CTAs per SM, one-species classes only (96 registers)
 
 template <class FW, int N>
 struct ForceSmem {

@@ -488,7 +488,7 @@ __device__ __forceinline__ void row_general(const RowArgs &a, int kq, int lane, 
     finish_row(a, i, cnt, smask, lane);
 }
 
-constexpr int kBuildWarps = 8;
+constexpr int kBuildWarps = 4;
 constexpr int kTile = 320;   // stencil candidates a warp stages for one bin
 
 // One warp per bin (warps claim bins in order from a counter).  For a
