@@ -51,7 +51,6 @@ struct Pending {
     flr_request req;
     std::vector<float> pos;      // copied inputs
     std::vector<int32_t> species;
-    float bb[8];                 // fractional bounding box (host_frac_bbox), computed by the submitting thread
     int64_t t_submit;
 };
 
@@ -296,9 +295,8 @@ void admit(flr_server *s, std::vector<Pending> &out)
     }
 }
 
-// Pack a batch's inputs and the structures' fractional bounding boxes
-// (computed at submission, on the caller's thread) into the slot's pinned
-// arena (host work only).
+// Pack a batch's inputs into the slot's pinned arena and compute each
+// structure's fractional bounding box (host work only).
 int pack(Slot &sl)
 {
     size_t n = 0;
@@ -315,7 +313,7 @@ int pack(Slot &sl)
         std::memcpy(sl.species + off, q.species.data(), sizeof(int32_t) * (size_t)na);
         std::memcpy(sl.cells + 9 * k, q.req.cell, sizeof(double) * 9);
         for (int d = 0; d < 3; ++d) sl.pbc[3 * k + d] = q.req.pbc[d] ? 1 : 0;
-        std::memcpy(sl.bb + 8 * k, q.bb, sizeof(q.bb));
+        host_frac_bbox(q.req.cell, q.pos.data(), na, sl.bb + 8 * k);
         off += (size_t)na;
     }
     sl.offsets[m] = (int32_t)off;
@@ -626,9 +624,6 @@ int flr_server_submit(flr_server *s, const flr_request *req)
         }
     p.req.pos = nullptr;
     p.req.species = nullptr;
-    // the bin-grid plan's bounding box: here on the caller's thread, so the
-    // worker's per-batch host work is the copies alone
-    host_frac_bbox(p.req.cell, p.pos.data(), p.req.n_atoms, p.bb);
     p.t_submit = now_ns();
     {
         std::lock_guard<std::mutex> lk(s->mu);
