@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
     int p = wc.pos();
     int i = p < n_take ? (a.order ? __ldg(a.order + p) : p) : i_end;
     AtomPre cur = preload(a, i, i_end, lane);
+    preload_pairs(a, cur, i, i_end, lane);
     rows_async<N, FW::kOne>(a, cur, i, i_end, fw.gr, fw.A, lane);
     int p2 = n_take, i2 = i_end;
     AtomPre nxt;
@@ -103,9 +104,11 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
             }
             if (want_vatom && lane < 9) a.vir_atom[9 * (size_t)i + lane] = 0.f;
             rows_async<N, FW::kOne>(a, nxt, i2, i_end, fw.gr, fw.A, lane);
+            preload_pairs(a, nxt, i2, i_end, lane);
             continue;
         }
         force_atom<N, FW>(a, fw, sm.goff, lane, cur, i, nxt, i2, i_end, nq, seq, vir, want_vatom);
+        preload_pairs(a, nxt, i2, i_end, lane);
     }  // atoms
     drain<N, FW>(fw, lane, nq, true, a.rcut, a.Facc, a.status, vir, want_vatom);
     if (want_vatom)

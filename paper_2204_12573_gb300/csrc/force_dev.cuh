@@ -342,17 +342,23 @@ __device__ __forceinline__ AtomPre preload(const ForceArgs &a, int i, int i_end,
     p.nrm = 0.f;
     p.r0 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < i_end) {
-        // read-only loads (ld.global.nc): free to move across the force atomics.
-        // All five are issued at once, none waits for another: the pair count
-        // and record row exist for every atom (lane < 32 <= max_nbr) and are
-        // used only when the atom has pairs, and only below the count.
+        // read-only loads (ld.global.nc): free to move across the force
+        // atomics; all four are issued at once
         p.g = __ldg(a.group + i);
         p.row = __ldg(a.row + i);
         p.nrm = __ldg(a.norm + i);
         p.np = __ldg(a.pair_cnt + i);
-        p.r0 = __ldg(a.pair_rec + (size_t)i * a.max_nbr + lane);
     }
     return p;
+}
+
+// The atom's first 32 pair records, on the lanes below its pair count only
+// (the row holds max_nbr slots, of which about 17 are in use).  Issued once
+// the count has arrived -- after the previous atom's work -- so the load
+// waits for nothing and reads no unused slot.
+__device__ __forceinline__ void preload_pairs(const ForceArgs &a, AtomPre &p, int i, int i_end, int lane)
+{
+    if (i < i_end && lane < p.np) p.r0 = __ldg(a.pair_rec + (size_t)i * a.max_nbr + lane);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
