@@ -1049,7 +1049,11 @@ int ensure_hostio(flr_ctx *c, int n)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_join, cudaEventDisableTiming);
         for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k)
             e = cudaEventCreateWithFlags(&io->ev_down[k], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "host-state streams and events");
+        if (e != cudaSuccess) {
+            const int r = cuda_fail(e, "host-state streams and events");
+            free_hostio(c);   // nothing half-made stays behind for the next call
+            return r;
+        }
     }
     HostIO *io = c->hio;
     if (io->cap < n) {
@@ -1080,6 +1084,7 @@ void free_hostio(flr_ctx *c)
         if (io->ev_down[k]) cudaEventDestroy(io->ev_down[k]);
     delete io;
     c->hio = nullptr;
+    c->out_gate = nullptr;
 }
 
 // Atoms [lo, hi) of chunk k of n.
