@@ -16,8 +16,10 @@
  *   calling thread; the message stays valid until the next call on that
  *   thread.
  * - All per-atom arrays are DEVICE pointers owned by the caller (for example
- *   torch tensors).  The library never frees them and never keeps them past
- *   the call, except where stated for flr_md_state.
+ *   torch tensors), except the HOST arrays of flr_host_state and of the
+ *   server's requests.  The library never frees them and never keeps them
+ *   past the call, except where stated for flr_md_state and flr_host_state
+ *   (asynchronous copies).
  * - Calls that take a cudaStream_t enqueue work on that stream and return
  *   without synchronizing, unless stated otherwise.  Errors found on the
  *   device (neighbour-list overflow, non-finite forces, internal wait
@@ -367,9 +369,11 @@ typedef struct {
  * set).
  * Asynchronous: the copies run on two copy streams of the context, in eight
  * chunks, each chunk's upload for the next step starting once its download
- * has landed, and the results read-back of one call overlaps the next
- * call's kernels (a call's quadratic forms wait for the previous call's
- * read-back before they overwrite the outputs).  The host arrays may be
+ * has landed.  A step's positions are final after its drift and list
+ * rebuild and are downloaded then, while its kernels run, so only the
+ * velocities' round trip lies between two steps; the results read-back of
+ * one call overlaps the next call's kernels (a call's quadratic forms wait
+ * for the previous call's read-back before they overwrite the outputs).  The host arrays may be
  * read or changed only after flr_sync or after `stream` has passed
  * flr_host_join.  FLR_EINVAL for NULL pos or vel or the conditions of
  * flr_md_step. */

@@ -1047,8 +1047,8 @@ int ensure_hostio(flr_ctx *c, int n)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_packed, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_read, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_join, cudaEventDisableTiming);
-        for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k)
-            e = cudaEventCreateWithFlags(&io->ev_down[k], cudaEventDisableTiming);
+        for (int k = 0; k < 2 * kHostChunks && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&io->ev_down[k / kHostChunks][k % kHostChunks], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             const int r = cuda_fail(e, "host-state streams and events");
             free_hostio(c);   // nothing half-made stays behind for the next call
@@ -1080,8 +1080,8 @@ void free_hostio(flr_ctx *c)
     cudaEvent_t evs[4] = {io->ev_up, io->ev_packed, io->ev_read, io->ev_join};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
-    for (int k = 0; k < kHostChunks; ++k)
-        if (io->ev_down[k]) cudaEventDestroy(io->ev_down[k]);
+    for (int k = 0; k < 2 * kHostChunks; ++k)
+        if (io->ev_down[k / kHostChunks][k % kHostChunks]) cudaEventDestroy(io->ev_down[k / kHostChunks][k % kHostChunks]);
     delete io;
     c->hio = nullptr;
     c->out_gate = nullptr;
@@ -1094,53 +1094,55 @@ inline void chunk_range(int n, int k, size_t &lo, size_t &hi)
     hi = (size_t)n * (k + 1) / kHostChunks;
 }
 
-// Host state -> staging rows (chunk k after the previous download of the
-// same chunk has reached the host) -> working copies on `st`.
+// Host state -> staging rows -> working copies on `st`.  Each chunk's
+// upload waits only for the previous download of the same chunk, and all
+// position chunks go before the velocity chunks: the positions of a step are
+// final (and downloaded) once its drift and rebuild are done, so the next
+// step's position uploads run while the step's kernels still do, and only
+// the velocities' round trip remains between two steps.
 int host_upload(flr_ctx *c, const flr_host_state *h, flr_md_state *md, cudaStream_t st)
 {
     HostIO *io = c->hio;
     const int n = md->n_atoms;
-    float *p3 = io->stage, *v3 = io->stage + 3 * (size_t)io->cap;
+    float *rows[2] = {io->stage, io->stage + 3 * (size_t)io->cap};
+    const float *src[2] = {h->pos, h->vel};
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
-        size_t lo, hi;
-        chunk_range(n, k, lo, hi);
-        if (io->last_n >= 0)
-            e = cudaStreamWaitEvent(io->up, io->ev_down[io->last_n == n ? k : kHostChunks - 1], 0);
-        if (e == cudaSuccess && hi > lo)
-            e = cudaMemcpyAsync(p3 + 3 * lo, h->pos + 3 * lo, 12 * (hi - lo), cudaMemcpyHostToDevice, io->up);
-        if (e == cudaSuccess && hi > lo)
-            e = cudaMemcpyAsync(v3 + 3 * lo, h->vel + 3 * lo, 12 * (hi - lo), cudaMemcpyHostToDevice, io->up);
-    }
+    for (int q = 0; q < 2; ++q)
+        for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
+            size_t lo, hi;
+            chunk_range(n, k, lo, hi);
+            if (io->last_n >= 0)
+                e = cudaStreamWaitEvent(io->up, io->ev_down[q][io->last_n == n ? k : kHostChunks - 1], 0);
+            if (e == cudaSuccess && hi > lo)
+                e = cudaMemcpyAsync(rows[q] + 3 * lo, src[q] + 3 * lo, 12 * (hi - lo), cudaMemcpyHostToDevice, io->up);
+        }
     if (e == cudaSuccess) e = cudaEventRecord(io->ev_up, io->up);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, io->ev_up, 0);
     if (e != cudaSuccess) return cuda_fail(e, "upload host state");
-    return launch_state_unpack(c, p3, v3, reinterpret_cast<float4 *>(md->pos), reinterpret_cast<float4 *>(md->vel), n,
-                               st);
+    return launch_state_unpack(c, rows[0], rows[1], reinterpret_cast<float4 *>(md->pos),
+                               reinterpret_cast<float4 *>(md->vel), n, st);
 }
 
-// Working copies -> staging rows on `st` -> host state, in chunks on the
-// download stream.
-int host_download(flr_ctx *c, const flr_host_state *h, flr_md_state *md, cudaStream_t st)
+// Positions (q = 0) or velocities (q = 1) of the working copies -> staging
+// rows on `st` -> host, in chunks on the download stream.
+int host_download(flr_ctx *c, const flr_host_state *h, flr_md_state *md, int q, cudaStream_t st)
 {
     HostIO *io = c->hio;
     const int n = md->n_atoms;
-    float *p3 = io->stage, *v3 = io->stage + 3 * (size_t)io->cap;
-    int s = launch_state_pack(c, reinterpret_cast<const float4 *>(md->pos), reinterpret_cast<const float4 *>(md->vel),
-                              p3, v3, n, st);
+    float *rows = io->stage + (q ? 3 * (size_t)io->cap : 0);
+    float *dst = q ? h->vel : h->pos;
+    int s = launch_state_pack(c, reinterpret_cast<const float4 *>(q ? md->vel : md->pos), rows, n, st);
     if (s != FLR_OK) return s;
     cudaError_t e = cudaEventRecord(io->ev_packed, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(io->down, io->ev_packed, 0);
     for (int k = 0; k < kHostChunks && e == cudaSuccess; ++k) {
         size_t lo, hi;
         chunk_range(n, k, lo, hi);
-        if (hi > lo) e = cudaMemcpyAsync(h->pos + 3 * lo, p3 + 3 * lo, 12 * (hi - lo), cudaMemcpyDeviceToHost, io->down);
-        if (e == cudaSuccess && hi > lo)
-            e = cudaMemcpyAsync(h->vel + 3 * lo, v3 + 3 * lo, 12 * (hi - lo), cudaMemcpyDeviceToHost, io->down);
-        if (e == cudaSuccess) e = cudaEventRecord(io->ev_down[k], io->down);
+        if (hi > lo) e = cudaMemcpyAsync(dst + 3 * lo, rows + 3 * lo, 12 * (hi - lo), cudaMemcpyDeviceToHost, io->down);
+        if (e == cudaSuccess) e = cudaEventRecord(io->ev_down[q][k], io->down);
     }
     if (e != cudaSuccess) return cuda_fail(e, "download host state");
-    io->last_n = n;
+    if (q == 1) io->last_n = n;
     return FLR_OK;
 }
 
@@ -1263,6 +1265,8 @@ int md_run(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_o
         prof_begin(c, FLR_KERNEL_REBUILD, st);
         if (s == FLR_OK) s = launch_rebuild_cond(c, nl, pos, md->species, n, st, true, pos);
         prof_end(c, FLR_KERNEL_REBUILD, st);
+        // the step's positions are final here (drift, wrap at a rebuild)
+        if (s == FLR_OK && h) s = host_download(c, h, md, 0, st);
         if (s == FLR_OK) s = evaluate(c, nl, pos, md->species, n, &o, kick, st);
         if (s == FLR_OK && nvt) {
             // second half step from the kinetic energy after the final kick
@@ -1282,7 +1286,7 @@ int md_run(flr_ctx *c, flr_md_state *md, flr_nbrlist *nl, int32_t n_steps, flr_o
             if (s != FLR_OK) return s;
             if (cnt > 0) md->halted = 1;
         }
-        if (h) s = host_download(c, h, md, st);
+        if (h) s = host_download(c, h, md, 1, st);
         if (s != FLR_OK) return s;
         if (md->halted) break;
     }

@@ -187,8 +187,8 @@ constexpr int kHostChunks = 8;
 struct HostIO {
     cudaStream_t up, down;
     cudaEvent_t ev_up;                  // this step's inputs are in the staging rows (up)
-    cudaEvent_t ev_packed;              // the step's state is in the staging rows (compute stream)
-    cudaEvent_t ev_down[kHostChunks];   // chunk c of the state has reached the host (down)
+    cudaEvent_t ev_packed;              // positions or velocities are in the staging rows (compute stream)
+    cudaEvent_t ev_down[2][kHostChunks];   // chunk c of the positions [0] / velocities [1] has reached the host (down)
     cudaEvent_t ev_read;                // the last read-back of a call has landed (down)
     cudaEvent_t ev_join;                // everything enqueued on down so far (flr_host_join)
     float *stage;                       // [2][cap][3] positions, then velocities
@@ -317,8 +317,7 @@ int launch_md_drift(flr_ctx *ctx, flr_nbrlist *nl, float4 *pos, float4 *vel, con
 // working copies (flr_md_step_host)
 int launch_state_unpack(flr_ctx *ctx, const float *pos3, const float *vel3, float4 *pos, float4 *vel, int n,
                         cudaStream_t st);
-int launch_state_pack(flr_ctx *ctx, const float4 *pos, const float4 *vel, float *pos3, float *vel3, int n,
-                      cudaStream_t st);
+int launch_state_pack(flr_ctx *ctx, const float4 *src, float *dst3, int n, cudaStream_t st);
 
 // Grid of a persistent kernel: every SM filled to its occupancy limit, but
 // never more blocks than there is work for.

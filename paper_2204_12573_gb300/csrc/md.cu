@@ -75,18 +75,15 @@ __global__ void __launch_bounds__(256) k_state_unpack(const float *p3, const flo
     vel[i] = make_float4(v3[k], v3[k + 1], v3[k + 2], 0.f);
 }
 
-__global__ void __launch_bounds__(256) k_state_pack(const float4 *pos, const float4 *vel, float *p3, float *v3, int n)
+__global__ void __launch_bounds__(256) k_state_pack(const float4 *src, float *dst3, int n)
 {
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const size_t k = 3 * (size_t)i;
-    const float4 p = pos[i], v = vel[i];
-    p3[k] = p.x;
-    p3[k + 1] = p.y;
-    p3[k + 2] = p.z;
-    v3[k] = v.x;
-    v3[k + 1] = v.y;
-    v3[k + 2] = v.z;
+    const float4 v = src[i];
+    dst3[k] = v.x;
+    dst3[k + 1] = v.y;
+    dst3[k + 2] = v.z;
 }
 
 // Kinetic energy sum_i m_i v_i^2 / 2 (eV) in a fixed order: fixed grid,
@@ -224,11 +221,10 @@ int launch_state_unpack(flr_ctx *ctx, const float *pos3, const float *vel3, floa
     return cuda_fail(cudaGetLastError(), "unpack host state");
 }
 
-int launch_state_pack(flr_ctx *ctx, const float4 *pos, const float4 *vel, float *pos3, float *vel3, int n,
-                      cudaStream_t st)
+int launch_state_pack(flr_ctx *ctx, const float4 *src, float *dst3, int n, cudaStream_t st)
 {
     if (n <= 0) return FLR_OK;
-    k_state_pack<<<(n + 255) / 256, 256, 0, st>>>(pos, vel, pos3, vel3, n);
+    k_state_pack<<<(n + 255) / 256, 256, 0, st>>>(src, dst3, n);
     count_launch(ctx);
     return cuda_fail(cudaGetLastError(), "pack host state");
 }
