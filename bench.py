@@ -577,8 +577,9 @@ def run_ours(args):
     # call per step, uploads the step's positions and velocities from pinned
     # host memory (x, y, z rows), steps on the device, downloads the new state
     # and then reads back the step's energies, forces and sigma (asynchronous;
-    # the library overlaps one call's read-back with the next call's kernels
-    # and each chunk's upload with the previous download)
+    # the library moves the positions while the step's kernels run, overlaps
+    # one call's read-back with the next call's kernels and each chunk's
+    # upload with the previous download)
     e2e = None
     if not args.no_e2e:
         ff.set_precision("bf16x3")
@@ -605,8 +606,9 @@ def run_ours(args):
         e2e = {"value": job_throughput(world, n, args.steps, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "note": "per step one flr_md_step_host call: H2D pos+vel (pinned x, y, z rows), md step, D2H pos+vel, "
-                       "then D2H energy, forces, sigma; the state round trip in 8 chunks on two copy streams, the "
-                       "read-back overlapping the next call's kernels"}
+                       "then D2H energy, forces, sigma; copies in 8 chunks on two copy streams, the positions "
+                       "downloaded (and the next step's uploaded) while the step's kernels run, the read-back "
+                       "overlapping the next call's kernels"}
 
     serving = None
     if args.serving_seconds > 0:
