@@ -177,23 +177,9 @@ struct flr_ctx {
     int maps_prec;
     // per-kernel event timing (flr_profile_*)
     struct ProfState *prof;
-    // host-state MD (flr_md_step_host): copy streams, events and staging rows
+    // host-state MD (flr_md_step_host): copy streams, events and staging rows (api.cu)
     struct HostIO *hio;
     cudaEvent_t out_gate;      // when set, evaluations wait for it before writing their outputs
-};
-
-// Copy streams, events and device staging rows of flr_md_step_host.
-constexpr int kHostChunks = 8;
-struct HostIO {
-    cudaStream_t up, down;
-    cudaEvent_t ev_up;                  // this step's inputs are in the staging rows (up)
-    cudaEvent_t ev_packed;              // positions or velocities are in the staging rows (compute stream)
-    cudaEvent_t ev_down[2][kHostChunks];   // chunk c of the positions [0] / velocities [1] has reached the host (down)
-    cudaEvent_t ev_read;                // the last read-back of a call has landed (down)
-    cudaEvent_t ev_join;                // everything enqueued on down so far (flr_host_join)
-    float *stage;                       // [2][cap][3] positions, then velocities
-    int cap;
-    int last_n;                         // atoms of the previous call (-1: no copies in flight yet)
 };
 
 struct ProfState {
