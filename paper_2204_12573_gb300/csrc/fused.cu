@@ -104,7 +104,7 @@ struct FusedArgs {
 };
 
 // A warp-wide bounded wait on an mbarrier phase (lane 0 waits, the warp
-// follows its verdict); on failure records the timeout and raises the abort flag.
+// follows its result); on failure records the timeout and raises the abort flag.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int lane, volatile int *abort_flag,
                                           int *status)
 {

@@ -130,7 +130,7 @@ __device__ __forceinline__ void load16(const float *p, float v[16])
 }
 
 // Epilogue: wait for a full accumulator (lane 0 waits, the warp follows its
-// verdict, so the warp stays converged); false on timeout or abort.
+// result, so the warp stays converged); false on timeout or abort.
 __device__ __forceinline__ bool acc_wait(uint32_t tfull, int it, int lane, volatile int *abort_flag, int *status)
 {
     int okw = 1;
