@@ -121,12 +121,13 @@ __host__ __device__ constexpr bool grad_nz(int lm, int c)
 // l of harmonic index lm
 __host__ __device__ constexpr int l_of(int lm) { return lm < 1 ? 0 : (lm < 4 ? 1 : (lm < 9 ? 2 : 3)); }
 
-// T_n(x) (r_cut - r)^2 for n < N, and optionally its r-derivative
+// T_n(x) (r_cut - r)^2 for n < N, and optionally its r-derivative;
+// tr = 2 / r_cut, so x = r tr - 1 needs no division per pair
 template <int N, bool GRAD>
-__device__ __forceinline__ void radial(float r, float rc, float Rf[N], float dRf[N])
+__device__ __forceinline__ void radial(float r, float rc, float tr, float Rf[N], float dRf[N])
 {
-    const float x = 2.f * r / rc - 1.f;
-    const float dxdr = 2.f / rc;
+    const float x = r * tr - 1.f;
+    const float dxdr = tr;
     const float t = rc - r;
     const float fc = t * t;
     const float dfc = -2.f * t;

@@ -125,6 +125,7 @@ int launch_desc(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const in
     a.cells.shift = nl->shift_d;
     a.cells.struct_of = nl->n_structs > 1 ? nl->struct_of : nullptr;
     a.rcut = (float)ctx->p.r_cut;
+    a.two_over_rc = (float)(2.0 / ctx->p.r_cut);
     a.tab[0] = ctx->tab_full;
     a.tab[1] = ctx->tab_single;
     for (int r = 0; r < 2; ++r) {

@@ -32,6 +32,7 @@ struct DescArgs {
     int max_nbr, n;
     Cells cells;               // per-structure image shifts
     float rcut;
+    float two_over_rc;         // 2 / r_cut (the radial basis' x = 2 r / r_cut - 1 as one FMA)
     const int32_t *tab[2];     // compact index -> (a, b, l)
     int K[2], kp32[2], kp64[2];
     float *A;                  // [n][2N*16]
@@ -83,7 +84,7 @@ struct __align__(16) DescWarp {
 // accumulation picks the accumulator by a warp-uniform index test instead of
 // loading each pair's species.
 template <int N, class W>
-__device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, float acc0[4], float acc1[4])
+__device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, float tr, float acc0[4], float acc1[4])
 {
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     if (lane < m) r = dw.rec[lane];
@@ -96,7 +97,7 @@ __device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, flo
         const float d2 = r.x * r.x + r.y * r.y + r.z * r.z;
         const float rr = sqrtf(d2), inv = 1.f / rr;
         float Rf[N], dummy[N];
-        radial<N, false>(rr, rc, Rf, dummy);
+        radial<N, false>(rr, rc, tr, Rf, dummy);
         float Y[16];
         real_ylm(r.x * inv, r.y * inv, r.z * inv, Y);
 #pragma unroll
@@ -221,7 +222,7 @@ __device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, c
         np += __popc(m);
         __syncwarp();
         while (nv >= BATCH) {
-            desc_batch<N>(dw, lane, BATCH, rc, acc0, acc1);
+            desc_batch<N>(dw, lane, BATCH, rc, a.two_over_rc, acc0, acc1);
             const float4 rest = lane < nv - BATCH ? dw.rec[BATCH + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp();
             if (lane < nv - BATCH) dw.rec[lane] = rest;
@@ -229,7 +230,7 @@ __device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, c
             __syncwarp();
         }
     }
-    if (nv > 0) desc_batch<N>(dw, lane, nv, rc, acc0, acc1);
+    if (nv > 0) desc_batch<N>(dw, lane, nv, rc, a.two_over_rc, acc0, acc1);
     if (lane == 0) a.pair_cnt[i] = np;
 
     // A to shared memory (padded rows) and to global memory (blocks in use only)

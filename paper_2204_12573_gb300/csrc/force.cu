@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kWarpsForce * 32, MINB) k_force(ForceArgs a)
         force_atom<N, FW>(a, fw, sm.goff, lane, cur, i, nxt, i2, i_end, nq, seq, vir, want_vatom);
         preload_pairs(a, nxt, i2, i_end, lane);
     }  // atoms
-    drain<N, FW>(fw, lane, nq, true, a.rcut, a.Facc, a.status, vir, want_vatom);
+    drain<N, FW>(fw, lane, nq, true, a.rcut, a.two_over_rc, a.Facc, a.status, vir, want_vatom);
     if (want_vatom)
         for (int s = 0; s < kSlots; ++s) flush_slot(fw, lane, s, a.vir_atom);
 
@@ -404,6 +404,7 @@ int launch_force(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     a.max_nbr = nl->max_nbr;
     a.n = n;
     a.rcut = (float)ctx->p.r_cut;
+    a.two_over_rc = (float)(2.0 / ctx->p.r_cut);
     for (int r = 0; r < 2; ++r) {
         a.K[r] = ctx->dims.K[r];
         a.G[r] = ctx->G[r];

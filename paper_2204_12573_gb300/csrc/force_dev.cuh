@@ -38,6 +38,7 @@ struct ForceArgs {
     const int32_t *entries, *count, *group, *row;
     int max_nbr, n;
     float rcut;
+    float two_over_rc;         // 2 / r_cut (x = 2 r / r_cut - 1 as one FMA per pair)
     int K[2];
     const float *G[2];         // g = dE/dB rows from the quadratic-form epilogue
     const float *A, *norm;
@@ -131,11 +132,11 @@ __device__ __forceinline__ long long to_fix(float v, int *status)
 
 // Evaluate m <= 32 queued pairs, one per lane.
 template <int N, class FW>
-__device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
+__device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc, float tr,
                                             unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     int my_slot = -1;
-    float dv[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float pr[3] = {0.f, 0.f, 0.f}, pf[3] = {0.f, 0.f, 0.f};   // this lane's r_ij and f_ij (per-atom virial)
     if (lane < m) {
         const float4 rec = fw.q[lane];
         const int packed = __float_as_int(rec.w);
@@ -151,9 +152,9 @@ __device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
         //   c_lm = f_c s_lm,  c'_lm = (2/r_cut) f_c s'_lm + f_c' s_lm,
         //   s_lm = sum_n w_{n,lm} T_n(x),  s'_lm = sum_n w_{n,lm} T_n'(x),
         // so T_0 = 1 and T_1' = 1 cost no multiply and T_0' = 0 no term.
-        const float x = 2.f * rr / rc - 1.f;
+        const float x = rr * tr - 1.f;
         const float tc = rc - rr;
-        const float fc = tc * tc, dfc = -2.f * tc, k1 = (2.f / rc) * fc;
+        const float fc = tc * tc, dfc = -2.f * tc, k1 = tr * fc;
         float T[N], dT[N];
         cheb_tail<N>(x, T, dT);
         const float *wp = fw.W + slot * FW::WSLOT + (FW::kOne ? 0 : sj * 128);
@@ -198,11 +199,11 @@ __device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
         atomicAdd(di + 0, (unsigned long long)ix);
         atomicAdd(di + 1, (unsigned long long)iy);
         atomicAdd(di + 2, (unsigned long long)iz);
-        dv[0] = -rec.x * fx; dv[1] = -rec.x * fy; dv[2] = -rec.x * fz;
-        dv[3] = -rec.y * fx; dv[4] = -rec.y * fy; dv[5] = -rec.y * fz;
-        dv[6] = -rec.z * fx; dv[7] = -rec.z * fy; dv[8] = -rec.z * fz;
+        // W_ab -= (r_ij)_a (f_ij)_b, one FMA per entry
+        pr[0] = rec.x; pr[1] = rec.y; pr[2] = rec.z;
+        pf[0] = fx; pf[1] = fy; pf[2] = fz;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) vir[k] += dv[k];
+        for (int k = 0; k < 9; ++k) vir[k] = fmaf(-pr[k / 3], pf[k % 3], vir[k]);
         my_slot = slot;
     }
     // The per-atom virial (when requested): the queue is filled atom by atom,
@@ -228,7 +229,7 @@ __device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
         const bool leader = (seg & (0u - seg)) == (1u << lane);                    // lowest lane of the segment
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            const long long x = lane < m ? to_fix(dv[c], status) : 0;
+            const long long x = lane < m ? to_fix(-pr[c / 3] * pf[c % 3], status) : 0;
             const unsigned lo = __reduce_add_sync(seg, (unsigned)(x & 0x3FFFFF));
             const int hi = __reduce_add_sync(seg, (int)(x >> 22));
             if (leader && lane < m) fw.V[my_slot][c] += (long long)hi * 4194304ll + (long long)lo;
@@ -239,12 +240,12 @@ __device__ __forceinline__ void force_batch(FW &fw, int lane, int m, float rc,
 
 // Evaluate every queued pair (all) or every full batch, and compact the queue.
 template <int N, class FW>
-__device__ __forceinline__ void drain(FW &fw, int lane, int &nq, bool all, float rc,
+__device__ __forceinline__ void drain(FW &fw, int lane, int &nq, bool all, float rc, float tr,
                                       unsigned long long *Facc, int *status, float vir[9], bool want_vatom)
 {
     while (nq >= 32 || (all && nq > 0)) {
         const int m = nq < 32 ? nq : 32;
-        force_batch<N, FW>(fw, lane, m, rc, Facc, status, vir, want_vatom);
+        force_batch<N, FW>(fw, lane, m, rc, tr, Facc, status, vir, want_vatom);
         const int rest = nq - m;
         float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
         int sq = 0;
@@ -410,7 +411,8 @@ __device__ __forceinline__ void force_atom(const ForceArgs &a, FW &fw, const int
 
     // w slot for this atom: if a queued pair still refers to the slot, evaluate the queue first
     const int slot = seq & (kSlots - 1);
-    if (nq > 0 && fw.qseq[0] <= seq - kSlots) drain<N, FW>(fw, lane, nq, true, rc, a.Facc, a.status, vir, want_vatom);
+    if (nq > 0 && fw.qseq[0] <= seq - kSlots)
+        drain<N, FW>(fw, lane, nq, true, rc, a.two_over_rc, a.Facc, a.status, vir, want_vatom);
     if (want_vatom) flush_slot(fw, lane, slot, a.vir_atom);   // otherwise the slot holds nothing to write
     if (lane == 0) fw.atom[slot] = i;
 
@@ -475,7 +477,7 @@ __device__ __forceinline__ void force_atom(const ForceArgs &a, FW &fw, const int
         }
         nq += take;
         __syncwarp();
-        drain<N, FW>(fw, lane, nq, false, rc, a.Facc, a.status, vir, want_vatom);
+        drain<N, FW>(fw, lane, nq, false, rc, a.two_over_rc, a.Facc, a.status, vir, want_vatom);
     }
     ++seq;
 }

@@ -487,6 +487,7 @@ int launch_fused(flr_ctx *ctx, const flr_nbrlist *nl, const float4 *pos, const i
     d.cells.shift = nl->shift_d;
     d.cells.struct_of = nl->n_structs > 1 ? nl->struct_of : nullptr;
     d.rcut = (float)ctx->p.r_cut;
+    d.two_over_rc = (float)(2.0 / ctx->p.r_cut);
     d.tab[0] = ctx->tab_full;
     d.tab[1] = ctx->tab_single;
     for (int r = 0; r < 2; ++r) {
