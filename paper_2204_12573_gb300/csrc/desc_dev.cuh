@@ -24,6 +24,7 @@ namespace {
 
 constexpr int kDescAStride = 20;   // padded channel stride of A in shared memory (conflict-free float4 rows)
 constexpr int kYStride = 20;       // padded row of staged harmonics (conflict-free float4 stores)
+constexpr int kRfStride = 12;      // padded row of a pair's staged radial values (two conflict-free float4 stores)
 
 struct DescArgs {
     const float4 *pos;
@@ -58,7 +59,7 @@ template <int N, int BATCH = 32, bool ONE = false>
 union __align__(16) DescStage {
     struct {
         float Y[BATCH][kYStride];        // harmonics of the staged pairs
-        float Rf[N][BATCH + 1];          // their radial values, pair index fastest
+        float Rf[BATCH][kRfStride];      // their radial values, one padded row per pair
     } p;
     struct {
         float A[2 * N * kDescAStride];
@@ -100,8 +101,11 @@ __device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, flo
         radial<N, false>(rr, rc, tr, Rf, dummy);
         float Y[16];
         real_ylm(r.x * inv, r.y * inv, r.z * inv, Y);
-#pragma unroll
-        for (int n = 0; n < N; ++n) dw.st.p.Rf[n][slot] = Rf[n];
+        static_assert(N >= 5 && N <= 8, "two float4 rows of radial values");
+        float4 *rrow = reinterpret_cast<float4 *>(&dw.st.p.Rf[slot][0]);
+        rrow[0] = make_float4(Rf[0], Rf[1], Rf[2], Rf[3]);
+        rrow[1] = make_float4(Rf[4], N > 5 ? Rf[N > 5 ? 5 : 0] : 0.f, N > 6 ? Rf[N > 6 ? 6 : 0] : 0.f,
+                              N > 7 ? Rf[N > 7 ? 7 : 0] : 0.f);
 #pragma unroll
         for (int k = 0; k < 16; k += 4)
             *reinterpret_cast<float4 *>(&dw.st.p.Y[slot][k]) = make_float4(Y[k], Y[k + 1], Y[k + 2], Y[k + 3]);
@@ -112,13 +116,13 @@ __device__ __forceinline__ void desc_batch(W &dw, int lane, int m, float rc, flo
         // species-0 pairs, then species-1 pairs (the staged order), each in list order
 #pragma unroll 4
         for (int p = 0; p < n0; ++p) {
-            const float rf = dw.st.p.Rf[my_n][p];
+            const float rf = dw.st.p.Rf[p][my_n];
             const float4 y = *reinterpret_cast<const float4 *>(&dw.st.p.Y[p][4 * quad]);
             acc0[0] += rf * y.x; acc0[1] += rf * y.y; acc0[2] += rf * y.z; acc0[3] += rf * y.w;
         }
 #pragma unroll 4
         for (int p = n0; p < m; ++p) {
-            const float rf = dw.st.p.Rf[my_n][p];
+            const float rf = dw.st.p.Rf[p][my_n];
             const float4 y = *reinterpret_cast<const float4 *>(&dw.st.p.Y[p][4 * quad]);
             acc1[0] += rf * y.x; acc1[1] += rf * y.y; acc1[2] += rf * y.z; acc1[3] += rf * y.w;
         }
@@ -237,9 +241,12 @@ __device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, c
     float *sA = dw.st.b.A;   // the staging area is free once the pairs are done
     const int my_n = lane >> 2, quad = lane & 3;
     if (my_n < N) {
-        *reinterpret_cast<float4 *>(sA + my_n * kDescAStride + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
-        *reinterpret_cast<float4 *>(sA + (N + my_n) * kDescAStride + 4 * quad) =
-            make_float4(acc1[0], acc1[1], acc1[2], acc1[3]);
+        // the B2 pass reads only the rows of the class's blocks
+        if (cls != 2)
+            *reinterpret_cast<float4 *>(sA + my_n * kDescAStride + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
+        if (cls != 1)
+            *reinterpret_cast<float4 *>(sA + (N + my_n) * kDescAStride + 4 * quad) =
+                make_float4(acc1[0], acc1[1], acc1[2], acc1[3]);
         float *Ag = a.A + (size_t)i * (C * 16);
         if (cls != 2)
             *reinterpret_cast<float4 *>(Ag + my_n * 16 + 4 * quad) = make_float4(acc0[0], acc0[1], acc0[2], acc0[3]);
