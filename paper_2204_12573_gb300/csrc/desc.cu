@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 5) k_desc(DescArgs a)
             if (lane == 0) a.norm[i] = 0.f;
             continue;
         }
-        const float nrm = desc_atom<N>(a, dw, lane, cur, i);
+        float4 b0;   // channel pair `lane` of B2, kept in registers
+        const float nrm = desc_atom<N, DescWarp<N>, true>(a, dw, lane, cur, i, &b0);
         const float inv = nrm > 0.f ? 1.f / nrm : 0.f;
         const int cls = group_cls(g), reg = group_region(g);
         const int npairs = cls == 0 ? NPF : NPS;
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(kWarpsDesc * 32, 5) k_desc(DescArgs a)
         for (int k = 0; k < MAXP; ++k) {
             const int t = lane + 32 * k;
             if (t < npairs) {
-                const float4 bb = sB[t];
+                const float4 bb = k == 0 ? b0 : sB[t];
                 const float4 v = make_float4(bb.x * inv, bb.y * inv, bb.z * inv, bb.w * inv);
                 if (d32) *reinterpret_cast<float4 *>(d32 + 4 * t) = v;
                 if (dt)

@@ -178,11 +178,14 @@ __device__ __forceinline__ float4 b2_pair(const float *sA, int a, int b)
 // The descriptor of atom i with group g = cur.g >= 0: scans the neighbour
 // list, records the pairs inside r_cut (pair_rec, pair_cnt) for the force
 // kernel, accumulates A (written to global memory, blocks of the class only),
-// contracts B2 of the class's channel pairs into dw.st.b.B (unnormalized),
-// writes ||B|| to norm[i] and returns it.  The caller scales B by 1 / ||B||
-// and writes the normalized row where its quadratic-form kernel reads it.
-template <int N, class W>
-__device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, const DescPre &cur, int i)
+// contracts B2 of the class's channel pairs into dw.st.b.B (unnormalized;
+// with KEEP0, channel pair `lane` goes to *b0 instead, so the first 32 stay
+// in registers), writes ||B|| to norm[i] and returns it.  The caller scales
+// B by 1 / ||B|| and writes the normalized row where its quadratic-form
+// kernel reads it.
+template <int N, class W, bool KEEP0 = false>
+__device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, const DescPre &cur, int i,
+                                          float4 *b0 = nullptr)
 {
     constexpr int C = 2 * N;
     constexpr int BATCH = W::kBatch;
@@ -268,7 +271,10 @@ __device__ __forceinline__ float desc_atom(const DescArgs &a, W &dw, int lane, c
         if (t < npairs) {
             const int e = __ldg(tab + 4 * t);
             const float4 bb = b2_pair(sA, choff + (e & 255), choff + ((e >> 8) & 255));
-            sB[t] = bb;
+            if (KEEP0 && k == 0)
+                *b0 = bb;   // the caller keeps channel pair `lane` in registers
+            else
+                sB[t] = bb;
             ss += bb.x * bb.x + bb.y * bb.y + bb.z * bb.z + bb.w * bb.w;
         }
     }
