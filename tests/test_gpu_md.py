@@ -347,3 +347,31 @@ def test_host_state_requires_pos_and_vel():
                                  ctypes.byref(host), F._stream(None))
     assert rc != 0
     assert st.step == 0
+
+
+def test_host_state_uncertainty_stop():
+    """The uncertainty stop through flr_md_step_host: the call ends after the
+    halting step, and the host rows hold that step's state and results, the
+    same bits as the device-state call."""
+    import torch
+    from paper_2204_12573_gb300 import flare as F
+    s = synth.tiny_system(0)
+    ffa, sysa, vela, nla, _ = _setup(s, 0.0005)
+    ffb, sysb, velb, nlb, _ = _setup(s, 0.0005)
+    sig = F.energy_forces_uncertainty(ffa, sysa, nla)["sigma"].cpu().numpy()
+    thr = 0.9 * float(sig.max())
+    sta = F.MDState(sysa, vela, dt=0.0005, sigma_stop=thr)
+    stb = F.MDState(sysb, velb, dt=0.0005, sigma_stop=thr)
+    outa, outb = F.make_outputs(s.n_atoms), F.make_outputs(s.n_atoms)
+    host = F.HostState(sysb.pos.cpu(), velb.cpu(), results=("energy", "forces", "sigma", "totals"))
+    F.md_step(ffa, sta, nla, 5, outa)
+    F.md_step_host(ffb, stb, nlb, 5, outb, host)
+    ffa.sync()
+    ffb.sync()
+    torch.cuda.synchronize()
+    assert sta.halted and stb.halted and sta.step == stb.step == 1
+    assert np.array_equal(host.pos.numpy(), sysa.pos[:, :3].cpu().numpy())
+    assert np.array_equal(host.vel.numpy(), vela[:, :3].cpu().numpy())
+    for key in ("energy", "forces", "sigma"):
+        assert np.array_equal(host[key].numpy(), outa[key].cpu().numpy()), key
+    assert host["totals"][15].item() == outa["totals"][15].item() >= 1
