@@ -231,53 +231,46 @@ struct TotArgs {
     int kick;
 };
 
-// One block of 128 threads: the FP64 pipe of one SM is narrow on this part,
-// and the warp-shuffle tree costs 12 FP64 adds per thread and level, so fewer
-// threads finish sooner (1024 threads spent most of 40 us in the tree).
-constexpr int kTotThreads = 128;
+// One block per total, 13 blocks on 13 SMs (9 virial entries, E, kinetic
+// energy, max sigma, isolated atoms): the FP64 pipe of one SM is narrow on
+// this part, and one block holding every total waited on the latency of its
+// serial loads (22 us per evaluation).  Each block sums its column of the
+// partials in a fixed order (rows strided over its threads, a fixed
+// shuffle tree, the warps in order).
+constexpr int kTotThreads = 256;
+constexpr int kTotBlocks = 13;
 __global__ void __launch_bounds__(kTotThreads) k_totals(TotArgs a)
 {
-    __shared__ double red[32][12];
-    double acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < a.n_vir; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < 9; ++k) acc[k] += a.vir_part[(size_t)b * 9 + k];
-    for (int b = threadIdx.x; b < a.n_part; b += blockDim.x) {
-        acc[9] += a.part[(size_t)b * 4 + 0];
-        acc[10] += a.part[(size_t)b * 4 + 1];
-        acc[11] = fmax(acc[11], a.part[(size_t)b * 4 + 2]);
+    __shared__ double red[kTotThreads / 32];
+    const int q = blockIdx.x;
+    const bool is_max = q == 11;   // sigma >= 0: 0 is the identity of the max as of the sum
+    const double *src = q < 9 ? a.vir_part + q : a.part + (q - 9);
+    const int stride = q < 9 ? 9 : 4;
+    const int n = q < 9 ? a.n_vir : a.n_part;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < n; b += kTotThreads) {
+        const double v = src[(size_t)b * stride];
+        acc = is_max ? fmax(acc, v) : acc + v;
     }
-    double iso = 0.0;
-    for (int b = threadIdx.x; b < a.n_part; b += blockDim.x) iso += a.part[(size_t)b * 4 + 3];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int o = 16; o; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 11; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-        acc[11] = fmax(acc[11], __shfl_xor_sync(0xffffffffu, acc[11], o));
-        iso += __shfl_xor_sync(0xffffffffu, iso, o);
+        const double y = __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = is_max ? fmax(acc, y) : acc + y;
     }
-    __shared__ double riso[32];
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) red[w][k] = acc[k];
-        riso[w] = iso;
-    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[12] = {0};
-        double I = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            for (int k = 0; k < 11; ++k) t[k] += red[q][k];
-            t[11] = fmax(t[11], red[q][11]);
-            I += riso[q];
-        }
-        a.totals[FLR_TOT_ENERGY] = t[9];
-        for (int k = 0; k < 9; ++k) a.totals[FLR_TOT_VIRIAL + k] = t[k];
-        a.totals[FLR_TOT_MAX_SIGMA] = t[11];
-        a.totals[FLR_TOT_N_ISOLATED] = I;
-        if (a.kick) a.totals[FLR_TOT_KINETIC] = t[10];
+    if (threadIdx.x != 0) return;
+    double t = red[0];
+    for (int w = 1; w < kTotThreads / 32; ++w) t = is_max ? fmax(t, red[w]) : t + red[w];
+    if (q < 9) {
+        a.totals[FLR_TOT_VIRIAL + q] = t;
+    } else if (q == 9) {
+        a.totals[FLR_TOT_ENERGY] = t;
+    } else if (q == 10) {
+        if (a.kick) a.totals[FLR_TOT_KINETIC] = t;
+    } else if (q == 11) {
+        a.totals[FLR_TOT_MAX_SIGMA] = t;
+    } else {
+        a.totals[FLR_TOT_N_ISOLATED] = t;
         a.totals[FLR_TOT_N_VAR_FP64] = a.ref_count ? (double)*a.ref_count : 0.0;
     }
 }
@@ -460,7 +453,7 @@ int launch_finalize(flr_ctx *ctx, const flr_nbrlist *nl, int n, flr_outputs *out
     t.nl_flags = nl ? nl->flags : nullptr;
     t.ref_count = ctx->var_mode == FLR_VAR_AUTO ? ctx->ref_count : nullptr;
     t.kick = kick.enabled;
-    if (out->totals) k_totals<<<1, kTotThreads, 0, st>>>(t);
+    if (out->totals) k_totals<<<kTotBlocks, kTotThreads, 0, st>>>(t);
     count_launch(ctx, out->totals ? 2 : 1);
     return cuda_fail(cudaGetLastError(), "finalize");
 }
